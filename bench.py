@@ -1,0 +1,273 @@
+#!/usr/bin/env python3
+"""Benchmark: signals/s to a certified KKT tolerance of 1e-6 for batch-mode MPL.
+
+One step = one bmpl_solve of the whole batch (every outer iteration of every
+signal until each is certified), inputs resident in HBM when timing starts.
+Workload: the batch compressive-sensing configuration with the paper's
+Table I/II dictionary shape (A 1024 x 8192 Gaussian, unit-norm atoms,
+p = 256 signals, k ~ U[20, 60], lambda_i = 0.02 ||A^T b_i||_inf, rho = 15).
+
+Prints one JSON line.  Under torchrun each rank solves its own batch (the
+signals are independent, eq. 3), so scaling is weak and there is no collective
+on the data path; rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "signals/sec to KKT tol 1e-6 (mixed+warm-start vs plain FP32 BMPL, 1 GB300)"
+UNIT = "signals/s"
+TOL = 1e-6
+FP32_LANES_PER_SM = 128
+
+
+def workload_desc(cfg: str, P, path: str) -> dict:
+    meta = P.meta
+    return {
+        "workload": (f"{cfg}: A {P.n}x{P.m} Gaussian unit-norm atoms, p={P.p} signals, "
+                     f"k~U[{meta.get('kmin')},{meta.get('kmax')}], sigma={meta.get('sigma')}, "
+                     f"lambda_i={meta.get('lam_frac')}*||A^T b_i||_inf, rho={P.rho}, tol={TOL}"),
+        "n": P.n, "m": P.m, "p": P.p, "rho": P.rho, "tol": TOL, "path": path,
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def cpu_baseline(cfg: str, P, max_signals: int) -> dict:
+    import oracle
+    k = min(P.p, max_signals)
+    idx = np.arange(k)
+    threads = oracle.num_threads()
+    t0 = time.perf_counter()
+    oracle.bmpl(P.At, P.B[idx], P.lam[idx], P.rho, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {k} of the {P.p} signals of {cfg}, FP64 Algorithm 1 with exact finish, "
+                      f"OpenMP over signals, {dt:.2f} s wall"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The oracle as the reference arm (CPU, rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_1302_5010_gb300 import synth
+    import oracle
+    P = synth.make_config(args.config)
+    k = min(P.p, args.ref_signals)
+    threads = oracle.num_threads()
+    for _ in range(args.warmup):
+        oracle.bmpl(P.At, P.B[:1], P.lam[:1], P.rho, threads=threads)
+    times = []
+    for s in range(args.steps):
+        idx = (np.arange(k) + s * k) % P.p
+        t0 = time.perf_counter()
+        oracle.bmpl(P.At, P.B[idx], P.lam[idx], P.rho, threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = k * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_desc(args.config, P, "oracle-fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{k} signals per step of {args.config}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--path", default="plain", choices=["plain", "mixed"])
+    ap.add_argument("--ref-signals", type=int, default=64)
+    ap.add_argument("--cpu-signals", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1302_5010_gb300 import mpl, synth
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    # each rank its own batch of independent signals (weak scaling)
+    P = synth.make_config(args.config) if rank == 0 else synth.make_config(args.config, seed_shift=1000 * rank)
+    precision = 1 if args.path == "mixed" else 0
+    At = torch.from_numpy(P.At).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    lam = torch.from_numpy(P.lam).to(dev)
+    X = torch.empty((P.p, P.m), dtype=torch.float32, device=dev)
+    solver = mpl.Solver(At, rho=P.rho, precision=precision)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.solve(B, lam, X, TOL, stream)
+    torch.cuda.synchronize()
+
+    solver.set(mpl.MPL_OPT_PROFILE, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, phase_tot, launches, certified = [], np.zeros(8), 0, True
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0.record(stream)
+        res = solver.solve(B, lam, X, TOL, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        phase_tot += np.array(mpl.mpl_get_phase_times(solver.h), dtype=np.float64)
+        launches += solver.launches()
+        certified &= bool(np.all(res.stats["status"] == mpl.MPL_SIG_CERTIFIED))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    solver.set(mpl.MPL_OPT_PROFILE, 0)
+    tot_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * P.p * args.steps / (tot_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    Bh, lamh = P.B.copy(), P.lam.copy()
+    Xh = np.zeros((P.p, P.m), dtype=np.float32)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve(Bh, lamh, Xh, TOL, None)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": P.p * args.steps / e2e_s * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(Bh.nbytes + lamh.nbytes), "d2h_bytes_per_step": int(Xh.nbytes)}
+
+    # roofline of the dominant phase
+    pk = peaks()
+    names = ["total", "correlation", "selection", "gram", "finish", "master", "residual"]
+    phase = {nm: phase_tot[i] / args.steps for i, nm in enumerate(names)}
+    cols = phase_tot[7] / args.steps  # signal columns processed by the correlation per step
+    flops = 2.0 * P.n * P.m * cols
+    corr_ms = phase["correlation"]
+    if precision == 0:
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak_tf = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "k_corr_f32", "bound": "alu", "peak_unit_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+    else:
+        peak_tf = pk["bf16_tflops"]
+        roof = {"kernel": "k_corr_bf16", "bound": "tensor", "peak_unit_note": f"bf16 dense, {pk['source']}"}
+    achieved = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else 0.0
+    roof.update({"achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                 "traffic": None, "phase_ms_per_step": {k: round(v, 4) for k, v in phase.items()}})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if precision == 0 else "bf16+f32", "data": "synthetic",
+            "config": workload_desc(args.config, P, "plain-fp32" if precision == 0 else "mixed-bf16"),
+            "certified_all": certified, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roof}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.config, P, args.cpu_signals)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

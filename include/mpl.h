@@ -1,0 +1,165 @@
+/*
+ * mpl.h -- C ABI of the GB300 batch-mode Matching Pursuit LASSO library.
+ *
+ * The library solves, for every column b_i of B independently,
+ *
+ *     x_i = argmin_x  lambda_i * ||x||_1 + 0.5 * ||b_i - A x||^2
+ *
+ * which is the LASSO of eq. 2 per signal and the batch problem of eq. 3 with
+ * the 1/2 factor of eq. 2 (eq. 3 as printed omits it; it is the same problem
+ * with lambda halved).  It runs the MPL outer loop of Algorithm 1 for all
+ * signals at once (the batch mode of Sec. 3): the correlation A^T R of the
+ * worst-case analysis for every signal as one GEMM, the rho largest
+ * violators per signal, growth of each active set, the master problem
+ * (eq. "primal_MPL") by accelerated proximal gradient on the Gram block
+ * A_S^T A_S, and the residual R = B - A_S X_S, until every signal meets the
+ * stopping condition ||xi^T A||_inf <= lambda of Sec. 2.3 to a relative
+ * tolerance, certified in FP64.
+ *
+ * Conventions
+ *   - All matrices are column-major with the leading dimension equal to the
+ *     number of rows: A is n x m (each atom a_j is n contiguous floats),
+ *     B is n x p (each signal contiguous), X is m x p (each code contiguous).
+ *   - Pointers may be device memory or host memory (the library tells them
+ *     apart; host buffers are staged through device memory inside the call).
+ *   - Every entry point returns an mpl_status_t; no entry point aborts the
+ *     process.  MPL_ERR_ARG is returned synchronously for bad arguments.
+ *   - A handle is not thread-safe: use one handle per host thread/stream.
+ */
+#ifndef MPL_H
+#define MPL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpl_ctx* mpl_handle_t;
+
+typedef enum {
+    MPL_OK = 0,
+    MPL_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, lambda <= 0 ...) */
+    MPL_ERR_CUDA = 2,           /* a CUDA runtime call failed; the handle may be unusable */
+    MPL_ERR_OOM = 3,            /* device allocation failed */
+    MPL_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+    MPL_ERR_NOT_CONVERGED = 5,  /* solve finished, but some signal is not certified (see stats) */
+    MPL_ERR_UNSUPPORTED = 6     /* option or size outside what this build supports */
+} mpl_status_t;
+
+/* Keys for mpl_set_option / mpl_get_option. */
+typedef enum {
+    MPL_OPT_RHO = 0,        /* atoms added per outer iteration (varrho, Sec. 2.1). default 1 */
+    MPL_OPT_PRECISION = 1,  /* 0: correlation A^T R in FP32 (plain);
+                               1: BF16 operands on tensor cores, FP32 accumulation, with
+                                  near-ties re-scored in FP32 (mixed).  default 0 */
+    MPL_OPT_MAX_OUTER = 2,  /* cap on outer iterations.  default 200 */
+    MPL_OPT_SMAX = 3,       /* capacity of each active set.  default min(n, m, 256) */
+    MPL_OPT_EPS_IN = 4,     /* relative-decrease tolerance of eq. (inner) for the FP32
+                               master problem.  default 1e-4 */
+    MPL_OPT_INNER_MAX = 5,  /* s_max, PG iterations per master problem.  default 400 */
+    MPL_OPT_WARM_START = 6, /* 0: x^0 = 0 (Alg. 1, step 1);
+                               2: proposal network seeds the active sets.  default 0 */
+    MPL_OPT_SYNC_EVERY = 7, /* host/device handshake period in outer iterations. default 1 */
+    MPL_OPT_PROFILE = 8     /* 1: record per-phase device times (mpl_get_phase_times). default 0 */
+} mpl_option_t;
+
+/* Per-signal outcome (host struct filled by mpl_get_stats). */
+typedef enum {
+    MPL_SIG_CERTIFIED = 0,      /* KKT certified to tol in FP64 */
+    MPL_SIG_MAX_OUTER = 1,      /* stopped by MPL_OPT_MAX_OUTER */
+    MPL_SIG_CAPACITY = 2,       /* active set reached MPL_OPT_SMAX */
+    MPL_SIG_UNCERTIFIED = 3,    /* exact finish failed repeatedly */
+    MPL_SIG_NONFINITE = 4       /* NaN/Inf met in the data or iterates */
+} mpl_signal_status_t;
+
+typedef struct {
+    int32_t outer_iters;  /* evaluations of the correlation (FMVPs, Sec. 4.2) */
+    int32_t inner_iters;  /* PG iterations over all master problems (PMVP pairs) */
+    int32_t active_size;  /* |S| at exit */
+    int32_t nnz;          /* nonzeros of x */
+    int32_t status;       /* mpl_signal_status_t */
+    int32_t finishes;     /* FP64 exact-finish attempts */
+    double objective;     /* lambda*||x||_1 + 0.5*||b - A x||^2, FP64 */
+    double kkt;           /* certified upper bound on the max KKT violation / lambda */
+    double gap;           /* relative duality gap with the scaled dual point of eq. 5 */
+} mpl_signal_stats_t;
+
+/*
+ * mpl_create -- load a dictionary.
+ *   A   n x m column-major FP32 (atom j at A + j*n), device or host memory.
+ *       Copied: the caller may free A after the call returns.
+ *   n   signal length, 1 <= n <= 65536.  m  number of atoms, 1 <= m <= 2^26.
+ *   out receives the handle.
+ * The library keeps an FP32 and (on first mixed solve) a BF16 copy of A and
+ * the column norms.  The one-time layout work corresponds to the paper's
+ * offline precomputation for BMPL (Sec. 3, remark on Q).
+ * Errors: MPL_ERR_ARG, MPL_ERR_OOM, MPL_ERR_CUDA.
+ */
+mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out);
+
+/*
+ * bmpl_solve -- solve p LASSO problems sharing the dictionary (eq. 3).
+ *   B       n x p column-major FP32 signals (device or host).
+ *   p       number of signals, p >= 0 (p = 0 returns MPL_OK at once).
+ *   lambda  p FP32 values, each > 0 and finite (device or host).
+ *   X       m x p column-major FP32 output, overwritten with the solutions
+ *           (device or host).
+ *   tol     relative KKT tolerance (e.g. 1e-6): a signal is certified when,
+ *           in FP64 or by a rigorous FP32 error bound, |a_j^T r - lambda*s_j|
+ *           <= tol*lambda on the support and |a_j^T r| <= (1+tol)*lambda off it.
+ *   stream  a cudaStream_t (NULL = legacy default stream).
+ * Device buffers are read and written in stream order; the call returns after
+ * the solve has completed on the stream (the outer loop is host-driven), so X
+ * and the statistics are ready on return.
+ * Returns MPL_OK when every signal is certified, MPL_ERR_NOT_CONVERGED when
+ * some signal is not (its best iterate is still written to X), or an error.
+ */
+mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lambda, float* X,
+                        double tol, void* stream);
+
+/*
+ * mpl_correlate -- the worst-case analysis product of Algorithm 1, step 3,
+ * g_i = A^T r_i for p given vectors (a full matrix-vector product, FMVP,
+ * Sec. 2.4), computed by the handle's current correlation path
+ * (MPL_OPT_PRECISION).
+ *   R  n x p column-major FP32 (device or host).
+ *   C  m x p column-major FP32 output, C[i*m + j] = a_j^T r_i (device or host).
+ * Synchronous with respect to the stream.  Errors: MPL_ERR_ARG, MPL_ERR_CUDA,
+ * MPL_ERR_TIMEOUT (a bounded tensor-core pipeline wait expired).
+ */
+mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void* stream);
+
+/* Release the handle and all its device memory.  NULL-safe. */
+void mpl_destroy(mpl_handle_t h);
+
+/* Set / read an option (mpl_option_t).  Errors: MPL_ERR_ARG for unknown keys or
+ * out-of-range values, MPL_ERR_UNSUPPORTED for modes this build lacks. */
+mpl_status_t mpl_set_option(mpl_handle_t h, int key, double value);
+mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* value);
+
+/* Copy per-signal statistics of the last bmpl_solve to host memory
+ * (p entries; p must equal the last solve's p). */
+mpl_status_t mpl_get_stats(mpl_handle_t h, int p, mpl_signal_stats_t* host_out);
+
+/* Copy the last solve's FP64 solutions (the certified iterates, before the
+ * FP32 rounding of X) as a dense m x p column-major array (device or host). */
+mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
+
+/* Phase data of the last solve.  Entries 0..6 are device milliseconds,
+ * filled when MPL_OPT_PROFILE is 1: total, correlation, selection, Gram
+ * growth, exact finish, master problem, residual.  Entry 7 is the number of
+ * signal columns the correlation processed, summed over outer iterations
+ * (always filled).  Returns the number of values written (<= cap, <= 8). */
+int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
+
+/* Number of CUDA kernel launches issued by the last bmpl_solve. */
+int64_t mpl_get_launch_count(mpl_handle_t h);
+
+/* Human-readable text for a status code (static storage). */
+const char* mpl_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPL_H */

@@ -1,0 +1,570 @@
+// C ABI of the BMPL library (include/mpl.h): handle, options, device
+// workspace and the outer loop of Algorithm 1 over all signals (Sec. 3).
+//
+// One outer iteration, for the signals still active:
+//   correlation  C = A^T R                       (FP32 SIMT or BF16 tcgen05)
+//   selection    top-rho violators, stop test     (k_select, k_compact)
+//   growth       Gram rows A_S^T A_J, h_J         (k_gram)
+//   finish       FP64 exact finish / certificate  (k_finish, signals w/o violators)
+//   master       accelerated PG on the Gram block (k_apg, persistent work queue)
+//   residual     R = B - A_S X_S                  (k_residual)
+// followed by one 40-byte device-to-host read of the work counters.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mpl_internal.cuh"
+
+using namespace mpl;
+
+namespace {
+
+// Option key for phase timing (not part of the public enum).
+constexpr int OPT_PROFILE = MPL_OPT_PROFILE;
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mpl_ctx {
+    int n = 0, m = 0, dev = 0, sms = 0;
+    float* A32 = nullptr;
+    __nv_bfloat16* A16 = nullptr;
+    float* colnorm = nullptr;
+    float* scal = nullptr;  // device scalars: [0] = max column norm
+    float colmax = 0.f;
+    // options
+    int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
+    int sync_every = 1, profile = 0;
+    double eps_in = 1e-4;
+    // workspace
+    int cap_p = 0, cap_smax = 0;
+    bool cap_r16 = false;
+    std::vector<Buf> bufs;
+    Dev dv{};
+    Counters* cnt_h = nullptr;  // pinned
+    // staging for host-resident arguments
+    float* Bst = nullptr;
+    float* lamst = nullptr;
+    float* Xst = nullptr;
+    size_t Bst_b = 0, lamst_b = 0, Xst_b = 0;
+    // tensor-map block for the BF16 GEMM (A16, R16c)
+    alignas(64) unsigned char tmap[256];
+    int tmap_p = -1;
+    // last solve
+    int last_p = 0;
+    std::vector<mpl_signal_stats_t> stats;
+    int64_t launches = 0;
+    double phase_ms[8] = {0};
+    std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+mpl_status_t from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return MPL_OK;
+    if (e == cudaErrorMemoryAllocation) return MPL_ERR_OOM;
+    if (e == cudaErrorNotSupported) return MPL_ERR_UNSUPPORTED;
+    return MPL_ERR_CUDA;
+}
+
+#define CK(x)                                               \
+    do {                                                    \
+        cudaError_t e_ = (x);                               \
+        if (e_ != cudaSuccess) {                            \
+            if (getenv("MPL_DEBUG"))                        \
+                fprintf(stderr, "mpl: %s failed: %s (%s:%d)\n", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return from_cuda(e_);                           \
+        }                                                   \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_ws(mpl_ctx* h) {
+    for (auto& b : h->bufs) cudaFree(b.p);
+    h->bufs.clear();
+    h->cap_p = 0;
+    h->cap_smax = 0;
+    h->cap_r16 = false;
+    h->tmap_p = -1;
+}
+
+template <typename T>
+cudaError_t alloc(mpl_ctx* h, T** out, size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    h->bufs.push_back({p, count * sizeof(T)});
+    *out = static_cast<T*>(p);
+    return cudaSuccess;
+}
+
+int default_smax(const mpl_ctx* h) { return std::min(std::min(h->n, h->m), 256); }
+
+mpl_status_t ensure_ws(mpl_ctx* h, int p) {
+    const int smax = h->smax > 0 ? h->smax : default_smax(h);
+    const bool need_r16 = h->precision == 1;
+    if (p <= h->cap_p && smax == h->cap_smax && (!need_r16 || h->cap_r16)) return MPL_OK;
+    free_ws(h);
+    const int P = std::max(p, 1);
+    const int n = h->n, m = h->m;
+    const int mw = (m + 31) / 32;
+    Dev& d = h->dv;
+    d = Dev{};
+    const size_t pn = (size_t)P * n, ps = (size_t)P * smax, pss = (size_t)P * smax * smax;
+    CK(alloc(h, &d.R32, pn));
+    CK(alloc(h, &d.R64, pn));
+    if (need_r16) {
+        CK(alloc(h, &d.R16, pn + 64));
+        CK(alloc(h, &d.R16c, pn + 64 * (size_t)n));
+    }
+    CK(alloc(h, &d.Cs, (size_t)P * m));
+    CK(alloc(h, &d.mask, (size_t)P * mw));
+    CK(alloc(h, &d.S, ps));
+    CK(alloc(h, &d.xS, ps));
+    CK(alloc(h, &d.xS64, ps));
+    CK(alloc(h, &d.G, pss));
+    CK(alloc(h, &d.h, ps));
+    CK(alloc(h, &d.ritz, ps));
+    if (smax > FIN_SMEM_P) CK(alloc(h, &d.chol, pss));
+    int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
+                    &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin,
+                    &d.list_apg};
+    for (int** q : ints) CK(alloc(h, q, (size_t)P));
+    CK(alloc(h, &d.rnorm, (size_t)P));
+    CK(alloc(h, &d.eps, (size_t)P));
+    double** dbl[] = {&d.obj, &d.kkt_in, &d.kkt_out, &d.ginf, &d.rr, &d.rb};
+    for (double** q : dbl) CK(alloc(h, q, (size_t)P));
+    CK(alloc(h, &d.cnt, 1));
+    CK(cudaMemset(d.xS, 0, ps * sizeof(float)));
+    CK(cudaMemset(d.G, 0, pss * sizeof(float)));
+    d.n = n;
+    d.m = m;
+    d.smax = smax;
+    d.mw = mw;
+    h->cap_p = P;
+    h->cap_smax = smax;
+    h->cap_r16 = need_r16;
+    return MPL_OK;
+}
+
+cudaError_t ensure_staging(float** buf, size_t* cap, size_t bytes) {
+    if (bytes <= *cap) return cudaSuccess;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), bytes);
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
+}
+
+// Rounding-error constants of the bounds used by the selection (unit roundoff u = 2^-24).
+void set_bounds(mpl_ctx* h, Dev& d) {
+    const double u = std::ldexp(1.0, -24);
+    const double nu = (double)h->n * u;
+    const double gam = nu / (1.0 - nu);
+    const double c32 = 2.0 * (gam + u);  // sequential FP32 dot vs exact, incl. rounding of r
+    d.bound_c32 = (float)(c32 * 1.01);
+    if (h->precision == 1) {
+        // BF16 operands (relative 2^-8 each) with an FP32 accumulator assumed to
+        // keep at least 22 bits per addition; plus the FP32 terms above.
+        const double cb = 1.25 * (std::ldexp(1.0, -7) + std::ldexp(1.0, -16) + (double)h->n * std::ldexp(1.0, -22));
+        d.bound_c = (float)(cb + c32);
+    } else {
+        d.bound_c = (float)(c32 * 1.01);
+    }
+}
+
+struct PhaseTimer {
+    mpl_ctx* h;
+    cudaStream_t s;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    size_t used = 0;
+    cudaEvent_t get() {
+        if (used == h->evpool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->evpool.push_back(e);
+        }
+        return h->evpool[used++];
+    }
+    cudaEvent_t begin() {
+        if (!h->profile) return nullptr;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        return e;
+    }
+    void end(int phase, cudaEvent_t b) {
+        if (!h->profile || !b) return;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        marks.push_back({phase, {b, e}});
+    }
+    void collect() {
+        for (int k = 0; k < 7; ++k) h->phase_ms[k] = 0.0;
+        for (auto& mk : marks) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, mk.second.first, mk.second.second);
+            h->phase_ms[mk.first] += ms;
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* mpl_status_string(int status) {
+    switch (status) {
+        case MPL_OK: return "ok";
+        case MPL_ERR_ARG: return "invalid argument";
+        case MPL_ERR_CUDA: return "CUDA error";
+        case MPL_ERR_OOM: return "out of device memory";
+        case MPL_ERR_TIMEOUT: return "device wait timed out";
+        case MPL_ERR_NOT_CONVERGED: return "some signal not certified";
+        case MPL_ERR_UNSUPPORTED: return "unsupported option or size";
+        default: return "unknown status";
+    }
+}
+
+mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
+    if (!out) return MPL_ERR_ARG;
+    *out = nullptr;
+    if (!A || n < 1 || n > 65536 || m < 1 || m > (1 << 26)) return MPL_ERR_ARG;
+    mpl_ctx* h = new (std::nothrow) mpl_ctx();
+    if (!h) return MPL_ERR_OOM;
+    h->n = n;
+    h->m = m;
+    auto fail = [&](mpl_status_t st) {
+        mpl_destroy(h);
+        return st;
+    };
+    if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(MPL_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess)
+        return fail(MPL_ERR_CUDA);
+    const size_t bytes = (size_t)n * m * sizeof(float);
+    if (cudaMalloc(&h->A32, bytes) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMalloc(&h->colnorm, (size_t)m * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMalloc(&h->scal, 16 * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMallocHost(&h->cnt_h, sizeof(Counters)) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMemcpy(h->A32, A, bytes, cudaMemcpyDefault) != cudaSuccess) return fail(MPL_ERR_CUDA);
+    int64_t nl = 0;
+    if (launch_colnorm(h->A32, n, m, h->colnorm, nullptr, 0, &nl) != cudaSuccess) return fail(MPL_ERR_CUDA);
+    if (launch_max_reduce(h->colnorm, m, h->scal, 0, &nl) != cudaSuccess) return fail(MPL_ERR_CUDA);
+    if (cudaMemcpy(&h->colmax, h->scal, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(MPL_ERR_CUDA);
+    *out = h;
+    return MPL_OK;
+}
+
+void mpl_destroy(mpl_handle_t h) {
+    if (!h) return;
+    free_ws(h);
+    cudaFree(h->A32);
+    cudaFree(h->A16);
+    cudaFree(h->colnorm);
+    cudaFree(h->scal);
+    cudaFree(h->Bst);
+    cudaFree(h->lamst);
+    cudaFree(h->Xst);
+    if (h->cnt_h) cudaFreeHost(h->cnt_h);
+    for (auto e : h->evpool) cudaEventDestroy(e);
+    delete h;
+}
+
+mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
+    if (!h || !std::isfinite(v)) return MPL_ERR_ARG;
+    switch (key) {
+        case MPL_OPT_RHO:
+            if (v < 1 || v > 4096) return MPL_ERR_ARG;
+            h->rho = (int)v;
+            return MPL_OK;
+        case MPL_OPT_PRECISION:
+            if (v != 0 && v != 1) return MPL_ERR_ARG;
+            if (v == 1 && (h->n % 8) != 0) return MPL_ERR_UNSUPPORTED;  // 16-byte TMA rows
+            h->precision = (int)v;
+            return MPL_OK;
+        case MPL_OPT_MAX_OUTER:
+            if (v < 1 || v > 100000) return MPL_ERR_ARG;
+            h->max_outer = (int)v;
+            return MPL_OK;
+        case MPL_OPT_SMAX:
+            if (v < 1 || v > 1024 || v > h->m) return MPL_ERR_ARG;
+            h->smax = (int)v;
+            return MPL_OK;
+        case MPL_OPT_EPS_IN:
+            if (!(v > 0 && v < 1)) return MPL_ERR_ARG;
+            h->eps_in = v;
+            return MPL_OK;
+        case MPL_OPT_INNER_MAX:
+            if (v < 1 || v > 1000000) return MPL_ERR_ARG;
+            h->inner_max = (int)v;
+            return MPL_OK;
+        case MPL_OPT_WARM_START:
+            if (v != 0) return MPL_ERR_UNSUPPORTED;
+            h->warm = 0;
+            return MPL_OK;
+        case MPL_OPT_SYNC_EVERY:
+            if (v < 1 || v > 64) return MPL_ERR_ARG;
+            h->sync_every = (int)v;
+            return MPL_OK;
+        case OPT_PROFILE:
+            h->profile = v != 0;
+            return MPL_OK;
+        default:
+            return MPL_ERR_ARG;
+    }
+}
+
+mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
+    if (!h || !v) return MPL_ERR_ARG;
+    switch (key) {
+        case MPL_OPT_RHO: *v = h->rho; return MPL_OK;
+        case MPL_OPT_PRECISION: *v = h->precision; return MPL_OK;
+        case MPL_OPT_MAX_OUTER: *v = h->max_outer; return MPL_OK;
+        case MPL_OPT_SMAX: *v = h->smax > 0 ? h->smax : default_smax(h); return MPL_OK;
+        case MPL_OPT_EPS_IN: *v = h->eps_in; return MPL_OK;
+        case MPL_OPT_INNER_MAX: *v = h->inner_max; return MPL_OK;
+        case MPL_OPT_WARM_START: *v = h->warm; return MPL_OK;
+        case MPL_OPT_SYNC_EVERY: *v = h->sync_every; return MPL_OK;
+        case OPT_PROFILE: *v = h->profile; return MPL_OK;
+        default: return MPL_ERR_ARG;
+    }
+}
+
+mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lambda, float* X, double tol,
+                        void* stream) {
+    if (!h || p < 0 || !(tol > 0.0) || !(tol < 1.0)) return MPL_ERR_ARG;
+    if (p > 0 && (!B || !lambda || !X)) return MPL_ERR_ARG;
+    h->launches = 0;
+    for (double& v : h->phase_ms) v = 0.0;
+    h->last_p = p;
+    h->stats.assign((size_t)p, mpl_signal_stats_t{});
+    if (p == 0) return MPL_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->dev));
+    mpl_status_t ws = ensure_ws(h, p);
+    if (ws != MPL_OK) return ws;
+    const int n = h->n, m = h->m;
+    int64_t nl = 0;
+    if (h->precision == 1 && !h->A16) {
+        CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
+        CK(launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, &nl));
+    }
+    // arguments: stage host-resident buffers through device memory
+    const float* Bd = B;
+    const float* lamd = lambda;
+    float* Xd = X;
+    const bool X_host = !is_device_ptr(X);
+    if (!is_device_ptr(B)) {
+        CK(ensure_staging(&h->Bst, &h->Bst_b, (size_t)n * p * sizeof(float)));
+        CK(cudaMemcpyAsync(h->Bst, B, (size_t)n * p * sizeof(float), cudaMemcpyHostToDevice, st));
+        Bd = h->Bst;
+    }
+    if (!is_device_ptr(lambda)) {
+        CK(ensure_staging(&h->lamst, &h->lamst_b, (size_t)p * sizeof(float)));
+        CK(cudaMemcpyAsync(h->lamst, lambda, (size_t)p * sizeof(float), cudaMemcpyHostToDevice, st));
+        lamd = h->lamst;
+    }
+    if (X_host) {
+        CK(ensure_staging(&h->Xst, &h->Xst_b, (size_t)m * p * sizeof(float)));
+        Xd = h->Xst;
+    }
+
+    Dev d = h->dv;
+    d.p = p;
+    d.rho = std::min(h->rho, m);
+    d.precision = h->precision;
+    d.inner_max = h->inner_max;
+    d.eps_in = (float)h->eps_in;
+    d.tol = tol;
+    d.colmax = h->colmax;
+    d.A32 = h->A32;
+    d.A16 = h->A16;
+    d.B = Bd;
+    d.lam = lamd;
+    set_bounds(h, d);
+    if (h->precision == 1 && h->tmap_p != h->cap_p) {
+        CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
+        h->tmap_p = h->cap_p;
+    }
+
+    PhaseTimer pt{h, st, {}, 0};
+    cudaEvent_t t_all = pt.begin();
+    CK(launch_init(d, st, &nl));
+    int act_ub = p;
+    double corr_cols = 0.0;  // signal columns processed by the correlation, summed over iterations
+    const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
+    for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
+        const int cur = t & 1;
+        const int no_grow = t >= h->max_outer;
+        corr_cols += act_ub;
+        cudaEvent_t e0 = pt.begin();
+        if (h->precision == 1) {
+            CK(launch_gather_r16(d, cur, act_ub, st, &nl));
+            CK(launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, st, &nl));
+        } else {
+            CK(launch_corr_f32(d, cur, act_ub, st, &nl));
+        }
+        pt.end(1, e0);
+        e0 = pt.begin();
+        CK(launch_select(d, cur, no_grow, act_ub, st, &nl));
+        CK(launch_compact(d, cur, st, &nl));
+        pt.end(2, e0);
+        e0 = pt.begin();
+        CK(launch_gram(d, act_ub, st, &nl));
+        pt.end(3, e0);
+        e0 = pt.begin();
+        CK(launch_finish(d, act_ub, st, &nl));
+        pt.end(4, e0);
+        e0 = pt.begin();
+        const int vcap = std::min(d.smax, (t + 1) * d.rho);
+        CK(launch_apg(d, act_ub, h->sms, vcap, st, &nl));
+        pt.end(5, e0);
+        e0 = pt.begin();
+        CK(launch_residual(d, act_ub, st, &nl));
+        pt.end(6, e0);
+        CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
+        act_ub = h->cnt_h->act_n[cur ^ 1];
+    }
+    CK(cudaMemsetAsync(Xd, 0, (size_t)m * p * sizeof(float), st));
+    CK(launch_scatter(d, Xd, nullptr, st, &nl));
+    pt.end(0, t_all);
+    if (X_host) CK(cudaMemcpyAsync(X, Xd, (size_t)m * p * sizeof(float), cudaMemcpyDeviceToHost, st));
+
+    // per-signal statistics
+    std::vector<int> iv(10 * (size_t)p);
+    std::vector<double> dvv(6 * (size_t)p);
+    const int* isrc[] = {d.outer, d.inner, d.ssize, d.nnz, d.sstatus, d.finishes};
+    for (int k = 0; k < 6; ++k)
+        CK(cudaMemcpyAsync(iv.data() + (size_t)k * p, isrc[k], (size_t)p * sizeof(int), cudaMemcpyDeviceToHost, st));
+    const double* dsrc[] = {d.obj, d.kkt_in, d.kkt_out, d.ginf, d.rr, d.rb};
+    for (int k = 0; k < 6; ++k)
+        CK(cudaMemcpyAsync(dvv.data() + (size_t)k * p, dsrc[k], (size_t)p * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<float> lamh((size_t)p);
+    CK(cudaMemcpyAsync(lamh.data(), lamd, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    pt.collect();
+    h->phase_ms[7] = corr_cols;
+    h->launches = nl;
+    bool all_ok = true;
+    for (int i = 0; i < p; ++i) {
+        mpl_signal_stats_t& s = h->stats[(size_t)i];
+        s.outer_iters = iv[(size_t)0 * p + i];
+        s.inner_iters = iv[(size_t)1 * p + i];
+        s.active_size = iv[(size_t)2 * p + i];
+        s.nnz = iv[(size_t)3 * p + i];
+        s.status = iv[(size_t)4 * p + i];
+        s.finishes = iv[(size_t)5 * p + i];
+        const double obj = dvv[(size_t)0 * p + i];
+        s.objective = obj;
+        s.kkt = std::max(dvv[(size_t)1 * p + i], dvv[(size_t)2 * p + i]);
+        const double ginf = dvv[(size_t)3 * p + i], rr = dvv[(size_t)4 * p + i], rb = dvv[(size_t)5 * p + i];
+        const double lam = (double)lamh[(size_t)i];
+        const double sc = (ginf > lam && ginf > 0) ? lam / ginf : 1.0;
+        const double D = -0.5 * sc * sc * rr + sc * rb;
+        s.gap = obj > 0 ? (obj - D) / obj : 0.0;
+        if (s.status != MPL_SIG_CERTIFIED) all_ok = false;
+    }
+    return all_ok ? MPL_OK : MPL_ERR_NOT_CONVERGED;
+}
+
+mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void* stream) {
+    if (!h || p < 0 || (p > 0 && (!R || !C))) return MPL_ERR_ARG;
+    if (p == 0) return MPL_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->dev));
+    mpl_status_t ws = ensure_ws(h, p);
+    if (ws != MPL_OK) return ws;
+    const int n = h->n, m = h->m;
+    int64_t nl = 0;
+    if (h->precision == 1 && !h->A16) {
+        CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
+        CK(launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, &nl));
+    }
+    const float* Rd = R;
+    if (!is_device_ptr(R)) {
+        CK(ensure_staging(&h->Bst, &h->Bst_b, (size_t)n * p * sizeof(float)));
+        CK(cudaMemcpyAsync(h->Bst, R, (size_t)n * p * sizeof(float), cudaMemcpyHostToDevice, st));
+        Rd = h->Bst;
+    }
+    Dev d = h->dv;
+    d.p = p;
+    d.A32 = h->A32;
+    d.A16 = h->A16;
+    CK(launch_prep_correlate(d, Rd, st, &nl));
+    if (h->precision == 1) {
+        if (h->tmap_p != h->cap_p) {
+            CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
+            h->tmap_p = h->cap_p;
+        }
+        CK(launch_gather_r16(d, 0, p, st, &nl));
+        CK(launch_corr_bf16(d, 0, h->tmap, p, h->sms, st, &nl));
+    } else {
+        CK(launch_corr_f32(d, 0, p, st, &nl));
+    }
+    CK(cudaMemcpyAsync(C, d.Cs, (size_t)m * p * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->launches = nl;
+    if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
+    return MPL_OK;
+}
+
+mpl_status_t mpl_get_stats(mpl_handle_t h, int p, mpl_signal_stats_t* out) {
+    if (!h || !out || p != h->last_p) return MPL_ERR_ARG;
+    std::memcpy(out, h->stats.data(), sizeof(mpl_signal_stats_t) * (size_t)p);
+    return MPL_OK;
+}
+
+mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
+    if (!h || !X64 || p != h->last_p) return MPL_ERR_ARG;
+    if (p == 0) return MPL_OK;
+    Dev d = h->dv;
+    d.p = p;
+    const size_t bytes = (size_t)h->m * p * sizeof(double);
+    double* dst = X64;
+    double* tmp = nullptr;
+    if (!is_device_ptr(X64)) {
+        CK(cudaMalloc(&tmp, bytes));
+        dst = tmp;
+    }
+    int64_t nl = 0;
+    cudaError_t e = cudaMemsetAsync(dst, 0, bytes, 0);
+    if (e == cudaSuccess) e = launch_scatter(d, nullptr, dst, 0, &nl);
+    if (e == cudaSuccess && tmp) e = cudaMemcpy(X64, tmp, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
+    return from_cuda(e);
+}
+
+int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
+    if (!h || !ms_out) return 0;
+    const int k = std::min(cap, 8);
+    for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
+    return k;
+}
+
+int64_t mpl_get_launch_count(mpl_handle_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of the BMPL library.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpl.h"
+
+namespace mpl {
+
+// Per-signal phase decided by the selection kernel each outer iteration.
+enum SigState : int {
+    ST_GROW = 1,      // new atoms were appended: Gram growth, master problem, residual
+    ST_FINALIZE = 2,  // no violator left: FP64 exact finish and certificate
+    ST_DONE = 3,      // certified (or given up); leaves the active list
+};
+
+// Device-side counters and work-list lengths (one instance per solve).
+struct Counters {
+    int act_n[2];    // active-list lengths (double-buffered by outer-iteration parity)
+    int grow_n;      // signals that took new atoms
+    int fin_n;       // signals sent to the exact finish
+    int apg_n;       // signals in the master-problem list (grow + failed finishes)
+    int apg_head;    // work-queue head of the persistent master-problem kernel
+    int err;         // first device-side error code (0 = none)
+    int sel_fallback;// candidate-buffer overflows in the selection
+    __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
+};
+
+// Everything a kernel may touch, passed by value.
+struct Dev {
+    int n, m, p, smax, rho, mw;  // mw = words of the per-signal membership bitmap
+    int precision;               // 0 plain FP32, 1 mixed BF16
+    int inner_max;
+    float eps_in;
+    double tol;
+    float colmax;                // max_j ||a_j|| (rounded up)
+    float bound_c;               // |score_gemm - a_j^T r| <= bound_c * colmax * ||r||
+    float bound_c32;             // same for the fixed-order FP32 re-score
+    const float* A32;            // m x n atom-major
+    const __nv_bfloat16* A16;    // m x n atom-major (mixed)
+    const float* B;              // p x n signals (device)
+    const float* lam;            // p
+    float* R32;                  // p x n residual (FP32)
+    double* R64;                 // p x n residual of the exact finish (FP64)
+    __nv_bfloat16* R16;          // p x n residual (BF16, mixed)
+    __nv_bfloat16* R16c;         // act_n x n compacted BF16 residual for the GEMM
+    float* Cs;                   // act_n x m correlation scores (row k <-> act[k])
+    uint32_t* mask;              // p x mw membership bitmap of S_i
+    int* S;                      // p x smax active-set atom indices (append order)
+    float* xS;                   // p x smax FP32 master-problem iterate
+    double* xS64;                // p x smax FP64 finished solution
+    float* G;                    // p x smax x smax Gram blocks A_S^T A_S (ld = smax)
+    float* h;                    // p x smax A_S^T b
+    float* ritz;                 // p x smax power-iteration vector (warm start of L)
+    double* chol;                // p x smax x smax FP64 workspace (large supports)
+    int* state;                  // p SigState
+    int* ssize;                  // p |S_i|
+    int* snew;                   // p atoms appended this iteration
+    int* finalized;              // p 1 when R holds the residual of the exact finish
+    int* outer;                  // p outer iterations
+    int* inner;                  // p PG iterations
+    int* finishes;               // p exact-finish attempts
+    int* fails;                  // p consecutive failed finishes
+    int* sstatus;                // p mpl_signal_status_t
+    int* nnz;                    // p
+    float* rnorm;                // p ||r|| upper bound
+    float* eps;                  // p current eq. (inner) tolerance
+    double* obj;                 // p FP64 objective
+    double* kkt_in;              // p KKT violation / lambda on S (from the finish)
+    double* kkt_out;             // p certified bound off S / lambda (from selection)
+    double* ginf;                // p certified bound on ||A^T r||_inf
+    double* rr;                  // p ||r||^2
+    double* rb;                  // p r^T b
+    int* act[2];                 // active lists (signal ids), by outer-iteration parity
+    int* list_grow;              // signals with new atoms
+    int* list_fin;               // signals sent to the exact finish
+    int* list_apg;               // master-problem work list
+    Counters* cnt;
+    __device__ const int* act_of(int c) const { return act[c]; }
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns the CUDA error of its launch and adds its launches to *nl.
+cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+// BF16 tensor-core correlation (tcgen05 + TMA).  prepare() encodes the TMA
+// descriptors for A16 (m x n) and R16c (pmax x n) into tmap (256 bytes).
+cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16,
+                              const __nv_bfloat16* R16c, void* tmap);
+cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms,
+                             cudaStream_t s, int64_t* nl);
+cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
+cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_finish(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
+cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl);
+cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, int64_t* nl);
+cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl);
+cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
+                           cudaStream_t s, int64_t* nl);
+cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl);
+
+// Device-side error codes written to Counters::err.
+enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SHAPE = 3 };
+
+// Candidate capacity of the selection kernel (per signal, in shared memory).
+constexpr int SEL_KCAP = 4096;
+constexpr int SEL_THREADS = 512;
+// Master problem: Gram block kept in shared memory up to this size.
+constexpr int APG_SMEM_S = 200;
+constexpr int APG_THREADS = 256;
+// Exact finish: FP64 factor in shared memory up to this support size.
+constexpr int FIN_SMEM_P = 112;
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_MAX_PIVOTS = 16;
+constexpr int FIN_MAX_FAILS = 6;
+
+}  // namespace mpl

@@ -1,0 +1,399 @@
+// Worst-case analysis, second half (Algorithm 1, step 3): per signal, the rho
+// atoms outside the active set with the largest |a_j^T r| above lambda, and
+// the stopping test ||r^T A||_inf <= lambda of Sec. 2.3.
+//
+// One CTA per active signal.  The correlation scores come from a GEMM whose
+// error against the exact a_j^T r is bounded by delta = bound_c*colmax*||r||
+// (FP32: gamma_n; BF16 operands: 2^-7 plus the accumulation term).  The atoms
+// whose GEMM score can still matter,
+//     K = { j not in S : s_j >= max(s_(rho) - 2D, lambda(1+tol) - D) },
+// with s_(rho) the rho-th largest GEMM score and D the bound between a GEMM
+// score and the fixed-order FP32 re-score, are collected and re-scored with
+// one warp-level dot product of fixed summation order.  Selection ranks by the
+// re-score (ties to the lower atom index), so the plain FP32 and the mixed BF16
+// paths select identically by construction.  For a signal whose residual is
+// the FP64 residual of an exact finish, candidates whose re-score is within its
+// own bound of lambda(1+tol) are scored once more in FP64: this certifies the
+// off-support half of the KKT conditions (eq. 8).
+#include "mpl_internal.cuh"
+
+namespace mpl {
+
+namespace {
+
+__device__ __forceinline__ bool in_set(const uint32_t* msk, int j) {
+    return (msk[j >> 5] >> (j & 31)) & 1u;
+}
+
+// Fixed-order FP32 dot of atom a with residual r by one warp; every lane
+// returns the same value.  Lane l sums its float4 chunks k = 4l + 128q in
+// order of q, then a fixed butterfly combines the lanes.
+__device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const float* __restrict__ r,
+                                              int n, int lane) {
+    float acc = 0.f;
+    if ((n & 3) == 0) {
+        for (int k = lane * 4; k < n; k += 128) {
+            const float4 av = __ldg(reinterpret_cast<const float4*>(a + k));
+            const float4 rv = __ldg(reinterpret_cast<const float4*>(r + k));
+            acc = fmaf(av.x, rv.x, acc);
+            acc = fmaf(av.y, rv.y, acc);
+            acc = fmaf(av.z, rv.z, acc);
+            acc = fmaf(av.w, rv.w, acc);
+        }
+    } else {
+        for (int k = lane; k < n; k += 32) acc = fmaf(__ldg(a + k), __ldg(r + k), acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+__device__ __forceinline__ double warp_dot_f64(const float* __restrict__ a, const double* __restrict__ r,
+                                               int n, int lane) {
+    double acc = 0.0;
+    for (int k = lane; k < n; k += 32) acc = fma((double)__ldg(a + k), r[k], acc);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+struct SelSmem {
+    unsigned hist[2048];
+    unsigned long long key[SEL_KCAP];  // sort keys of the violators
+    int idx[SEL_KCAP];                 // candidate atoms
+    float sc[SEL_KCAP];                // their re-scores
+    int vflag[SEL_KCAP];               // 1 = violator
+    unsigned kc;                       // candidates collected
+    unsigned vc;                       // violators
+    unsigned bin, need;
+    unsigned outmax;                   // largest key outside K
+    float offmax;                      // largest certified bound inside K
+    int nonfinite;
+};
+
+// Key of atom j: the IEEE bits of |score| (monotone for non-negative floats);
+// members of S and non-finite scores key to 0 (non-finite is flagged).
+__device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk, int j, int* nf) {
+    if (in_set(msk, j)) return 0u;
+    const float v = fabsf(row[j]);
+    const unsigned u = __float_as_uint(v);
+    if (u >= 0x7f800000u) { *nf = 1; return 0u; }
+    return u;
+}
+
+// Key of the kth largest score (1-based) among the m keys, by 3 radix passes
+// over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.
+__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    unsigned prefix = 0, pmask = 0;
+    unsigned need = (unsigned)kth;
+    const int shifts[3] = {21, 10, 0};
+    const int widths[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; ++pass) {
+        const int nb = 1 << widths[pass];
+        const int sh_ = shifts[pass];
+        for (int b = tid; b < nb; b += nt) sh.hist[b] = 0;
+        __syncthreads();
+        int nf = 0;
+        for (int j = tid; j < m; j += nt) {
+            const unsigned kj = key_of(row, msk, j, &nf);
+            if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
+        }
+        if (nf) sh.nonfinite = 1;
+        __syncthreads();
+        if (tid < 32) {
+            const int lane = tid;
+            const int per = nb / 32;
+            unsigned own = 0;
+            for (int b = 0; b < per; ++b) own += sh.hist[lane * per + b];
+            // inclusive suffix sum over lanes (lane 31 holds the largest bins)
+            unsigned suf = own;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
+                if (lane + o < 32) suf += v;
+            }
+            const unsigned above = suf - own;  // counts in lanes > lane
+            const bool hit = (above < need) && (suf >= need);
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (bal == 0u) {
+                if (lane == 0) { sh.bin = 0; sh.need = need; }
+            } else {
+                const int hl = 31 - __clz(bal);  // the unique hitting lane
+                if (lane == hl) {
+                    unsigned cum = above;
+                    int b = per - 1;
+                    for (; b > 0; --b) {
+                        const unsigned c = sh.hist[lane * per + b];
+                        if (cum + c >= need) break;
+                        cum += c;
+                    }
+                    sh.bin = (unsigned)(lane * per + b);
+                    sh.need = need - cum;
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= sh.bin << sh_;
+        pmask |= (unsigned)(nb - 1) << sh_;
+        need = sh.need;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// Collect { j not in S : key >= tkey } into sh.idx (capacity SEL_KCAP) and the
+// largest key left outside.  Returns the number found (may exceed the capacity).
+__device__ unsigned collect(const float* row, const uint32_t* msk, int m, unsigned tkey, SelSmem& sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) { sh.kc = 0; sh.outmax = 0; }
+    __syncthreads();
+    int nf = 0;
+    unsigned omax = 0;
+    for (int j = tid; j < m; j += nt) {
+        const unsigned kj = key_of(row, msk, j, &nf);
+        if (kj >= tkey && kj > 0u) {
+            const unsigned pos = atomicAdd(&sh.kc, 1u);
+            if (pos < (unsigned)SEL_KCAP) sh.idx[pos] = j;
+        } else if (kj > omax) {
+            omax = kj;
+        }
+    }
+    if (omax) atomicMax(&sh.outmax, omax);
+    __syncthreads();
+    return sh.kc;
+}
+
+// Bitonic sort of sh.key[0..len) descending; len a power of two.
+__device__ void sort_desc(SelSmem& sh, int len) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 2; k <= len; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < len; t += nt) {
+                const int ixj = t ^ j;
+                if (ixj > t) {
+                    const unsigned long long a = sh.key[t], b = sh.key[ixj];
+                    const bool desc = ((t & k) == 0);
+                    if (desc ? (a < b) : (a > b)) { sh.key[t] = b; sh.key[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_grow) {
+    const int kblk = blockIdx.x;
+    if (kblk >= d.cnt->act_n[cur]) return;
+    const int i = d.act[cur][kblk];
+    if (d.state[i] == ST_DONE) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SelSmem& sh = *reinterpret_cast<SelSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int n = d.n, m = d.m;
+    float* row = d.Cs + (size_t)kblk * m;
+    const uint32_t* msk = d.mask + (size_t)i * d.mw;
+    const float* r32 = d.R32 + (size_t)i * n;
+    const double* r64 = d.R64 + (size_t)i * n;
+    const int fin = d.finalized[i];
+    const float lam = d.lam[i];
+    const double lam_hi = (double)lam * (1.0 + d.tol);  // certification threshold
+    const float lam_sel = (float)lam_hi;                // selection threshold
+    const float rn = d.rnorm[i];
+    const float delta32 = d.bound_c32 * d.colmax * rn;  // |rescore - a^T r|
+    float delta = d.bound_c * d.colmax * rn;            // |gemm score - a^T r|
+    if (tid == 0) sh.nonfinite = 0;
+    __syncthreads();
+
+    const int ss = d.ssize[i];
+    const int kth = min(d.rho, m);
+    bool exact_scores = false;  // row holds re-scores themselves (overflow fallback)
+    unsigned kc = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const float D = exact_scores ? 0.f : delta + delta32;
+        const unsigned kkey = radix_kth(row, msk, m, kth, sh);
+        const float s_rho = __uint_as_float(kkey);
+        float tau = fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
+        tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
+        const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
+        kc = collect(row, msk, m, tkey, sh);
+        if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
+        // Too many candidates in the band: re-score every atom outside S in place
+        // (this row is private to the signal) and select on the re-scores.
+        for (int j = warp; j < m; j += nwarps) {
+            float v = 0.f;
+            if (!in_set(msk, j)) v = warp_dot_f32(d.A32 + (size_t)j * n, r32, n, lane);
+            if (lane == 0) row[j] = v;
+        }
+        __syncthreads();
+        if (tid == 0) atomicAdd(&d.cnt->sel_fallback, 1);
+        exact_scores = true;
+        delta = delta32;
+    }
+    kc = min(kc, (unsigned)SEL_KCAP);
+
+    // Re-score the candidates (one warp each) and mark the violators.
+    if (tid == 0) { sh.vc = 0; sh.offmax = 0.f; }
+    __syncthreads();
+    float offmax = 0.f;
+    for (unsigned c = warp; c < kc; c += nwarps) {
+        const int j = sh.idx[c];
+        const float* aj = d.A32 + (size_t)j * n;
+        const float c32 = fabsf(warp_dot_f32(aj, r32, n, lane));
+        float score = c32;
+        int viol = c32 > lam_sel;
+        float certb = c32 + delta32;
+        if (fin && !viol && (double)c32 + (double)delta32 > lam_hi) {
+            const double c64 = fabs(warp_dot_f64(aj, r64, n, lane));
+            score = (float)c64;
+            viol = c64 > lam_hi;
+            certb = (float)(c64 * (1.0 + 1e-12));
+        }
+        if (lane == 0) {
+            sh.sc[c] = score;
+            sh.vflag[c] = viol;
+        }
+        offmax = fmaxf(offmax, certb);
+    }
+    if (lane == 0 && offmax > 0.f) atomicMax(reinterpret_cast<unsigned*>(&sh.offmax), __float_as_uint(offmax));
+    __syncthreads();
+    // Sort keys: (re-score bits, inverted index) so that larger scores come
+    // first and the lower index wins ties.
+    for (unsigned c = tid; c < kc; c += blockDim.x) {
+        if (sh.vflag[c]) {
+            const unsigned pos = atomicAdd(&sh.vc, 1u);
+            sh.key[pos] = ((unsigned long long)__float_as_uint(sh.sc[c]) << 32) |
+                          (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
+        }
+    }
+    __syncthreads();
+    const int vc = (int)sh.vc;
+    int len = 1;
+    while (len < vc) len <<= 1;
+    for (int t = vc + tid; t < len; t += blockDim.x) sh.key[t] = 0ull;
+    __syncthreads();
+    if (vc > 1) sort_desc(sh, len);
+
+    // State transition (one thread).
+    if (tid == 0) {
+        d.outer[i] += 1;
+        if (sh.nonfinite) {
+            d.sstatus[i] = MPL_SIG_NONFINITE;
+            d.state[i] = ST_DONE;
+        } else {
+            // certified bound on |a_j^T r| over atoms outside S
+            const float outside = (sh.outmax ? __uint_as_float(sh.outmax) : 0.f) + delta;
+            const double offb = fmax((double)outside, (double)sh.offmax);
+            int q = min(vc, d.rho);
+            if (q > d.smax - ss) q = d.smax - ss;
+            if (no_grow) q = 0;
+            if (q > 0) {
+                int* Si = d.S + (size_t)i * d.smax;
+                float* xi = d.xS + (size_t)i * d.smax;
+                uint32_t* mw = d.mask + (size_t)i * d.mw;
+                for (int a = 0; a < q; ++a) {
+                    const int j = (int)(0xffffffffu - (unsigned)(sh.key[a] & 0xffffffffull));
+                    Si[ss + a] = j;
+                    xi[ss + a] = 0.f;  // warm start: new entries at zero (Alg. 1, step 4)
+                    mw[j >> 5] |= 1u << (j & 31);
+                }
+                d.ssize[i] = ss + q;
+                d.snew[i] = q;
+                d.finalized[i] = 0;
+                d.state[i] = ST_GROW;
+            } else if (fin) {
+                d.kkt_out[i] = fmax(offb - (double)lam, 0.0) / (double)lam;
+                d.ginf[i] = fmax(d.ginf[i], offb);
+                d.state[i] = ST_DONE;
+                if (vc == 0) d.sstatus[i] = MPL_SIG_CERTIFIED;
+                else d.sstatus[i] = no_grow ? MPL_SIG_MAX_OUTER : MPL_SIG_CAPACITY;
+            } else {
+                d.snew[i] = 0;
+                d.state[i] = ST_FINALIZE;
+            }
+        }
+    }
+}
+
+// Stable compaction of the active list into the work lists of this outer
+// iteration (one CTA): grow, finish, master problem, and the next active list.
+__global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
+    const int nact = d.cnt->act_n[cur];
+    const int* act = d.act[cur];
+    int* nxt = d.act[cur ^ 1];
+    __shared__ int wsum[3][32];
+    __shared__ int base[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 3) base[tid] = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nact; c0 += 1024) {
+        const int k = c0 + tid;
+        int sig = -1, st = ST_DONE;
+        if (k < nact) { sig = act[k]; st = d.state[sig]; }
+        const int f[3] = {st == ST_GROW, st == ST_FINALIZE, st != ST_DONE};
+        int pre[3];
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const unsigned b = __ballot_sync(0xffffffffu, f[q]);
+            pre[q] = __popc(b & lt);
+            if (lane == 0) wsum[q][warp] = __popc(b);
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                int v = wsum[q][lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                wsum[q][lane] = v;  // inclusive
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int off = base[q] + (warp ? wsum[q][warp - 1] : 0) + pre[q];
+            if (f[q]) {
+                if (q == 0) { d.list_grow[off] = sig; d.list_apg[off] = sig; }
+                else if (q == 1) d.list_fin[off] = sig;
+                else nxt[off] = sig;
+            }
+        }
+        __syncthreads();
+        if (tid < 3) base[tid] += wsum[tid][31];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        d.cnt->grow_n = base[0];
+        d.cnt->apg_n = base[0];
+        d.cnt->fin_n = base[1];
+        d.cnt->act_n[cur ^ 1] = base[2];
+        d.cnt->apg_head = 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl) {
+    if (act_n_ub <= 0) return cudaSuccess;
+    const size_t sm = sizeof(SelSmem);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl) {
+    k_compact<<<1, 1024, 0, s>>>(d, cur);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+}  // namespace mpl

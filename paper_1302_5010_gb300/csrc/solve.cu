@@ -1,0 +1,549 @@
+// Master problem (eq. "primal_MPL") and residual (Algorithm 1, steps 4-8),
+// batched over signals, plus solve set-up and output.
+//
+//   k_init      x^0 = 0, xi^0 = b, I_0 = {} (Alg. 1, step 1)
+//   k_gram      new rows of the Gram block G_S = A_S^T A_S and h_S = A_S^T b
+//               for the atoms appended this iteration (the explicit copies of
+//               A_I that Sec. 2.4 recommends become Gram rows here)
+//   k_apg       accelerated proximal gradient on
+//                   min_u lambda*||u||_1 + 0.5 u^T G u - h^T u
+//               warm started from x_S (Alg. 1, step 4), stopped by eq. (inner)
+//               or s_max; persistent CTAs pull signals from a device queue
+//   k_residual  xi = b - A_S x_S (Alg. 1, step 8), FP32 (+ BF16 copy)
+//   k_scatter   dense X from the active sets
+#include "mpl_internal.cuh"
+
+namespace mpl {
+
+namespace {
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += red[w];  // same order in every thread
+    return t;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+__device__ __forceinline__ float softf(float v, float t) {
+    return v > t ? v - t : (v < -t ? v + t : 0.f);
+}
+
+// ------------------------------------------------------------------ init
+__global__ void __launch_bounds__(256) k_init(Dev d) {
+    const int i = blockIdx.x;
+    if (i >= d.p) return;
+    __shared__ double red[32];
+    const int n = d.n;
+    const float* b = d.B + (size_t)i * n;
+    float* r32 = d.R32 + (size_t)i * n;
+    double* r64 = d.R64 + (size_t)i * n;
+    double ss = 0.0;
+    int nf = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float v = b[k];
+        if (!isfinite(v)) nf = 1;
+        r32[k] = v;
+        r64[k] = (double)v;
+        if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(v);
+        ss += (double)v * (double)v;
+    }
+    uint32_t* mw = d.mask + (size_t)i * d.mw;
+    for (int w = threadIdx.x; w < d.mw; w += blockDim.x) mw[w] = 0u;
+    nf = __syncthreads_or(nf);
+    const double bb = block_sum_d(ss, red);
+    if (threadIdx.x == 0) {
+        const float lam = d.lam[i];
+        const bool bad = nf || !(lam > 0.f) || !isfinite(lam);
+        d.state[i] = bad ? ST_DONE : ST_GROW;
+        d.sstatus[i] = bad ? MPL_SIG_NONFINITE : MPL_SIG_MAX_OUTER;
+        d.ssize[i] = 0;
+        d.snew[i] = 0;
+        d.finalized[i] = 1;  // x = 0 and xi = b are exact
+        d.outer[i] = 0;
+        d.inner[i] = 0;
+        d.finishes[i] = 0;
+        d.fails[i] = 0;
+        d.nnz[i] = 0;
+        d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
+        d.eps[i] = d.eps_in;
+        d.obj[i] = 0.5 * bb;
+        d.rr[i] = bb;
+        d.rb[i] = bb;
+        d.kkt_in[i] = 0.0;
+        d.kkt_out[i] = 0.0;
+        d.ginf[i] = 0.0;
+        d.act[0][i] = i;
+        if (i == 0) {
+            d.cnt->act_n[0] = d.p;
+            d.cnt->act_n[1] = 0;
+            d.cnt->grow_n = d.cnt->fin_n = d.cnt->apg_n = d.cnt->apg_head = 0;
+            d.cnt->err = 0;
+            d.cnt->sel_fallback = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ gram
+// G[a][b] for a in [0, s), b in [s0, s) (mirrored), tile 64 (a) x 32 (b).
+constexpr int GBM = 64, GBN = 32, GBK = 32;
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_gram(Dev d) {
+    const int g = blockIdx.x;
+    if (g >= d.cnt->grow_n) return;
+    const int i = d.list_grow[g];
+    const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
+    const int a0 = blockIdx.y * GBM;
+    if (a0 >= s) return;
+    const int n = d.n, smax = d.smax;
+    const int* Si = d.S + (size_t)i * smax;
+    float* Gi = d.G + (size_t)i * smax * smax;
+    __shared__ __align__(16) float As[GBK][GBM + 4];
+    __shared__ __align__(16) float Bs[GBK][GBN + 4];
+    const int tid = threadIdx.x;
+    const int ty = tid >> 3, tx = tid & 7;
+    const int lr = tid >> 3, lk = (tid & 7) * 4;
+
+    for (int b0 = 0; b0 < q; b0 += GBN) {
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        const int ra0 = a0 + lr, ra1 = a0 + lr + 32;
+        const float* pa0 = (ra0 < s) ? d.A32 + (size_t)Si[ra0] * n : nullptr;
+        const float* pa1 = (ra1 < s) ? d.A32 + (size_t)Si[ra1] * n : nullptr;
+        const int rb = b0 + lr;
+        const float* pb = (rb < q) ? d.A32 + (size_t)Si[s0 + rb] * n : nullptr;
+        for (int k0 = 0; k0 < n; k0 += GBK) {
+            const int kk = k0 + lk;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, vb = v0;
+            if (VEC) {
+                if (kk < n) {
+                    if (pa0) v0 = __ldg(reinterpret_cast<const float4*>(pa0 + kk));
+                    if (pa1) v1 = __ldg(reinterpret_cast<const float4*>(pa1 + kk));
+                    if (pb) vb = __ldg(reinterpret_cast<const float4*>(pb + kk));
+                }
+            } else {
+                float t0[4] = {0, 0, 0, 0}, t1[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
+                for (int e = 0; e < 4; ++e) {
+                    if (kk + e < n) {
+                        if (pa0) t0[e] = pa0[kk + e];
+                        if (pa1) t1[e] = pa1[kk + e];
+                        if (pb) tb[e] = pb[kk + e];
+                    }
+                }
+                v0 = make_float4(t0[0], t0[1], t0[2], t0[3]);
+                v1 = make_float4(t1[0], t1[1], t1[2], t1[3]);
+                vb = make_float4(tb[0], tb[1], tb[2], tb[3]);
+            }
+            As[lk + 0][lr] = v0.x; As[lk + 1][lr] = v0.y; As[lk + 2][lr] = v0.z; As[lk + 3][lr] = v0.w;
+            As[lk + 0][lr + 32] = v1.x; As[lk + 1][lr + 32] = v1.y;
+            As[lk + 2][lr + 32] = v1.z; As[lk + 3][lr + 32] = v1.w;
+            Bs[lk + 0][lr] = vb.x; Bs[lk + 1][lr] = vb.y; Bs[lk + 2][lr] = vb.z; Bs[lk + 3][lr] = vb.w;
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < GBK; ++k) {
+                const float x0 = As[k][ty * 2], x1 = As[k][ty * 2 + 1];
+                const float4 y = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+                acc[0][0] = fmaf(x0, y.x, acc[0][0]); acc[0][1] = fmaf(x0, y.y, acc[0][1]);
+                acc[0][2] = fmaf(x0, y.z, acc[0][2]); acc[0][3] = fmaf(x0, y.w, acc[0][3]);
+                acc[1][0] = fmaf(x1, y.x, acc[1][0]); acc[1][1] = fmaf(x1, y.y, acc[1][1]);
+                acc[1][2] = fmaf(x1, y.z, acc[1][2]); acc[1][3] = fmaf(x1, y.w, acc[1][3]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int a = a0 + ty * 2 + u;
+            if (a >= s) continue;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int bb = b0 + tx * 4 + v;
+                if (bb >= q) continue;
+                const int col = s0 + bb;
+                Gi[(size_t)a * smax + col] = acc[u][v];
+                Gi[(size_t)col * smax + a] = acc[u][v];
+            }
+        }
+    }
+    // h for the new atoms (fixed-order warp dots), once per signal
+    if (blockIdx.y == 0) {
+        const int lane = tid & 31, warp = tid >> 5;
+        const float* b = d.B + (size_t)i * n;
+        for (int bb = warp; bb < q; bb += (blockDim.x >> 5)) {
+            const float* aj = d.A32 + (size_t)Si[s0 + bb] * n;
+            float acc = 0.f;
+            for (int k = lane; k < n; k += 32) acc = fmaf(aj[k], b[k], acc);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) d.h[(size_t)i * smax + s0 + bb] = acc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ APG
+// Gram block in shared memory when s <= gcap (<= APG_SMEM_S), else read from
+// global memory (L2).  Dynamic shared memory: [G gcap^2 | 6 vectors of vcap].
+__device__ __forceinline__ void gram_mv(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                        float* __restrict__ y) {
+    // y = G x, one row per thread; G symmetric so column r is read with unit
+    // stride across threads (conflict-free in shared memory, coalesced in global)
+    for (int r = threadIdx.x; r < s; r += blockDim.x) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = 0;
+        for (; c + 3 < s; c += 4) {
+            a0 = fmaf(G[(size_t)(c + 0) * ld + r], x[c + 0], a0);
+            a1 = fmaf(G[(size_t)(c + 1) * ld + r], x[c + 1], a1);
+            a2 = fmaf(G[(size_t)(c + 2) * ld + r], x[c + 2], a2);
+            a3 = fmaf(G[(size_t)(c + 3) * ld + r], x[c + 3], a3);
+        }
+        for (; c < s; ++c) a0 = fmaf(G[(size_t)c * ld + r], x[c], a0);
+        y[r] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+struct ApgVec {
+    float *u, *up, *Gu, *Gup, *h, *v;
+    float red[32];
+    int item;
+};
+
+__global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) {
+    extern __shared__ __align__(16) float gsm[];
+    __shared__ ApgVec sh;
+    const int tid = threadIdx.x;
+    const int smax = d.smax;
+    if (tid == 0) {
+        float* base = gsm + (size_t)gcap * gcap;
+        sh.u = base; sh.up = base + vcap; sh.Gu = base + 2 * vcap;
+        sh.Gup = base + 3 * vcap; sh.h = base + 4 * vcap; sh.v = base + 5 * vcap;
+    }
+    for (;;) {
+        if (tid == 0) sh.item = atomicAdd(&d.cnt->apg_head, 1);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= d.cnt->apg_n) break;
+        const int i = d.list_apg[it];
+        const int s = d.ssize[i];
+        const float lam = d.lam[i];
+        const float eps = d.eps[i];
+        const float* Gg = d.G + (size_t)i * smax * smax;
+        if (s > vcap) {  // cannot happen with a correct bound; refuse rather than overrun
+            if (tid == 0) atomicCAS(&d.cnt->err, 0, (int)DERR_SHAPE);
+            __syncthreads();
+            continue;
+        }
+        const bool insm = s <= gcap;
+        const float* G = insm ? gsm : Gg;
+        const int ld = insm ? s : smax;
+        if (insm) {
+            for (int e = tid; e < s * s; e += blockDim.x) {
+                const int r = e / s, c = e - r * s;
+                gsm[e] = Gg[(size_t)r * smax + c];
+            }
+        }
+        float* xi = d.xS + (size_t)i * smax;
+        float* ritz = d.ritz + (size_t)i * smax;
+        const int prev = s - d.snew[i];  // ritz vector valid for the first `prev` entries
+        for (int r = tid; r < s; r += blockDim.x) {
+            sh.u[r] = xi[r];
+            sh.h[r] = d.h[(size_t)i * smax + r];
+            sh.v[r] = (r < prev && d.outer[i] > 1) ? ritz[r] : 1.f;
+        }
+        __syncthreads();
+        // Step size: power iteration for lambda_max(G) (warm started), L = 1.05 theta.
+        float theta = 1.f;
+        const int npow = (prev > 0 && d.outer[i] > 1) ? 6 : 14;
+        for (int pi = 0; pi < npow; ++pi) {
+            gram_mv(G, ld, s, sh.v, sh.Gu);
+            __syncthreads();
+            float vv = 0.f, vg = 0.f;
+            for (int r = tid; r < s; r += blockDim.x) { vv += sh.v[r] * sh.v[r]; vg += sh.v[r] * sh.Gu[r]; }
+            const float tv = block_sum(vv, sh.red);
+            const float tg = block_sum(vg, sh.red);
+            float gg = 0.f;
+            for (int r = tid; r < s; r += blockDim.x) gg += sh.Gu[r] * sh.Gu[r];
+            const float tgg = block_sum(gg, sh.red);
+            theta = tv > 0.f ? tg / tv : 1.f;
+            const float inv = tgg > 0.f ? rsqrtf(tgg) : 0.f;
+            for (int r = tid; r < s; r += blockDim.x) sh.v[r] = sh.Gu[r] * inv;
+            __syncthreads();
+        }
+        for (int r = tid; r < s; r += blockDim.x) ritz[r] = sh.v[r];
+        float L = fmaxf(1.05f * theta, 1e-30f);
+
+        // F(u) and G u at the warm start
+        gram_mv(G, ld, s, sh.u, sh.Gu);
+        __syncthreads();
+        float part = 0.f;
+        for (int r = tid; r < s; r += blockDim.x) {
+            sh.up[r] = sh.u[r];
+            sh.Gup[r] = sh.Gu[r];
+            part += lam * fabsf(sh.u[r]) + sh.u[r] * (0.5f * sh.Gu[r] - sh.h[r]);
+        }
+        float F = block_sum(part, sh.red);
+        const float F0 = F;
+        float t = 1.f, beta = 0.f;
+        int iters = 0, restarts_in_row = 0;
+        for (int k = 0; k < d.inner_max; ++k) {
+            // extrapolate, prox-gradient step (the one matvec is G u of the new point)
+            const float invL = 1.f / L, thr = lam * invL;
+            for (int r = tid; r < s; r += blockDim.x) {
+                const float y = sh.u[r] + beta * (sh.u[r] - sh.up[r]);
+                const float gy = sh.Gu[r] + beta * (sh.Gu[r] - sh.Gup[r]) - sh.h[r];
+                const float z = softf(y - gy * invL, thr);
+                sh.up[r] = sh.u[r];
+                sh.Gup[r] = sh.Gu[r];
+                sh.u[r] = z;
+            }
+            __syncthreads();
+            gram_mv(G, ld, s, sh.u, sh.Gu);
+            __syncthreads();
+            part = 0.f;
+            for (int r = tid; r < s; r += blockDim.x)
+                part += lam * fabsf(sh.u[r]) + sh.u[r] * (0.5f * sh.Gu[r] - sh.h[r]);
+            const float Fn = block_sum(part, sh.red);
+            ++iters;
+            if (Fn > F) {
+                // function-value restart: back to the previous point, momentum off;
+                // a plain step that still increases F means L was too small
+                const bool genuine = (Fn - F) > 1e-4f * fmaxf(F0 - F, 1e-30f);
+                if (beta == 0.f && genuine) L *= 2.f;
+                for (int r = tid; r < s; r += blockDim.x) { sh.u[r] = sh.up[r]; sh.Gu[r] = sh.Gup[r]; }
+                __syncthreads();
+                beta = 0.f;
+                t = 1.f;
+                if (++restarts_in_row >= 3) break;  // stalled at FP32 resolution
+                continue;
+            }
+            restarts_in_row = 0;
+            const float dec = F - Fn, tot = F0 - Fn;
+            F = Fn;
+            // relative-decrease stop of eq. (inner)
+            if (tot <= 0.f ? dec <= 0.f : dec <= eps * tot) break;
+            const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+            beta = (t - 1.f) / tn;
+            t = tn;
+        }
+        for (int r = tid; r < s; r += blockDim.x) xi[r] = sh.u[r];
+        if (tid == 0) d.inner[i] += iters;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ residual
+__global__ void __launch_bounds__(256) k_residual(Dev d) {
+    const int g = blockIdx.x;
+    if (g >= d.cnt->apg_n) return;
+    const int i = d.list_apg[g];
+    const int n = d.n, smax = d.smax, s = d.ssize[i];
+    __shared__ int nzi[1024];
+    __shared__ float nzv[1024];
+    __shared__ int cntnz;
+    __shared__ float red[32];
+    if (threadIdx.x == 0) cntnz = 0;
+    __syncthreads();
+    const float* xi = d.xS + (size_t)i * smax;
+    const int* Si = d.S + (size_t)i * smax;
+    // nonzeros of x_S in append order (ordered compaction by one warp)
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int a0 = 0; a0 < s; a0 += 32) {
+            const int a = a0 + threadIdx.x;
+            const float v = a < s ? xi[a] : 0.f;
+            const unsigned b = __ballot_sync(0xffffffffu, v != 0.f);
+            const int off = base + __popc(b & ((1u << threadIdx.x) - 1u));
+            if (v != 0.f) { nzi[off] = Si[a]; nzv[off] = v; }
+            base += __popc(b);
+        }
+        if (threadIdx.x == 0) cntnz = base;
+    }
+    __syncthreads();
+    const int nz = cntnz;
+    const float* b = d.B + (size_t)i * n;
+    float* r32 = d.R32 + (size_t)i * n;
+    float ss = 0.f;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        float acc = b[k];
+        for (int a = 0; a < nz; ++a) acc = fmaf(-nzv[a], __ldg(d.A32 + (size_t)nzi[a] * n + k), acc);
+        r32[k] = acc;
+        if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(acc);
+        ss = fmaf(acc, acc, ss);
+    }
+    const float t = block_sum(ss, red);
+    if (threadIdx.x == 0) {
+        d.rnorm[i] = sqrtf(t) * (1.f + 1e-5f);
+        d.nnz[i] = nz;
+    }
+}
+
+// ------------------------------------------------------------------ output
+__global__ void k_scatter(Dev d, float* X, double* X64) {
+    const int i = blockIdx.x;
+    if (i >= d.p) return;
+    const int s = d.ssize[i];
+    const bool fin = d.finalized[i] != 0;
+    for (int a = threadIdx.x; a < s; a += blockDim.x) {
+        const int j = d.S[(size_t)i * d.smax + a];
+        const double v = fin ? d.xS64[(size_t)i * d.smax + a] : (double)d.xS[(size_t)i * d.smax + a];
+        if (X) X[(size_t)i * d.m + j] = (float)v;
+        if (X64) X64[(size_t)i * d.m + j] = v;
+    }
+}
+
+// ------------------------------------------------------------------ dictionary prep
+__global__ void k_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16) {
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const float* a = A32 + (size_t)j * n;
+    double ss = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const float v = a[k];
+        ss += (double)v * (double)v;
+        if (A16) A16[(size_t)j * n + k] = __float2bfloat16_rn(v);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) colnorm[j] = __double2float_ru(sqrt(ss));
+}
+
+__global__ void k_max_reduce(const float* v, int len, float* out) {
+    float mx = 0.f;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) mx = fmaxf(mx, v[t]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        *out = t;
+    }
+}
+
+__global__ void k_gather_r16(Dev d, int cur) {
+    const int k = blockIdx.x;
+    if (k >= d.cnt->act_n[cur]) return;
+    const int i = d.act[cur][k];
+    const int n = d.n;
+    const uint4* src = reinterpret_cast<const uint4*>(d.R16 + (size_t)i * n);
+    uint4* dst = reinterpret_cast<uint4*>(d.R16c + (size_t)k * n);
+    for (int t = threadIdx.x; t < n / 8; t += blockDim.x) dst[t] = src[t];
+}
+
+// Load caller residuals for a stand-alone correlation: R32 (and R16), identity active list.
+__global__ void k_prep_correlate(Dev d, const float* R) {
+    const int i = blockIdx.x;
+    if (i >= d.p) return;
+    const int n = d.n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float v = R[(size_t)i * n + k];
+        d.R32[(size_t)i * n + k] = v;
+        if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(v);
+    }
+    if (threadIdx.x == 0) {
+        d.act[0][i] = i;
+        if (i == 0) { d.cnt->act_n[0] = d.p; d.cnt->err = 0; }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, int64_t* nl) {
+    if (d.p <= 0) return cudaSuccess;
+    k_prep_correlate<<<d.p, 256, 0, s>>>(d, R);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl) {
+    if (d.p <= 0) return cudaSuccess;
+    k_init<<<d.p, 256, 0, s>>>(d);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    dim3 grid(ub, (d.smax + GBM - 1) / GBM);
+    if ((d.n & 3) == 0) k_gram<true><<<grid, 256, 0, s>>>(d);
+    else k_gram<false><<<grid, 256, 0, s>>>(d);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    vcap = ((vcap + 31) / 32) * 32;
+    if (vcap > d.smax) vcap = d.smax;
+    const int gcap = vcap < APG_SMEM_S ? vcap : APG_SMEM_S;
+    const size_t dyn = ((size_t)gcap * gcap + 6 * (size_t)vcap) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        const int mx = (int)(((size_t)APG_SMEM_S * APG_SMEM_S + 6 * 1024) * sizeof(float));
+        cudaError_t e = cudaFuncSetAttribute(k_apg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apg, APG_THREADS, dyn);
+    if (e != cudaSuccess) return e;
+    int grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > ub) grid = ub;
+    k_apg<<<grid, APG_THREADS, dyn, s>>>(d, vcap, gcap);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    k_residual<<<ub, 256, 0, s>>>(d);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl) {
+    if (d.p <= 0) return cudaSuccess;
+    k_scatter<<<d.p, 128, 0, s>>>(d, X, X64);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
+                           cudaStream_t s, int64_t* nl) {
+    const int per = 8;  // warps per block
+    k_colnorm<<<(m + per - 1) / per, per * 32, 0, s>>>(A32, n, m, colnorm, A16);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl) {
+    k_max_reduce<<<1, 1024, 0, s>>>(v, len, out);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
+    if (act_n_ub <= 0) return cudaSuccess;
+    k_gather_r16<<<act_n_ub, 128, 0, s>>>(d, cur);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+}  // namespace mpl

@@ -1,0 +1,70 @@
+"""The worst-case analysis product g = A^T r (Algorithm 1, step 3) from both
+correlation paths, against FP64 on the same data, within the rigorous error
+bounds that the selection's candidate band relies on:
+
+  FP32 SIMT path:   |c - a^T r| <= gamma_n * sum_k |a_k r_k|
+  BF16 tensor path: |c - a16^T r16| <= n 2^-22 * sum_k |a16_k r16_k|   (accumulation)
+                    |c - a^T r| <= (2^-7 + 2^-16 + n 2^-22) * ||a|| ||r||   (operands)
+"""
+import numpy as np
+import pytest
+
+from paper_1302_5010_gb300 import mpl
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(256, 1000, 1), (256, 1000, 37), (1000, 2050, 130), (1024, 8192, 256), (4096, 4096, 300)]
+
+
+def _bf16(x):
+    """Round float32 to bfloat16 (round to nearest even) and back."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _data(n, m, p, seed):
+    rng = np.random.default_rng(seed)
+    At = rng.standard_normal((m, n)).astype(np.float32)
+    At /= np.linalg.norm(At, axis=1, keepdims=True)
+    R = (rng.standard_normal((p, n)) * 0.3).astype(np.float32)
+    return At, R
+
+
+def _run(At, R, precision):
+    import torch
+    s = mpl.Solver(torch.from_numpy(At).cuda(), precision=precision)
+    C = torch.empty((R.shape[0], At.shape[0]), dtype=torch.float32, device="cuda")
+    s.correlate(torch.from_numpy(R).cuda(), C)
+    torch.cuda.synchronize()
+    s.close()
+    return C.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n,m,p", SHAPES)
+def test_fp32_path_within_gamma_n(n, m, p):
+    At, R = _data(n, m, p, n + m + p)
+    C = _run(At, R, 0)
+    A64, R64 = At.astype(np.float64), R.astype(np.float64)
+    exact = R64 @ A64.T
+    absdot = np.abs(R64) @ np.abs(A64).T
+    u = 2.0 ** -24
+    gam = n * u / (1 - n * u)
+    assert np.all(np.abs(C - exact) <= gam * absdot + 1e-30)
+
+
+@pytest.mark.parametrize("n,m,p", SHAPES)
+def test_bf16_path_within_bounds(n, m, p):
+    At, R = _data(n, m, p, 7 * n + m + p)
+    C = _run(At, R, 1)
+    A16, R16 = _bf16(At).astype(np.float64), _bf16(R).astype(np.float64)
+    exact16 = R16 @ A16.T
+    absdot16 = np.abs(R16) @ np.abs(A16).T
+    err16 = np.abs(C - exact16)
+    assert np.all(err16 <= n * 2.0 ** -22 * absdot16 + 1e-30), err16.max()
+    exact = R.astype(np.float64) @ At.astype(np.float64).T
+    bound = (2.0 ** -7 + 2.0 ** -16 + n * 2.0 ** -22) * np.outer(np.linalg.norm(R, axis=1),
+                                                                  np.linalg.norm(At, axis=1))
+    assert np.all(np.abs(C - exact) <= bound)
+    # and it is a real bf16 product, not a float32 one in disguise
+    assert np.abs(C - exact).max() > 1e-6 * np.abs(exact).max()

@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Small cases compare every signal; the full 1024 x 8192, p = 256 workload (the
+benchmark's configuration) compares a sample of signals one by one and checks
+the certificate of every signal in FP64."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import checkers as ck
+from paper_1302_5010_gb300 import mpl, synth
+from parity import check_against_oracle
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def solve_gpu(P, precision=0, tol=TOL, host=False, **opts):
+    torch = _torch()
+    solver = mpl.Solver(torch.from_numpy(P.At).cuda() if not host else P.At, rho=P.rho,
+                        precision=precision, **opts)
+    if host:
+        X = np.zeros((P.p, P.m), dtype=np.float32)
+        res = solver.solve(P.B, P.lam, X, tol)
+    else:
+        B = torch.from_numpy(P.B).cuda()
+        lam = torch.from_numpy(P.lam).cuda()
+        Xt = torch.empty((P.p, P.m), dtype=torch.float32, device="cuda")
+        res = solver.solve(B, lam, Xt, tol)
+        torch.cuda.synchronize()
+        X = Xt.cpu().numpy()
+    X64 = np.zeros((P.p, P.m), dtype=np.float64)
+    solver.solution_f64(X64)
+    solver.close()
+    return X, X64, res
+
+
+def oracle_solve(P, idx=None):
+    idx = np.arange(P.p) if idx is None else np.asarray(idx)
+    X, r = oracle.bmpl(P.At, P.B[idx], P.lam[idx], P.rho)
+    assert np.all(r["status"] == 0)
+    return X
+
+
+def assert_certified(res):
+    st = res.stats
+    assert np.all(st["status"] == mpl.MPL_SIG_CERTIFIED), st["status"]
+    assert np.all(st["kkt"] <= TOL), st["kkt"].max()
+    assert res.status == mpl.MPL_OK
+
+
+def test_c1_single_signal():
+    P = synth.make_config("c1")
+    X, X64, res = solve_gpu(P)
+    assert_certified(res)
+    Xo = oracle_solve(P)
+    check_against_oracle(P, X, Xo)
+    check_against_oracle(P, X64, Xo)
+    assert ck.kkt_violation(P.At, P.B[0], X64[0], float(P.lam[0])) <= 2 * TOL
+
+
+@pytest.mark.parametrize("n,m,p,rho", [(256, 1000, 37, 5), (250, 777, 9, 3), (512, 4096, 130, 12)])
+def test_ragged_shapes(n, m, p, rho):
+    """Several GEMM tiles with ragged tails in atoms, signals and (n % 4 != 0) length."""
+    P = synth.small_problem(n, m, p, 5, min(40, n // 6), rho=rho, seed=n + m + p, lam_frac=0.03)
+    X, X64, res = solve_gpu(P)
+    assert_certified(res)
+    check_against_oracle(P, X64, oracle_solve(P))
+
+
+def test_c2_subset_all_signals():
+    P = synth.make_config("c2", p=48)
+    X, X64, res = solve_gpu(P)
+    assert_certified(res)
+    Xo = oracle_solve(P)
+    check_against_oracle(P, X, Xo)
+    check_against_oracle(P, X64, Xo)
+
+
+def test_c2_full_sampled():
+    """Full batch, the configuration the benchmark times: a sample checked
+    against the oracle signal by signal; every signal's certificate re-checked
+    in FP64 by the oracle's independent certify()."""
+    P = synth.make_config("c2")
+    X, X64, res = solve_gpu(P)
+    assert_certified(res)
+    idx = np.random.default_rng(0).choice(P.p, size=12, replace=False)
+    check_against_oracle(P, X64[idx], oracle_solve(P, idx), idx)
+    for i in range(P.p):
+        c = oracle.certify(P.At, P.B[i], float(P.lam[i]), X64[i])
+        assert c["kkt"] <= 2 * TOL, (i, c)
+        assert abs(c["objective"] - res.stats["objective"][i]) <= 1e-9 * c["objective"]
+
+
+def test_lambda_above_max_and_zero_signal():
+    P = synth.small_problem(128, 600, 4, 5, 10, rho=4, seed=2)
+    lam = (np.abs(P.At.astype(np.float64) @ P.B.astype(np.float64).T).max(axis=0) * 1.001).astype(np.float32)
+    B = P.B.copy()
+    B[2] = 0.0
+    Q = synth.Problem("edge", P.At, B, lam, 4)
+    X, X64, res = solve_gpu(Q)
+    assert_certified(res)
+    assert np.all(X == 0)
+    assert np.all(res.stats["outer_iters"] == 1)
+
+
+def test_orthonormal_closed_form():
+    rng = np.random.default_rng(5)
+    Qm, _ = np.linalg.qr(rng.standard_normal((64, 64)))
+    At = Qm.T.astype(np.float32).copy()
+    B = rng.standard_normal((6, 64)).astype(np.float32)
+    lam = (0.2 * np.abs(At.astype(np.float64) @ B.T.astype(np.float64)).max(axis=0)).astype(np.float32)
+    P = synth.Problem("orth", At, B, lam, 8)
+    X, X64, res = solve_gpu(P)
+    assert_certified(res)
+    for i in range(P.p):
+        ref = ck.soft_threshold_orthonormal(At, B[i], float(lam[i]))
+        np.testing.assert_allclose(X64[i], ref, atol=1e-6 * np.abs(ref).max())
+
+
+def test_host_buffers_match_device_buffers():
+    P = synth.small_problem(256, 1024, 10, 5, 20, rho=5, seed=11)
+    Xd, X64d, _ = solve_gpu(P)
+    Xh, X64h, resh = solve_gpu(P, host=True)
+    assert_certified(resh)
+    np.testing.assert_array_equal(Xd, Xh)
+
+
+def test_deterministic_repeat():
+    P = synth.small_problem(256, 2048, 20, 10, 30, rho=6, seed=12)
+    X1, _, _ = solve_gpu(P)
+    X2, _, _ = solve_gpu(P)
+    np.testing.assert_array_equal(X1, X2)
+
+
+def test_empty_batch_and_bad_lambda():
+    torch = _torch()
+    P = synth.small_problem(64, 128, 3, 2, 4, rho=2, seed=3)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=2)
+    Xt = torch.zeros((0, P.m), device="cuda")
+    r = s.solve(torch.zeros((0, P.n), device="cuda"), torch.zeros(0, device="cuda"), Xt)
+    assert r.status == mpl.MPL_OK
+    lam = P.lam.copy()
+    lam[1] = -1.0
+    Xt = torch.zeros((P.p, P.m), device="cuda")
+    r = s.solve(torch.from_numpy(P.B).cuda(), torch.from_numpy(lam).cuda(), Xt)
+    assert r.status == mpl.MPL_ERR_NOT_CONVERGED
+    assert r.stats["status"][1] == mpl.MPL_SIG_NONFINITE
+    assert r.stats["status"][0] == mpl.MPL_SIG_CERTIFIED
+    s.close()
