@@ -131,6 +131,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     d = Dev{};
     const size_t pn = (size_t)P * n, ps = (size_t)P * smax, pss = (size_t)P * smax * smax;
     CK(alloc(h, &d.R32, pn));
+    CK(alloc(h, &d.R32lo, pn));
     CK(alloc(h, &d.R64, pn));
     if (need_r16) {
         CK(alloc(h, &d.R16, pn + 64));
@@ -433,7 +434,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         CK(launch_gram(d, act_ub, st, &nl));
         pt.end(3, e0);
         e0 = pt.begin();
-        CK(launch_finish(d, act_ub, st, &nl));
+        CK(launch_finish(d, act_ub, std::min(d.smax, (t + 1) * d.rho), st, &nl));
         pt.end(4, e0);
         e0 = pt.begin();
         const int vcap = std::min(d.smax, (t + 1) * d.rho);

@@ -41,7 +41,8 @@ struct Dev {
     const __nv_bfloat16* A16;    // m x n atom-major (mixed)
     const float* B;              // p x n signals (device)
     const float* lam;            // p
-    float* R32;                  // p x n residual (FP32)
+    float* R32;                  // p x n residual (FP32; high part after an exact finish)
+    float* R32lo;                // p x n low part of the exact-finish residual
     double* R64;                 // p x n residual of the exact finish (FP64)
     __nv_bfloat16* R16;          // p x n residual (BF16, mixed)
     __nv_bfloat16* R16c;         // act_n x n compacted BF16 residual for the GEMM
@@ -93,7 +94,7 @@ cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t 
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
-cudaError_t launch_finish(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl);
@@ -113,7 +114,7 @@ constexpr int SEL_THREADS = 512;
 constexpr int APG_SMEM_S = 200;
 constexpr int APG_THREADS = 256;
 // Exact finish: FP64 factor in shared memory up to this support size.
-constexpr int FIN_SMEM_P = 112;
+constexpr int FIN_SMEM_P = 96;
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_MAX_PIVOTS = 16;
 constexpr int FIN_MAX_FAILS = 6;

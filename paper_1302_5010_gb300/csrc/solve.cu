@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         const float v = b[k];
         if (!isfinite(v)) nf = 1;
         r32[k] = v;
+        d.R32lo[(size_t)i * n + k] = 0.f;
         r64[k] = (double)v;
         if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(v);
         ss += (double)v * (double)v;
