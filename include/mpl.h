@@ -130,6 +130,36 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
  */
 mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void* stream);
 
+/*
+ * mpl_correlate_noalloc -- the same FP32 correlation as mpl_correlate with
+ * MPL_OPT_PRECISION = 0, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a library-usage entry point.
+ *
+ * Who it is for: programs whose device memory is owned up front by their own
+ * pool allocator (a framework's caching allocator, a serving runtime with a
+ * fixed budget).  A cudaMalloc issued behind their back can fail once the pool
+ * has reserved the memory, and it synchronises the device mid-pipeline.  This
+ * call needs no handle and allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.
+ *
+ *   A  n x m column-major FP32 dictionary, device memory.
+ *   R  n x p column-major FP32 vectors, device memory.
+ *   C  m x p column-major FP32 output, C[i*m + j] = a_j^T r_i, device memory.
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is
+ *           asynchronous and stream-ordered.
+ * Limits: 1 <= n <= 65536, m >= 1, 0 <= p <= MPL_NOALLOC_MAX_SIGNALS; a larger
+ * p returns MPL_ERR_UNSUPPORTED, host pointers return MPL_ERR_ARG.
+ * Scratch: a fixed MPL_NOALLOC_SCRATCH_BYTES device array inside the library,
+ * held by every GPU that loads it until the process exits.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every
+ * call rewrites the scratch it reads, and all calls share it, so calls whose
+ * GPU work overlaps (different streams, no ordering between them) race.
+ */
+#define MPL_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define MPL_NOALLOC_MAX_SIGNALS ((int)((MPL_NOALLOC_SCRATCH_BYTES - 256u) / 4u))
+mpl_status_t mpl_correlate_noalloc(const float* A, int n, int m, const float* R, int p, float* C, void* stream);
+
 /* Release the handle and all its device memory.  NULL-safe. */
 void mpl_destroy(mpl_handle_t h);
 

@@ -37,6 +37,10 @@ MPL_OPT_WARM_START = 6
 MPL_OPT_SYNC_EVERY = 7
 MPL_OPT_PROFILE = 8
 
+# limits of the allocation-free entry point (include/mpl.h)
+MPL_NOALLOC_SCRATCH_BYTES = 1 << 20
+MPL_NOALLOC_MAX_SIGNALS = (MPL_NOALLOC_SCRATCH_BYTES - 256) // 4
+
 # per-signal status (mpl_signal_status_t)
 MPL_SIG_CERTIFIED = 0
 MPL_SIG_MAX_OUTER = 1
@@ -46,7 +50,7 @@ MPL_SIG_NONFINITE = 4
 
 EXPORTED = ("mpl_create", "bmpl_solve", "mpl_correlate", "mpl_destroy", "mpl_set_option", "mpl_get_option",
             "mpl_get_stats", "mpl_get_solution_f64", "mpl_get_phase_times", "mpl_get_launch_count",
-            "mpl_status_string")
+            "mpl_status_string", "mpl_correlate_noalloc")
 
 
 class SignalStats(ctypes.Structure):
@@ -86,6 +90,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.bmpl_solve.restype = i32
     lib.mpl_correlate.argtypes = [vp, vp, i32, vp, vp]
     lib.mpl_correlate.restype = i32
+    lib.mpl_correlate_noalloc.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+    lib.mpl_correlate_noalloc.restype = i32
     lib.mpl_destroy.argtypes = [vp]
     lib.mpl_destroy.restype = None
     lib.mpl_set_option.argtypes = [vp, i32, f64]
@@ -179,6 +185,14 @@ def mpl_correlate(h, R, p: int, C, stream=None) -> None:
     rc = load().mpl_correlate(h, _ptr(R), int(p), _ptr(C), _stream_ptr(stream))
     if rc != MPL_OK:
         raise MplError(rc, "mpl_correlate")
+
+
+def mpl_correlate_noalloc(A, n: int, m: int, R, p: int, C, stream=None) -> int:
+    """Allocation-free FP32 correlation (no handle): C (p, m) = rows of A^T R,
+    all three device arrays.  Returns the status code (no exception), so that
+    callers can see MPL_ERR_UNSUPPORTED / MPL_ERR_ARG."""
+    return int(load().mpl_correlate_noalloc(_ptr(A), int(n), int(m), _ptr(R), int(p), _ptr(C),
+                                            _stream_ptr(stream)))
 
 
 def mpl_get_stats(h, p: int) -> dict:
