@@ -60,7 +60,7 @@ typedef enum {
     MPL_OPT_INNER_MAX = 5,  /* s_max, PG iterations per master problem.  default 400 */
     MPL_OPT_WARM_START = 6, /* 0: x^0 = 0 (Alg. 1, step 1);
                                2: proposal network seeds the active sets.  default 0 */
-    MPL_OPT_SYNC_EVERY = 7, /* host/device handshake period in outer iterations. default 1 */
+    MPL_OPT_SYNC_EVERY = 7, /* outer iterations launched per host/device handshake. default 2 */
     MPL_OPT_PROFILE = 8     /* 1: record per-phase device times (mpl_get_phase_times). default 0 */
 } mpl_option_t;
 
@@ -79,7 +79,7 @@ typedef struct {
     int32_t active_size;  /* |S| at exit */
     int32_t nnz;          /* nonzeros of x */
     int32_t status;       /* mpl_signal_status_t */
-    int32_t finishes;     /* FP64 exact-finish attempts */
+    int32_t finishes;     /* active-set steps of the exact finish (all attempts) */
     double objective;     /* lambda*||x||_1 + 0.5*||b - A x||^2, FP64 */
     double kkt;           /* certified upper bound on the max KKT violation / lambda */
     double gap;           /* relative duality gap with the scaled dual point of eq. 5 */

@@ -28,6 +28,19 @@
 
 namespace mpl {
 
+#ifdef MPL_FIN_TRACE
+// Per-signal phase cycle counters of the exact finish (diagnostic builds only):
+// [factor, solve, crossing, gram-zero-check, verify, exact-zero-check, steps, refinements]
+__device__ long long g_fin_trace[8192][8];
+#define FT_BEGIN long long ft0_ = clock64();
+#define FT_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
+#define FT_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
+#else
+#define FT_BEGIN
+#define FT_ADD(slot) do {} while (0)
+#define FT_CNT(slot) do {} while (0)
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------- double-FP32
@@ -92,62 +105,200 @@ __device__ __forceinline__ double bsum(double v, double* red) {
     return t;
 }
 
+
+// Supports up to this size are factored and solved by one warp (no CTA barriers).
+constexpr int WARP_FACTOR_MAX = 64;
+
+// Left-looking (dot-product form) Cholesky, in place on the lower triangle of
+// M: column j is L_rj = (G_rj - sum_{q<j} L_rq L_jq) / L_jj.  The inner sums
+// read only finished columns, so their loads pipeline; rdiag receives 1/L_jj.
+// One warp (lanes over rows).  Returns 0, or -1 on a non-positive pivot.
+template <typename T>
+__device__ int chol_warp(T* M, int ld, int np, T* rdiag) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < np; ++j) {
+        const T* Lj = M + (size_t)j * ld;
+        for (int r = j + lane; r < np; r += 32) {
+            const T* Lr = M + (size_t)r * ld;
+            T a0 = Lr[j], a1 = T(0);
+            int q = 0;
+            for (; q + 1 < j; q += 2) {
+                a0 -= Lr[q] * Lj[q];
+                a1 -= Lr[q + 1] * Lj[q + 1];
+            }
+            if (q < j) a0 -= Lr[q] * Lj[q];
+            M[(size_t)r * ld + j] = a0 + a1;
+        }
+        __syncwarp();
+        const T sj = M[(size_t)j * ld + j];
+        if (!(sj > T(0))) return -1;
+        const T dg = sqrt(sj), inv = T(1) / dg;
+        __syncwarp();
+        for (int r = j + lane; r < np; r += 32) M[(size_t)r * ld + j] = (r == j) ? dg : M[(size_t)r * ld + j] * inv;
+        if (lane == 0) rdiag[j] = inv;
+        __syncwarp();
+    }
+    return 0;
+}
+
+// Same, one row per thread across the CTA.
+template <typename T>
+__device__ int chol_block(T* M, int ld, int np, T* rdiag, int* flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < np; ++j) {
+        const T* Lj = M + (size_t)j * ld;
+        for (int r = j + tid; r < np; r += nt) {
+            const T* Lr = M + (size_t)r * ld;
+            T a0 = Lr[j], a1 = T(0);
+            int q = 0;
+            for (; q + 1 < j; q += 2) {
+                a0 -= Lr[q] * Lj[q];
+                a1 -= Lr[q + 1] * Lj[q + 1];
+            }
+            if (q < j) a0 -= Lr[q] * Lj[q];
+            M[(size_t)r * ld + j] = a0 + a1;
+        }
+        __syncthreads();
+        const T sj = M[(size_t)j * ld + j];
+        if (!(sj > T(0))) {
+            if (tid == 0) *flag = 1;
+            return -1;
+        }
+        const T dg = sqrt(sj), inv = T(1) / dg;
+        __syncthreads();
+        for (int r = j + tid; r < np; r += nt) M[(size_t)r * ld + j] = (r == j) ? dg : M[(size_t)r * ld + j] * inv;
+        if (tid == 0) rdiag[j] = inv;
+        __syncthreads();
+    }
+    if (tid == 0) *flag = 0;
+    return 0;
+}
+
+// (L L^T) v = v by one warp, dot-product form (lanes split each sum).
+template <typename T>
+__device__ void solve_warp(const T* M, int ld, int np, const T* rdiag, T* v) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < np; ++j) {  // forward: L y = v
+        const T* Lj = M + (size_t)j * ld;
+        T acc = T(0);
+        for (int q = lane; q < j; q += 32) acc += Lj[q] * v[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v[j] = (v[j] - acc) * rdiag[j];
+        __syncwarp();
+    }
+    for (int j = np - 1; j >= 0; --j) {  // backward: L^T x = y
+        T acc = T(0);
+        for (int q = j + 1 + lane; q < np; q += 32) acc += M[(size_t)q * ld + j] * v[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v[j] = (v[j] - acc) * rdiag[j];
+        __syncwarp();
+    }
+}
+
+// (L L^T) v = v by one warp for np <= 64, column sweeps with the right-hand
+// side in registers (lane owns rows lane and lane + 32).
+template <typename T>
+__device__ void solve_warp_reg(const T* M, int ld, int np, const T* rdiag, T* v) {
+    const int lane = threadIdx.x & 31;
+    const int r0 = lane, r1 = lane + 32;
+    T y0 = r0 < np ? v[r0] : T(0), y1 = r1 < np ? v[r1] : T(0);
+    for (int j = 0; j < np; ++j) {  // forward
+        const int owner = j & 31;
+        const T mine = (j < 32) ? y0 : y1;
+        const T yj = __shfl_sync(0xffffffffu, mine, owner) * rdiag[j];
+        if (lane == owner) { if (j < 32) y0 = yj; else y1 = yj; }
+        if (r0 > j && r0 < np) y0 -= M[(size_t)r0 * ld + j] * yj;
+        if (r1 > j && r1 < np) y1 -= M[(size_t)r1 * ld + j] * yj;
+    }
+    for (int j = np - 1; j >= 0; --j) {  // backward with L^T: row j of L
+        const int owner = j & 31;
+        const T mine = (j < 32) ? y0 : y1;
+        const T xj = __shfl_sync(0xffffffffu, mine, owner) * rdiag[j];
+        if (lane == owner) { if (j < 32) y0 = xj; else y1 = xj; }
+        if (r0 < j) y0 -= M[(size_t)j * ld + r0] * xj;
+        if (r1 < j) y1 -= M[(size_t)j * ld + r1] * xj;
+    }
+    if (r0 < np) v[r0] = y0;
+    if (r1 < np) v[r1] = y1;
+    __syncwarp();
+}
+
+// Block version: warp 0 runs the sweeps (each sum is split over its lanes).
+template <typename T>
+__device__ void solve_block(const T* M, int ld, int np, const T* rdiag, T* v) {
+    if (threadIdx.x < 32) {
+        if (np <= 64) solve_warp_reg(M, ld, np, rdiag, v);
+        else solve_warp(M, ld, np, rdiag, v);
+    }
+    __syncthreads();
+}
+
+// Factor of G_PP: FP32 in shared memory (the Gram block itself is only
+// FP32-accurate; refinement with exact residuals recovers full accuracy), or
+// FP64 in the global workspace when FP32 refinement stagnates.  Every thread
+// of the CTA returns the same result.
+struct Factor {
+    float* Mf;       // FP32 factor, leading dimension ldf
+    float* rdf;
+    double* Md;      // FP64 factor (global workspace), leading dimension ldd
+    double* rdd;     // reciprocal diagonal for the FP64 factor
+    float* vf;       // FP32 right-hand side scratch
+    int ldf, ldd;
+    int fp64;        // which factor is current
+};
+
+__device__ int factor(Factor& F, int np, int* flag) {
+    if (!F.fp64) {
+        if (np > WARP_FACTOR_MAX) return chol_block(F.Mf, F.ldf, np, F.rdf, flag);
+        if (threadIdx.x < 32) {
+            const int f = chol_warp(F.Mf, F.ldf, np, F.rdf);
+            if (threadIdx.x == 0) *flag = f;
+        }
+        __syncthreads();
+        return *flag;
+    }
+    if (np > WARP_FACTOR_MAX) return chol_block(F.Md, F.ldd, np, F.rdd, flag);
+    if (threadIdx.x < 32) {
+        const int f = chol_warp(F.Md, F.ldd, np, F.rdd);
+        if (threadIdx.x == 0) *flag = f;
+    }
+    __syncthreads();
+    return *flag;
+}
+
+// v <- G_PP^{-1} v with the current factor (FP32 factor: solved in FP32).
+__device__ void fsolve(const Factor& F, int np, double* v) {
+    if (!F.fp64) {
+        for (int a = threadIdx.x; a < np; a += blockDim.x) F.vf[a] = (float)v[a];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            if (np <= 64) solve_warp_reg(F.Mf, F.ldf, np, F.rdf, F.vf);
+            else solve_warp(F.Mf, F.ldf, np, F.rdf, F.vf);
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < np; a += blockDim.x) v[a] = (double)F.vf[a];
+        __syncthreads();
+        return;
+    }
+    solve_block(F.Md, F.ldd, np, F.rdd, v);
+}
+
 struct FinShared {
-    double* M;   // factor (shared or global), ld
+    Factor F;
     double* x;   // current point on S (position-indexed)
     double* z;   // solve result on P
     double* w;   // scratch on P / S
     int* P;      // support positions
     int* sg;     // sign per position of S
     int* Pi;     // atom index of each support position
+    float* rh;   // exact residual, high part
+    float* rl;   // exact residual, low part
     double red[32];
     int ival[4];
     double dval[4];
 };
-
-// In-place FP64 Cholesky (lower) of the np x np block M.  0 or -1 on a
-// non-positive pivot.
-__device__ int chol(double* M, int ld, int np, FinShared& sh) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int j = 0; j < np; ++j) {
-        if (tid == 0) {
-            const double dj = M[(size_t)j * ld + j];
-            sh.ival[0] = (dj > 0.0) ? 0 : 1;
-            M[(size_t)j * ld + j] = dj > 0.0 ? sqrt(dj) : 1.0;
-        }
-        __syncthreads();
-        if (sh.ival[0]) return -1;
-        const double inv = 1.0 / M[(size_t)j * ld + j];
-        for (int r = j + 1 + tid; r < np; r += nt) M[(size_t)r * ld + j] *= inv;
-        __syncthreads();
-        const int rem = np - j - 1;
-        for (int e = tid; e < rem * rem; e += nt) {
-            const int r = j + 1 + e / rem, c = j + 1 + e % rem;
-            if (c <= r) M[(size_t)r * ld + c] -= M[(size_t)r * ld + j] * M[(size_t)c * ld + j];
-        }
-        __syncthreads();
-    }
-    return 0;
-}
-
-// Solve (L L^T) v = v in place.
-__device__ void chol_solve(const double* M, int ld, int np, double* v) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int j = 0; j < np; ++j) {
-        if (tid == 0) v[j] /= M[(size_t)j * ld + j];
-        __syncthreads();
-        const double vj = v[j];
-        for (int r = j + 1 + tid; r < np; r += nt) v[r] -= M[(size_t)r * ld + j] * vj;
-        __syncthreads();
-    }
-    for (int j = np - 1; j >= 0; --j) {
-        if (tid == 0) v[j] /= M[(size_t)j * ld + j];
-        __syncthreads();
-        const double vj = v[j];
-        for (int r = tid; r < j; r += nt) v[r] -= M[(size_t)j * ld + r] * vj;
-        __syncthreads();
-    }
-}
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
 __device__ int build_support(int s, FinShared& sh) {
@@ -166,7 +317,116 @@ __device__ int build_support(int s, FinShared& sh) {
     return sh.ival[1];
 }
 
-__global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm) {
+// r = b - A_P x in double-FP32.  Each thread keeps 8 independent chains (8
+// entries of r), so the loads of one atom column overlap the arithmetic.
+__device__ void residual_df(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
+                            const float* __restrict__ b, float* rh, float* rl) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k0 = 0; k0 < n; k0 += 8 * nt) {
+        const int live = min(8, (n - k0 + nt - 1) / nt);  // slots with any entry in range
+        df acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + tid + u * nt;
+            acc[u] = df{k < n ? b[k] : 0.f, 0.f};
+        }
+        // four atom columns per pass, all loads issued before the arithmetic
+        int a = 0;
+        for (; a + 3 < np; a += 4) {
+            const float* c0 = A + (size_t)Pi[a] * n;
+            const float* c1 = A + (size_t)Pi[a + 1] * n;
+            const float* c2 = A + (size_t)Pi[a + 2] * n;
+            const float* c3 = A + (size_t)Pi[a + 3] * n;
+            float v0[8], v1[8], v2[8], v3[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + tid + u * nt;
+                const bool ok = u < live && k < n;
+                v0[u] = ok ? __ldg(c0 + k) : 0.f;
+                v1[u] = ok ? __ldg(c1 + k) : 0.f;
+                v2[u] = ok ? __ldg(c2 + k) : 0.f;
+                v3[u] = ok ? __ldg(c3 + k) : 0.f;
+            }
+            const df x0 = xd[a], x1 = xd[a + 1], x2 = xd[a + 2], x3 = xd[a + 3];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u < live) {
+                    acc[u] = df_fma(acc[u], -v0[u], x0);
+                    acc[u] = df_fma(acc[u], -v1[u], x1);
+                    acc[u] = df_fma(acc[u], -v2[u], x2);
+                    acc[u] = df_fma(acc[u], -v3[u], x3);
+                }
+            }
+        }
+        for (; a < np; ++a) {
+            const float* col = A + (size_t)Pi[a] * n;
+            const df xa = xd[a];
+            float av[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + tid + u * nt;
+                av[u] = (u < live && k < n) ? __ldg(col + k) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < live) acc[u] = df_fma(acc[u], -av[u], xa);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + tid + u * nt;
+            if (k < n) { rh[k] = acc[u].hi; rl[k] = acc[u].lo; }
+        }
+    }
+}
+
+// a^T r in double-FP32 by one warp (4 independent chains per lane); every lane
+// returns the same value.
+__device__ double dot_df(const float* __restrict__ a, const float* rh, const float* rl, int n) {
+    const int lane = threadIdx.x & 31;
+    df c0 = {0.f, 0.f}, c1 = c0, c2 = c0, c3 = c0;
+    int k = lane;
+    for (; k + 224 < n; k += 256) {  // 8 loads of the atom in flight per lane
+        float av[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) av[u] = __ldg(a + k + 32 * u);
+        c0 = df_fma(c0, av[0], df{rh[k], rl[k]});
+        c1 = df_fma(c1, av[1], df{rh[k + 32], rl[k + 32]});
+        c2 = df_fma(c2, av[2], df{rh[k + 64], rl[k + 64]});
+        c3 = df_fma(c3, av[3], df{rh[k + 96], rl[k + 96]});
+        c0 = df_fma(c0, av[4], df{rh[k + 128], rl[k + 128]});
+        c1 = df_fma(c1, av[5], df{rh[k + 160], rl[k + 160]});
+        c2 = df_fma(c2, av[6], df{rh[k + 192], rl[k + 192]});
+        c3 = df_fma(c3, av[7], df{rh[k + 224], rl[k + 224]});
+    }
+    for (; k + 96 < n; k += 128) {
+        const float a0 = __ldg(a + k), a1 = __ldg(a + k + 32), a2 = __ldg(a + k + 64), a3 = __ldg(a + k + 96);
+        c0 = df_fma(c0, a0, df{rh[k], rl[k]});
+        c1 = df_fma(c1, a1, df{rh[k + 32], rl[k + 32]});
+        c2 = df_fma(c2, a2, df{rh[k + 64], rl[k + 64]});
+        c3 = df_fma(c3, a3, df{rh[k + 96], rl[k + 96]});
+    }
+    for (; k < n; k += 32) c0 = df_fma(c0, __ldg(a + k), df{rh[k], rl[k]});
+    df acc = df_add(df_add(c0, c1), df_add(c2, c3));
+    acc = warp_df_sum(acc);
+    return to_d(acc);
+}
+
+// Copy the lower triangle of G_PP into the current factor storage and factor it.
+__device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < np; r += nw) {
+        const float* grow = Gi + (size_t)sh.P[r] * smax;
+        for (int c = lane; c <= r; c += 32) {
+            const float v = grow[sh.P[c]];
+            if (sh.F.fp64) sh.F.Md[(size_t)r * sh.F.ldd + c] = (double)v;
+            else sh.F.Mf[(size_t)r * sh.F.ldf + c] = v;
+        }
+    }
+    __syncthreads();
+    return factor(sh.F, np, &sh.ival[0]);
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm, int rsm) {
     const int g = blockIdx.x;
     if (g >= d.cnt->fin_n) return;
     const int i = d.list_fin[g];
@@ -180,17 +440,28 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
     }
     if (tid == 0) {
         double* p = fsm;
-        sh.M = msm ? p : d.chol + (size_t)i * smax * smax;
-        if (msm) p += (size_t)scap * scap;
         sh.x = p; p += scap;
         sh.z = p; p += scap;
         sh.w = p; p += scap;
-        sh.P = reinterpret_cast<int*>(p);
+        sh.F.rdd = p; p += scap;
+        float* q = reinterpret_cast<float*>(p);
+        sh.F.rdf = q; q += scap;
+        sh.F.vf = q; q += scap;
+        sh.F.ldf = (scap + 1) | 1;  // odd stride spreads a column over the banks
+        sh.F.Mf = msm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
+        if (msm) q += (size_t)scap * sh.F.ldf;
+        sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
         sh.Pi = sh.sg + scap;
+        // residual pair in shared memory when it fits (rsm), else in the global R32 / R32lo rows
+        float* rbase = reinterpret_cast<float*>(sh.Pi + scap);
+        sh.rh = rsm ? rbase : d.R32 + (size_t)i * d.n;
+        sh.rl = rsm ? rbase + d.n : d.R32lo + (size_t)i * d.n;
+        sh.F.Md = d.chol + (size_t)i * smax * smax;  // shares the workspace with a global FP32 factor
+        sh.F.ldd = smax;
+        sh.F.fp64 = 0;
     }
     __syncthreads();
-    const int ld = msm ? scap : smax;
     const double lam = (double)d.lam[i];
     const double tol = d.tol;
     const int* Si = d.S + (size_t)i * smax;
@@ -198,8 +469,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
     const float* hi = d.h + (size_t)i * smax;
     float* xS = d.xS + (size_t)i * smax;
     const float* b = d.B + (size_t)i * n;
-    float* rh = d.R32 + (size_t)i * n;   // residual, high part
-    float* rl = d.R32lo + (size_t)i * n; // residual, low part
+    float* rh = sh.rh;
+    float* rl = sh.rl;
 
     for (int a = tid; a < s; a += nt) {
         const float v = xS[a];
@@ -208,22 +479,30 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
     }
     __syncthreads();
 
+    FT_BEGIN
     bool ok = false;
     double kkt_on = 0.0, cmax_s = 0.0;
     int np = 0;
     const int max_steps = 4 * s + 16;
-    for (int step = 0; step < max_steps; ++step) {
+    int steps = 0;
+    for (int step = 0; step < max_steps; ++step, ++steps) {
         np = build_support(s, sh);
         // ---- solve on P
         if (np > 0) {
-            for (int e = tid; e < np * np; e += nt) {
-                const int r = e / np, c = e - r * np;
-                sh.M[(size_t)r * ld + c] = (double)Gi[(size_t)sh.P[r] * smax + sh.P[c]];
-            }
             for (int a = tid; a < np; a += nt) sh.z[a] = (double)hi[sh.P[a]] - lam * (double)sh.sg[sh.P[a]];
-            __syncthreads();
-            if (chol(sh.M, ld, np, sh) != 0) break;
-            chol_solve(sh.M, ld, np, sh.z);
+            FT_CNT(6);
+            const int fres = load_factor(sh, Gi, smax, np);
+            FT_ADD(0);
+            if (fres != 0) {
+                if (sh.F.fp64) break;
+                __syncthreads();
+                if (tid == 0) sh.F.fp64 = 1;  // FP32 pivot breakdown: retry this step in FP64
+                __syncthreads();
+                --step;
+                continue;
+            }
+            fsolve(sh.F, np, sh.z);
+            FT_ADD(1);
         }
         // ---- first sign crossing on the segment x -> z
         if (tid == 0) { sh.dval[1] = 2.0; sh.ival[2] = -1; }
@@ -241,6 +520,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             }
         }
         __syncthreads();
+        FT_ADD(2);
         if (sh.ival[2] > 0) {
             const unsigned long long key = (unsigned long long)__double_as_longlong(sh.dval[1]);
             const int pstar = (int)(key & 0xFFFull);
@@ -284,6 +564,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             }
         }
         __syncthreads();
+        FT_ADD(3);
         if (sh.dval[2] != 0.0) {
             const unsigned long long key = (unsigned long long)__double_as_longlong(sh.dval[2]);
             const int a = 0xFFF - (int)(key & 0xFFFull);
@@ -296,30 +577,18 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             continue;
         }
         // ---- exact verification: r = b - A_P x, c = A^T r (double-FP32), Newton refinement on P
-        double dmax = 0.0;
+        double dmax = 0.0, dprev = 0.0;
+        bool broke = false;
         df* xd = reinterpret_cast<df*>(sh.z);  // z is free now: x_P split into FP32 pairs
         for (int a = tid; a < np; a += nt) sh.Pi[a] = Si[sh.P[a]];
-        for (int ref = 0; ref < 5; ++ref) {
+        for (int ref = 0; ref < 16; ++ref) {
             for (int a = tid; a < np; a += nt) xd[a] = to_df(sh.x[sh.P[a]]);
             __syncthreads();
-            for (int k = tid; k < n; k += nt) {
-                df acc = {b[k], 0.f};
-                for (int a = 0; a < np; ++a)
-                    acc = df_fma(acc, -__ldg(d.A32 + (size_t)sh.Pi[a] * n + k), xd[a]);
-                rh[k] = acc.hi;
-                rl[k] = acc.lo;
-            }
+            residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
             __syncthreads();
             double lmax = 0.0;
             for (int a = warp; a < np; a += nw) {
-                const float* aj = d.A32 + (size_t)sh.Pi[a] * n;
-                df acc = {0.f, 0.f};
-                for (int k = lane; k < n; k += 32) {
-                    const float av = __ldg(aj + k);
-                    acc = df_fma(acc, av, df{rh[k], rl[k]});
-                }
-                acc = warp_df_sum(acc);
-                const double dv = to_d(acc) - lam * (double)sh.sg[sh.P[a]];
+                const double dv = dot_df(d.A32 + (size_t)sh.Pi[a] * n, rh, rl, n) - lam * (double)sh.sg[sh.P[a]];
                 if (lane == 0) sh.w[a] = dv;
                 lmax = fmax(lmax, fabs(dv));
             }
@@ -330,11 +599,26 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             __syncthreads();
             dmax = 0.0;
             for (int q = 0; q < nw; ++q) dmax = fmax(dmax, sh.red[q]);
-            if (np == 0 || dmax <= 1e-3 * tol * lam || ref == 4) break;
-            chol_solve(sh.M, ld, np, sh.w);
+            if (np == 0 || dmax <= 0.1 * tol * lam) break;
+            if (ref > 0 && dmax > 0.25 * dprev) {
+                // slow contraction: the FP32 factor limits it, refactor once in FP64
+                if (!sh.F.fp64) {
+                    __syncthreads();
+                    if (tid == 0) sh.F.fp64 = 1;
+                    __syncthreads();
+                    if (load_factor(sh, Gi, smax, np) != 0) { broke = true; break; }
+                } else if (dmax >= dprev) {
+                    break;  // no further progress possible with this Gram block
+                }
+            }
+            dprev = dmax;
+            FT_CNT(7);
+            fsolve(sh.F, np, sh.w);
             for (int a = tid; a < np; a += nt) sh.x[sh.P[a]] += sh.w[a];
             __syncthreads();
         }
+        FT_ADD(4);
+        if (broke) break;
         // on exit w holds c_P - lambda*s_P of the last evaluated residual
         // sign consistency after refinement
         if (tid == 0) sh.ival[0] = 0;
@@ -351,11 +635,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         double worst_c = 0.0;
         for (int a = warp; a < s; a += nw) {
             if (sh.sg[a] != 0) continue;
-            const float* aj = d.A32 + (size_t)Si[a] * n;
-            df acc = {0.f, 0.f};
-            for (int k = lane; k < n; k += 32) acc = df_fma(acc, __ldg(aj + k), df{rh[k], rl[k]});
-            acc = warp_df_sum(acc);
-            const double ca = to_d(acc);
+            const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
             if (fabs(ca) > cmax) { cmax = fabs(ca); worst = a; worst_c = ca; }
         }
         if (tid == 0) { sh.dval[3] = 0.0; sh.ival[3] = -1; }
@@ -373,16 +653,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         __syncthreads();
         cmax_s = 0.0;
         for (int q = 0; q < nw; ++q) cmax_s = fmax(cmax_s, sh.red[q]);
+        FT_ADD(5);
         if (sh.dval[3] != 0.0) {
             const unsigned long long key = (unsigned long long)__double_as_longlong(sh.dval[3]);
             const int a = 0xFFF - (int)(key & 0xFFFull);
             // sign of the exact correlation of the entering atom
             if (warp == 0) {
-                const float* aj = d.A32 + (size_t)Si[a] * n;
-                df acc = {0.f, 0.f};
-                for (int k = lane; k < n; k += 32) acc = df_fma(acc, __ldg(aj + k), df{rh[k], rl[k]});
-                acc = warp_df_sum(acc);
-                if (lane == 0) sh.sg[a] = to_d(acc) > 0.0 ? 1 : -1;
+                const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
+                if (lane == 0) sh.sg[a] = ca > 0.0 ? 1 : -1;
             }
             __syncthreads();
             continue;
@@ -407,6 +685,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         for (int k = tid; k < n; k += nt) {
             const double v = (double)rh[k] + (double)rl[k];
             r64[k] = v;
+            if (rsm) { d.R32[(size_t)i * n + k] = rh[k]; d.R32lo[(size_t)i * n + k] = rl[k]; }
             if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(rh[k]);
             rr += v * v;
             rb += v * (double)b[k];
@@ -433,7 +712,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             d.nnz[i] = np;
             d.finalized[i] = 1;
             d.fails[i] = 0;
-            d.finishes[i] += 1;
+            d.finishes[i] += steps + 1;
         }
     } else {
         // keep the (monotonically improved) point as the next warm start
@@ -441,15 +720,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         __syncthreads();
         if (tid == 0) {
             d.finalized[i] = 0;
-            d.finishes[i] += 1;
+            d.finishes[i] += steps;
             const int f = ++d.fails[i];
             if (f >= FIN_MAX_FAILS) {
                 d.state[i] = ST_DONE;
                 d.sstatus[i] = MPL_SIG_UNCERTIFIED;
             } else {
                 d.eps[i] = fmaxf(d.eps[i] * 1e-2f, 1e-7f);
-                const int pos = atomicAdd(&d.cnt->apg_n, 1);
-                d.list_apg[pos] = i;
+                d.state[i] = ST_REFINE;  // picked up by the next iteration's compaction
             }
         }
     }
@@ -462,18 +740,32 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     scap = ((scap + 31) / 32) * 32;
     if (scap > d.smax) scap = d.smax;
     const int msm = scap <= FIN_SMEM_P ? 1 : 0;
-    const size_t dyn = ((msm ? (size_t)scap * scap : 0) + 3 * (size_t)scap) * sizeof(double) +
-                       3 * (size_t)scap * sizeof(int);
+    const size_t ldf = (size_t)((scap + 1) | 1);
+    const int rsm = d.n <= 4096 ? 1 : 0;
+    const size_t dyn = 4 * (size_t)scap * sizeof(double) + (2 * scap + (msm ? scap * ldf : 0)) * sizeof(float) +
+                       3 * (size_t)scap * sizeof(int) + (rsm ? 2 * (size_t)d.n * sizeof(float) : 0);
     static bool attr = false;
     if (!attr) {
-        const int mx = (int)(((size_t)FIN_SMEM_P * FIN_SMEM_P + 3 * 1024) * sizeof(double) + 3 * 1024 * sizeof(int));
-        cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_finish<<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm);
+    k_finish<<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);
     ++*nl;
     return cudaGetLastError();
 }
 
 }  // namespace mpl
+
+#ifdef MPL_FIN_TRACE
+extern "C" int mpl_debug_fin_trace(long long* out, int count, int reset) {
+    if (count > 8192) count = 8192;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 8 * (size_t)count) != cudaSuccess) return -1;
+    if (reset) {
+        static long long zero[8192][8];
+        if (cudaMemcpyToSymbol(mpl::g_fin_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
+    }
+    return count;
+}
+#endif

@@ -45,7 +45,9 @@ struct mpl_ctx {
     float colmax = 0.f;
     // options
     int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
-    int sync_every = 1, profile = 0;
+    int sync_every = 2, profile = 0;
+    cudaStream_t side = nullptr;  // the exact finish runs here, overlapping the master problems
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double eps_in = 1e-4;
     // workspace
     int cap_p = 0, cap_smax = 0;
@@ -145,7 +147,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.G, pss));
     CK(alloc(h, &d.h, ps));
     CK(alloc(h, &d.ritz, ps));
-    if (smax > FIN_SMEM_P) CK(alloc(h, &d.chol, pss));
+    CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin,
                     &d.list_apg};
@@ -207,16 +209,16 @@ struct PhaseTimer {
         }
         return h->evpool[used++];
     }
-    cudaEvent_t begin() {
+    cudaEvent_t begin(cudaStream_t on = nullptr) {
         if (!h->profile) return nullptr;
         cudaEvent_t e = get();
-        cudaEventRecord(e, s);
+        cudaEventRecord(e, on ? on : s);
         return e;
     }
-    void end(int phase, cudaEvent_t b) {
+    void end(int phase, cudaEvent_t b, cudaStream_t on = nullptr) {
         if (!h->profile || !b) return;
         cudaEvent_t e = get();
-        cudaEventRecord(e, s);
+        cudaEventRecord(e, on ? on : s);
         marks.push_back({phase, {b, e}});
     }
     void collect() {
@@ -287,6 +289,9 @@ void mpl_destroy(mpl_handle_t h) {
     cudaFree(h->lamst);
     cudaFree(h->Xst);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
 }
@@ -408,16 +413,19 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         h->tmap_p = h->cap_p;
     }
 
+    if (!h->side) {
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     PhaseTimer pt{h, st, {}, 0};
     cudaEvent_t t_all = pt.begin();
     CK(launch_init(d, st, &nl));
     int act_ub = p;
-    double corr_cols = 0.0;  // signal columns processed by the correlation, summed over iterations
     const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
     for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
         const int cur = t & 1;
         const int no_grow = t >= h->max_outer;
-        corr_cols += act_ub;
         cudaEvent_t e0 = pt.begin();
         if (h->precision == 1) {
             CK(launch_gather_r16(d, cur, act_ub, st, &nl));
@@ -430,23 +438,32 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         CK(launch_select(d, cur, no_grow, act_ub, st, &nl));
         CK(launch_compact(d, cur, st, &nl));
         pt.end(2, e0);
+        // the exact finish touches only signals without violators: overlap it
+        // with the Gram growth / master problem / residual of the others
+        const int scap = std::min(d.smax, (t + 1) * d.rho);
+        CK(cudaEventRecord(h->ev_fork, st));
+        CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        e0 = pt.begin(h->side);
+        CK(launch_finish(d, act_ub, scap, h->side, &nl));
+        pt.end(4, e0, h->side);
+        CK(cudaEventRecord(h->ev_join, h->side));
         e0 = pt.begin();
         CK(launch_gram(d, act_ub, st, &nl));
         pt.end(3, e0);
         e0 = pt.begin();
-        CK(launch_finish(d, act_ub, std::min(d.smax, (t + 1) * d.rho), st, &nl));
-        pt.end(4, e0);
-        e0 = pt.begin();
-        const int vcap = std::min(d.smax, (t + 1) * d.rho);
-        CK(launch_apg(d, act_ub, h->sms, vcap, st, &nl));
+        CK(launch_apg(d, act_ub, h->sms, scap, st, &nl));
         pt.end(5, e0);
         e0 = pt.begin();
         CK(launch_residual(d, act_ub, st, &nl));
         pt.end(6, e0);
-        CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
-        act_ub = h->cnt_h->act_n[cur ^ 1];
+        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+        const bool last = t + 1 >= hard_cap;
+        if ((t + 1) % h->sync_every == 0 || last) {
+            CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
+            act_ub = h->cnt_h->act_n[cur ^ 1];
+        }
     }
     CK(cudaMemsetAsync(Xd, 0, (size_t)m * p * sizeof(float), st));
     CK(launch_scatter(d, Xd, nullptr, st, &nl));
@@ -466,7 +483,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     CK(cudaMemcpyAsync(lamh.data(), lamd, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     pt.collect();
-    h->phase_ms[7] = corr_cols;
+    h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
     h->launches = nl;
     bool all_ok = true;
     for (int i = 0; i < p; ++i) {

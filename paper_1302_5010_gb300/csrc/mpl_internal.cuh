@@ -13,6 +13,7 @@ enum SigState : int {
     ST_GROW = 1,      // new atoms were appended: Gram growth, master problem, residual
     ST_FINALIZE = 2,  // no violator left: FP64 exact finish and certificate
     ST_DONE = 3,      // certified (or given up); leaves the active list
+    ST_REFINE = 4,    // the exact finish failed: one more master-problem pass next iteration
 };
 
 // Device-side counters and work-list lengths (one instance per solve).
@@ -24,6 +25,7 @@ struct Counters {
     int apg_head;    // work-queue head of the persistent master-problem kernel
     int err;         // first device-side error code (0 = none)
     int sel_fallback;// candidate-buffer overflows in the selection
+    unsigned long long cols;  // signal columns processed by the correlation (all iterations)
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 
@@ -113,9 +115,9 @@ constexpr int SEL_THREADS = 512;
 // Master problem: Gram block kept in shared memory up to this size.
 constexpr int APG_SMEM_S = 200;
 constexpr int APG_THREADS = 256;
-// Exact finish: FP64 factor in shared memory up to this support size.
-constexpr int FIN_SMEM_P = 96;
-constexpr int FIN_THREADS = 256;
+// Exact finish: FP32 factor in shared memory up to this support size (global beyond).
+constexpr int FIN_SMEM_P = 128;
+constexpr int FIN_THREADS = 512;
 constexpr int FIN_MAX_PIVOTS = 16;
 constexpr int FIN_MAX_FAILS = 6;
 

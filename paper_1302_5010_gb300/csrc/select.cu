@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
-    if (d.state[i] == ST_DONE) return;
+    const int st0 = d.state[i];
+    if (st0 == ST_DONE || st0 == ST_REFINE) return;  // no worst-case analysis this iteration
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SelSmem& sh = *reinterpret_cast<SelSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -330,7 +331,8 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
         const int k = c0 + tid;
         int sig = -1, st = ST_DONE;
         if (k < nact) { sig = act[k]; st = d.state[sig]; }
-        const int f[3] = {st == ST_GROW, st == ST_FINALIZE, st != ST_DONE};
+        const int f[3] = {st == ST_GROW || st == ST_REFINE, st == ST_FINALIZE, st != ST_DONE};
+        if (st == ST_REFINE) d.state[sig] = ST_GROW;  // master problem again, no new atoms
         int pre[3];
         const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -366,6 +368,7 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
         __syncthreads();
     }
     if (tid == 0) {
+        d.cnt->cols += (unsigned long long)nact;
         d.cnt->grow_n = base[0];
         d.cnt->apg_n = base[0];
         d.cnt->fin_n = base[1];

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->grow_n = d.cnt->fin_n = d.cnt->apg_n = d.cnt->apg_head = 0;
             d.cnt->err = 0;
             d.cnt->sel_fallback = 0;
+            d.cnt->cols = 0ull;
         }
     }
 }
