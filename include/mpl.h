@@ -61,7 +61,10 @@ typedef enum {
     MPL_OPT_WARM_START = 6, /* 0: x^0 = 0 (Alg. 1, step 1);
                                2: proposal network seeds the active sets.  default 0 */
     MPL_OPT_SYNC_EVERY = 7, /* outer iterations launched per host/device handshake. default 2 */
-    MPL_OPT_PROFILE = 8     /* 1: record per-phase device times (mpl_get_phase_times). default 0 */
+    MPL_OPT_PROFILE = 8,    /* 1: record per-phase device times (mpl_get_phase_times) with
+                               timing events, inside the captured graphs too. default 0 */
+    MPL_OPT_GRAPH = 9       /* 1: each outer iteration is replayed from a captured CUDA graph
+                               (captured on first use per batch size and iteration). default 1 */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -178,9 +181,12 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
 
 /* Phase data of the last solve.  Entries 0..6 are device milliseconds,
  * filled when MPL_OPT_PROFILE is 1: total, correlation, selection, Gram
- * growth, exact finish, master problem, residual.  Entry 7 is the number of
- * signal columns the correlation processed, summed over outer iterations
- * (always filled).  Returns the number of values written (<= cap, <= 8). */
+ * growth, exact finish, master problem, residual (with captured graphs only
+ * the correlation and the exact finish are timed).  Entry 7 is the number of
+ * signal columns the correlation processed, summed over outer iterations;
+ * entry 8 the algorithmic FLOPs of the exact finish (factorisations, solves,
+ * residual and correlation sums); both always filled.  Returns the number of
+ * values written (<= cap, <= 9). */
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
 
 /* Number of CUDA kernel launches issued by the last bmpl_solve. */

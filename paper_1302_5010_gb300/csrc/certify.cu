@@ -293,6 +293,7 @@ struct FinShared {
     int* P;      // support positions
     int* sg;     // sign per position of S
     int* Pi;     // atom index of each support position
+    int* adds;   // times each position entered the support in this finish
     float* rh;   // exact residual, high part
     float* rl;   // exact residual, low part
     double red[32];
@@ -411,6 +412,36 @@ __device__ double dot_df(const float* __restrict__ a, const float* rh, const flo
     return to_d(acc);
 }
 
+// a^T b of two FP32 atoms in double-FP32 (products are exact) by one warp.
+__device__ double dot_ff(const float* __restrict__ a, const float* __restrict__ b, int n) {
+    const int lane = threadIdx.x & 31;
+    df c0 = {0.f, 0.f}, c1 = c0;
+    int k = lane;
+    for (; k + 32 < n; k += 64) {
+        const float a0 = __ldg(a + k), b0 = __ldg(b + k), a1 = __ldg(a + k + 32), b1 = __ldg(b + k + 32);
+        c0 = df_fma(c0, a0, df{b0, 0.f});
+        c1 = df_fma(c1, a1, df{b1, 0.f});
+    }
+    for (; k < n; k += 32) c0 = df_fma(c0, __ldg(a + k), df{__ldg(b + k), 0.f});
+    return to_d(warp_df_sum(df_add(c0, c1)));
+}
+
+// Last resort for ill-conditioned blocks: G_PP recomputed from the atoms in
+// double-FP32 into the FP64 factor storage, then factored in FP64.
+__device__ int exact_factor(FinShared& sh, const float* A, int n, int np) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = warp; e < np * (np + 1) / 2; e += nw) {
+        int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        while (r * (r + 1) / 2 > e) --r;
+        const int c = e - r * (r + 1) / 2;
+        const double v = dot_ff(A + (size_t)sh.Pi[r] * n, A + (size_t)sh.Pi[c] * n, n);
+        if (lane == 0) sh.F.Md[(size_t)r * sh.F.ldd + c] = v;
+    }
+    __syncthreads();
+    return factor(sh.F, np, &sh.ival[0]);
+}
+
 // Copy the lower triangle of G_PP into the current factor storage and factor it.
 __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -453,8 +484,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
         sh.Pi = sh.sg + scap;
+        sh.adds = sh.Pi + scap;
         // residual pair in shared memory when it fits (rsm), else in the global R32 / R32lo rows
-        float* rbase = reinterpret_cast<float*>(sh.Pi + scap);
+        float* rbase = reinterpret_cast<float*>(sh.adds + scap);
         sh.rh = rsm ? rbase : d.R32 + (size_t)i * d.n;
         sh.rl = rsm ? rbase + d.n : d.R32lo + (size_t)i * d.n;
         sh.F.Md = d.chol + (size_t)i * smax * smax;  // shares the workspace with a global FP32 factor
@@ -483,14 +515,19 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
     bool ok = false;
     double kkt_on = 0.0, cmax_s = 0.0;
     int np = 0;
-    const int max_steps = 4 * s + 16;
+    const int max_steps = s + 32;
+    if (tid == 0) sh.ival[3] = 0;  // 1: the last step added an atom from the exact check
+    for (int a = tid; a < s; a += nt) sh.adds[a] = 0;
+    __syncthreads();
     int steps = 0;
+    unsigned long long flops = 0;  // algorithmic work (thread 0 keeps the tally)
     for (int step = 0; step < max_steps; ++step, ++steps) {
         np = build_support(s, sh);
         // ---- solve on P
         if (np > 0) {
             for (int a = tid; a < np; a += nt) sh.z[a] = (double)hi[sh.P[a]] - lam * (double)sh.sg[sh.P[a]];
             FT_CNT(6);
+            flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
             const int fres = load_factor(sh, Gi, smax, np);
             FT_ADD(0);
             if (fres != 0) {
@@ -504,10 +541,15 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             fsolve(sh.F, np, sh.z);
             FT_ADD(1);
         }
-        // ---- first sign crossing on the segment x -> z
-        if (tid == 0) { sh.dval[1] = 2.0; sh.ival[2] = -1; }
+        // ---- first sign crossing on the segment x -> z.  Skipped right after the
+        // exact check admitted an atom: its coefficient may be below the FP32
+        // Gram block's resolution, so it goes straight to exact refinement.
+        const bool exact_entry = sh.ival[3] != 0;
         __syncthreads();
-        for (int a = tid; a < np; a += nt) {
+        if (tid == 0) { sh.dval[1] = 2.0; sh.ival[2] = -1; sh.ival[3] = 0; }
+        __syncthreads();
+        if (!exact_entry) {
+          for (int a = tid; a < np; a += nt) {
             const int pa = sh.P[a];
             const double xa = sh.x[pa], za = sh.z[a];
             if (!(za * (double)sh.sg[pa] > 0.0)) {
@@ -518,6 +560,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
                 atomicMin(reinterpret_cast<unsigned long long*>(&sh.dval[1]), key);
                 sh.ival[2] = 1;
             }
+          }
         }
         __syncthreads();
         FT_ADD(2);
@@ -546,7 +589,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         for (int a = tid; a < np; a += nt) sh.x[sh.P[a]] = sh.z[a];
         __syncthreads();
         // ---- zero entries of S through the Gram block: add the largest violator
-        if (tid == 0) { sh.dval[2] = 0.0; sh.ival[3] = -1; }
+        if (tid == 0) sh.dval[2] = 0.0;
         __syncthreads();
         for (int a = warp; a < s; a += nw) {
             if (sh.sg[a] != 0) continue;
@@ -556,7 +599,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
 #pragma unroll
             for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const double ca = (double)hi[a] - acc;
-            if (lane == 0 && fabs(ca) > lam * (1.0 + 0.5 * tol)) {
+            if (lane == 0 && fabs(ca) > lam * (1.0 + 1e-3)) {  // well beyond the Gram block's resolution
                 // largest |c|, ties to the lowest position
                 unsigned long long key = ((unsigned long long)__double_as_longlong(fabs(ca)) & ~0xFFFull) |
                                          (unsigned long long)(0xFFF - a);
@@ -572,20 +615,23 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
                 double acc = 0.0;
                 for (int c = 0; c < np; ++c) acc += (double)Gi[(size_t)a * smax + sh.P[c]] * sh.x[sh.P[c]];
                 sh.sg[a] = ((double)hi[a] - acc) > 0.0 ? 1 : -1;
+                sh.ival[0] = ++sh.adds[a] > 3;  // an atom that keeps re-entering: give up
             }
             __syncthreads();
+            if (sh.ival[0]) break;
             continue;
         }
         // ---- exact verification: r = b - A_P x, c = A^T r (double-FP32), Newton refinement on P
         double dmax = 0.0, dprev = 0.0;
-        bool broke = false;
+        bool broke = false, exact_g = false;
         df* xd = reinterpret_cast<df*>(sh.z);  // z is free now: x_P split into FP32 pairs
         for (int a = tid; a < np; a += nt) sh.Pi[a] = Si[sh.P[a]];
-        for (int ref = 0; ref < 16; ++ref) {
+        for (int ref = 0; ref < 24; ++ref) {
             for (int a = tid; a < np; a += nt) xd[a] = to_df(sh.x[sh.P[a]]);
             __syncthreads();
             residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
             __syncthreads();
+            flops += 4ull * n * np;  // residual and on-support correlations
             double lmax = 0.0;
             for (int a = warp; a < np; a += nw) {
                 const double dv = dot_df(d.A32 + (size_t)sh.Pi[a] * n, rh, rl, n) - lam * (double)sh.sg[sh.P[a]];
@@ -608,11 +654,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
                     __syncthreads();
                     if (load_factor(sh, Gi, smax, np) != 0) { broke = true; break; }
                 } else if (dmax >= dprev) {
-                    break;  // no further progress possible with this Gram block
+                    if (exact_g) break;  // no further progress possible
+                    exact_g = true;      // the FP32 Gram block limits it: rebuild it exactly
+                    if (exact_factor(sh, d.A32, n, np) != 0) { broke = true; break; }
                 }
             }
             dprev = dmax;
             FT_CNT(7);
+            flops += 2ull * np * np;
             fsolve(sh.F, np, sh.w);
             for (int a = tid; a < np; a += nt) sh.x[sh.P[a]] += sh.w[a];
             __syncthreads();
@@ -629,6 +678,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         }
         __syncthreads();
         if (sh.ival[0]) continue;
+        flops += 2ull * n * (unsigned long long)(s - np);
         // exact check of the zero entries of S
         double cmax = 0.0;
         int worst = -1;
@@ -638,7 +688,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
             if (fabs(ca) > cmax) { cmax = fabs(ca); worst = a; worst_c = ca; }
         }
-        if (tid == 0) { sh.dval[3] = 0.0; sh.ival[3] = -1; }
+        if (tid == 0) sh.dval[3] = 0.0;
         __syncthreads();
         if (lane == 0 && worst >= 0 && cmax > lam * (1.0 + tol)) {
             unsigned long long key = ((unsigned long long)__double_as_longlong(cmax) & ~0xFFFull) |
@@ -660,9 +710,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             // sign of the exact correlation of the entering atom
             if (warp == 0) {
                 const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
-                if (lane == 0) sh.sg[a] = ca > 0.0 ? 1 : -1;
+                if (lane == 0) {
+                    sh.sg[a] = ca > 0.0 ? 1 : -1;
+                    sh.ival[3] = 1;  // enters through exact refinement
+                    sh.ival[0] = ++sh.adds[a] > 3;
+                }
             }
             __syncthreads();
+            if (sh.ival[0]) break;
             continue;
         }
         kkt_on = fmax(dmax / lam, fmax(cmax_s - lam, 0.0) / lam);
@@ -670,6 +725,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
         break;
     }
 
+    if (tid == 0) atomicAdd(&d.cnt->fin_flops, flops);
     if (ok) {
         double* x64 = d.xS64 + (size_t)i * smax;
         double l1 = 0.0, cm = 0.0;
@@ -735,6 +791,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
 
 }  // namespace
 
+cudaError_t prepare_finish() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     scap = ((scap + 31) / 32) * 32;
@@ -743,13 +807,9 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     const size_t ldf = (size_t)((scap + 1) | 1);
     const int rsm = d.n <= 4096 ? 1 : 0;
     const size_t dyn = 4 * (size_t)scap * sizeof(double) + (2 * scap + (msm ? scap * ldf : 0)) * sizeof(float) +
-                       3 * (size_t)scap * sizeof(int) + (rsm ? 2 * (size_t)d.n * sizeof(float) : 0);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+                       4 * (size_t)scap * sizeof(int) + (rsm ? 2 * (size_t)d.n * sizeof(float) : 0);
+    cudaError_t ep = prepare_finish();
+    if (ep != cudaSuccess) return ep;
     k_finish<<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);
     ++*nl;
     return cudaGetLastError();

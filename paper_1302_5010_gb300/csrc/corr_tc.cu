@@ -312,17 +312,22 @@ cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16, 
     return encode_rows(&maps[1], R16c, pmax, n, TC_BN);
 }
 
+cudaError_t prepare_corr_bf16() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    using L = TcSmem<TC_BN, TC_STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_corr_bf16<TC_BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms, cudaStream_t s,
                              int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
     using L = TcSmem<TC_BN, TC_STAGES>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr_bf16<TC_BN, TC_STAGES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t ep = prepare_corr_bf16();
+    if (ep != cudaSuccess) return ep;
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(tmap);
     const int tiles = ((d.m + TC_BM - 1) / TC_BM) * ((act_n_ub + TC_BN - 1) / TC_BN);
     const int grid = tiles < sms ? tiles : sms;

@@ -47,7 +47,18 @@ struct mpl_ctx {
     int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
     int sync_every = 2, profile = 0;
     cudaStream_t side = nullptr;  // the exact finish runs here, overlapping the master problems
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t main = nullptr;  // graph-mode solves run here (captured streams cannot be the legacy one)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
+    int use_graph = 1;
+    struct GraphEntry {
+        int p, tk, par, nog, prof;
+        double tol;
+        cudaGraphExec_t exec;
+        std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;  // phase timing nodes
+    };
+    std::vector<GraphEntry> graphs;  // captured outer iterations, valid for the current workspace
+    float* Bint = nullptr;           // fixed internal copies of B and lambda (graph parameters)
+    float* lamint = nullptr;
     double eps_in = 1e-4;
     // workspace
     int cap_p = 0, cap_smax = 0;
@@ -67,7 +78,7 @@ struct mpl_ctx {
     int last_p = 0;
     std::vector<mpl_signal_stats_t> stats;
     int64_t launches = 0;
-    double phase_ms[8] = {0};
+    double phase_ms[9] = {0};
     std::vector<cudaEvent_t> evpool;
 };
 
@@ -99,7 +110,19 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+void clear_graphs(mpl_ctx* h) {
+    for (auto& g : h->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        for (auto& mk : g.marks) {
+            cudaEventDestroy(mk.second.first);
+            cudaEventDestroy(mk.second.second);
+        }
+    }
+    h->graphs.clear();
+}
+
 void free_ws(mpl_ctx* h) {
+    clear_graphs(h);
     for (auto& b : h->bufs) cudaFree(b.p);
     h->bufs.clear();
     h->cap_p = 0;
@@ -157,12 +180,18 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     double** dbl[] = {&d.obj, &d.kkt_in, &d.kkt_out, &d.ginf, &d.rr, &d.rb};
     for (double** q : dbl) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.cnt, 1));
+    CK(alloc(h, &h->Bint, pn));
+    CK(alloc(h, &h->lamint, (size_t)P));
     CK(cudaMemset(d.xS, 0, ps * sizeof(float)));
     CK(cudaMemset(d.G, 0, pss * sizeof(float)));
     d.n = n;
     d.m = m;
     d.smax = smax;
     d.mw = mw;
+    CK(prepare_select());
+    CK(prepare_apg());
+    CK(prepare_finish());
+    CK(prepare_corr_bf16());
     h->cap_p = P;
     h->cap_smax = smax;
     h->cap_r16 = need_r16;
@@ -201,7 +230,13 @@ struct PhaseTimer {
     cudaStream_t s;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
     size_t used = 0;
+    bool own = false;  // events created for (and owned by) a captured graph
     cudaEvent_t get() {
+        if (own) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
         if (used == h->evpool.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -209,21 +244,34 @@ struct PhaseTimer {
         }
         return h->evpool[used++];
     }
+    void record(cudaEvent_t e, cudaStream_t on) {
+        // inside a capture, timing needs an external event-record node
+        if (own) cudaEventRecordWithFlags(e, on ? on : s, cudaEventRecordExternal);
+        else cudaEventRecord(e, on ? on : s);
+    }
+    int only_a = -1, only_b = -1;  // graph mode: time only these phases (cheaper)
     cudaEvent_t begin(cudaStream_t on = nullptr) {
         if (!h->profile) return nullptr;
         cudaEvent_t e = get();
-        cudaEventRecord(e, on ? on : s);
+        record(e, on);
         return e;
     }
     void end(int phase, cudaEvent_t b, cudaStream_t on = nullptr) {
         if (!h->profile || !b) return;
         cudaEvent_t e = get();
-        cudaEventRecord(e, on ? on : s);
+        record(e, on);
         marks.push_back({phase, {b, e}});
+    }
+    cudaEvent_t begin_if(int phase, cudaStream_t on = nullptr) {
+        if (only_a >= 0 && phase != only_a && phase != only_b) return nullptr;
+        return begin(on);
     }
     void collect() {
         for (int k = 0; k < 7; ++k) h->phase_ms[k] = 0.0;
-        for (auto& mk : marks) {
+        add(marks);
+    }
+    void add(const std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>& mks) {
+        for (auto& mk : mks) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, mk.second.first, mk.second.second);
             h->phase_ms[mk.first] += ms;
@@ -289,7 +337,11 @@ void mpl_destroy(mpl_handle_t h) {
     cudaFree(h->lamst);
     cudaFree(h->Xst);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
+    clear_graphs(h);
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->main) cudaStreamDestroy(h->main);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (auto e : h->evpool) cudaEventDestroy(e);
@@ -298,6 +350,7 @@ void mpl_destroy(mpl_handle_t h) {
 
 mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
     if (!h || !std::isfinite(v)) return MPL_ERR_ARG;
+    clear_graphs(h);  // captured iterations embed the options
     switch (key) {
         case MPL_OPT_RHO:
             if (v < 1 || v > 4096) return MPL_ERR_ARG;
@@ -335,6 +388,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
         case OPT_PROFILE:
             h->profile = v != 0;
             return MPL_OK;
+        case MPL_OPT_GRAPH:
+            if (v != 0 && v != 1) return MPL_ERR_ARG;
+            h->use_graph = (int)v;
+            return MPL_OK;
         default:
             return MPL_ERR_ARG;
     }
@@ -352,8 +409,87 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_START: *v = h->warm; return MPL_OK;
         case MPL_OPT_SYNC_EVERY: *v = h->sync_every; return MPL_OK;
         case OPT_PROFILE: *v = h->profile; return MPL_OK;
+        case MPL_OPT_GRAPH: *v = h->use_graph; return MPL_OK;
         default: return MPL_ERR_ARG;
     }
+}
+
+// One outer iteration of Algorithm 1 for every active signal (kernels only).
+// pt == nullptr: no timing events (graph capture).
+static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub, cudaStream_t run,
+                                    PhaseTimer* pt, int64_t* nl) {
+    const int cur = t & 1;
+    const int no_grow = t >= h->max_outer;
+    cudaError_t e;
+    cudaEvent_t e0 = pt ? pt->begin_if(1, run) : nullptr;
+    if (h->precision == 1) {
+        if ((e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+    }
+    if (pt) pt->end(1, e0, run);
+    e0 = pt ? pt->begin_if(2, run) : nullptr;
+    if ((e = launch_select(d, cur, no_grow, act_ub, run, nl)) != cudaSuccess) return e;
+    if ((e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
+    if (pt) pt->end(2, e0, run);
+    // the exact finish touches only signals without violators: overlap it
+    // with the Gram growth / master problem / residual of the others
+    const int scap = std::min(d.smax, (t + 1) * d.rho);
+    if ((e = cudaEventRecord(h->ev_fork, run)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    e0 = pt ? pt->begin_if(4, h->side) : nullptr;
+    if ((e = launch_finish(d, act_ub, scap, h->side, nl)) != cudaSuccess) return e;
+    if (pt) pt->end(4, e0, h->side);
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    e0 = pt ? pt->begin_if(3, run) : nullptr;
+    if ((e = launch_gram(d, act_ub, run, nl)) != cudaSuccess) return e;
+    if (pt) pt->end(3, e0, run);
+    e0 = pt ? pt->begin_if(5, run) : nullptr;
+    if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) return e;
+    if (pt) pt->end(5, e0, run);
+    e0 = pt ? pt->begin_if(6, run) : nullptr;
+    if ((e = launch_residual(d, act_ub, run, nl)) != cudaSuccess) return e;
+    if (pt) pt->end(6, e0, run);
+    return cudaStreamWaitEvent(run, h->ev_join, 0);
+}
+
+// Captured iteration for (p, t): iterations past the point where the
+// active-set bound saturates share one graph per parity.
+static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, double tol, cudaStream_t run,
+                                   size_t* out, int64_t* nl) {
+    const int tsat = (d.smax + d.rho - 1) / d.rho;
+    const int tk = std::min(t, tsat + 1);
+    const int par = t & 1, nog = t >= h->max_outer ? 1 : 0, prof = h->profile ? 1 : 0;
+    for (size_t gi = 0; gi < h->graphs.size(); ++gi) {
+        const auto& g = h->graphs[gi];
+        if (g.p == p && g.tk == tk && g.par == par && g.nog == nog && g.prof == prof && g.tol == tol) {
+            *out = gi;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaStreamBeginCapture(run, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int64_t cnt = 0;
+    PhaseTimer gpt{h, run, {}, 0, true};
+    gpt.only_a = 1;  // correlation and exact finish: the two phases a roofline needs
+    gpt.only_b = 4;
+    cudaError_t el = launch_iteration(h, d, t, p, run, prof ? &gpt : nullptr, &cnt);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(run, &graph);
+    if (el != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return el;
+    }
+    if (e != cudaSuccess) return e;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    h->graphs.push_back({p, tk, par, nog, prof, tol, exec, gpt.marks});
+    *out = h->graphs.size() - 1;
+    (void)nl;
+    return cudaSuccess;
 }
 
 mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lambda, float* X, double tol,
@@ -365,31 +501,34 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     h->last_p = p;
     h->stats.assign((size_t)p, mpl_signal_stats_t{});
     if (p == 0) return MPL_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(h->dev));
     mpl_status_t ws = ensure_ws(h, p);
     if (ws != MPL_OK) return ws;
     const int n = h->n, m = h->m;
     int64_t nl = 0;
+    if (!h->side) {
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->main, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    }
+    // all work runs on the library's stream, ordered after the caller's stream
+    const bool graph = h->use_graph != 0;
+    cudaStream_t st = h->main;
+    CK(cudaEventRecord(h->ev_in, caller));
+    CK(cudaStreamWaitEvent(st, h->ev_in, 0));
     if (h->precision == 1 && !h->A16) {
         CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
         CK(launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, &nl));
     }
-    // arguments: stage host-resident buffers through device memory
-    const float* Bd = B;
-    const float* lamd = lambda;
+    // arguments: B and lambda into the handle's fixed buffers (device or host source)
+    CK(cudaMemcpyAsync(h->Bint, B, (size_t)n * p * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(h->lamint, lambda, (size_t)p * sizeof(float), cudaMemcpyDefault, st));
     float* Xd = X;
     const bool X_host = !is_device_ptr(X);
-    if (!is_device_ptr(B)) {
-        CK(ensure_staging(&h->Bst, &h->Bst_b, (size_t)n * p * sizeof(float)));
-        CK(cudaMemcpyAsync(h->Bst, B, (size_t)n * p * sizeof(float), cudaMemcpyHostToDevice, st));
-        Bd = h->Bst;
-    }
-    if (!is_device_ptr(lambda)) {
-        CK(ensure_staging(&h->lamst, &h->lamst_b, (size_t)p * sizeof(float)));
-        CK(cudaMemcpyAsync(h->lamst, lambda, (size_t)p * sizeof(float), cudaMemcpyHostToDevice, st));
-        lamd = h->lamst;
-    }
     if (X_host) {
         CK(ensure_staging(&h->Xst, &h->Xst_b, (size_t)m * p * sizeof(float)));
         Xd = h->Xst;
@@ -405,64 +544,47 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     d.colmax = h->colmax;
     d.A32 = h->A32;
     d.A16 = h->A16;
-    d.B = Bd;
-    d.lam = lamd;
+    d.B = h->Bint;
+    d.lam = h->lamint;
     set_bounds(h, d);
     if (h->precision == 1 && h->tmap_p != h->cap_p) {
         CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
         h->tmap_p = h->cap_p;
     }
+    const float* lamd = h->lamint;
 
-    if (!h->side) {
-        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    }
     PhaseTimer pt{h, st, {}, 0};
     cudaEvent_t t_all = pt.begin();
     CK(launch_init(d, st, &nl));
     int act_ub = p;
     const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
+    std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
+    double graph_phase[8] = {0};
     for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
-        const int cur = t & 1;
-        const int no_grow = t >= h->max_outer;
-        cudaEvent_t e0 = pt.begin();
-        if (h->precision == 1) {
-            CK(launch_gather_r16(d, cur, act_ub, st, &nl));
-            CK(launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, st, &nl));
+        if (graph) {
+            size_t gi = 0;
+            CK(iteration_graph(h, d, t, p, tol, st, &gi, &nl));
+            CK(cudaGraphLaunch(h->graphs[gi].exec, st));
+            nl += (h->precision == 1 ? 8 : 7);
+            window.push_back(gi);
         } else {
-            CK(launch_corr_f32(d, cur, act_ub, st, &nl));
+            CK(launch_iteration(h, d, t, act_ub, st, &pt, &nl));
         }
-        pt.end(1, e0);
-        e0 = pt.begin();
-        CK(launch_select(d, cur, no_grow, act_ub, st, &nl));
-        CK(launch_compact(d, cur, st, &nl));
-        pt.end(2, e0);
-        // the exact finish touches only signals without violators: overlap it
-        // with the Gram growth / master problem / residual of the others
-        const int scap = std::min(d.smax, (t + 1) * d.rho);
-        CK(cudaEventRecord(h->ev_fork, st));
-        CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        e0 = pt.begin(h->side);
-        CK(launch_finish(d, act_ub, scap, h->side, &nl));
-        pt.end(4, e0, h->side);
-        CK(cudaEventRecord(h->ev_join, h->side));
-        e0 = pt.begin();
-        CK(launch_gram(d, act_ub, st, &nl));
-        pt.end(3, e0);
-        e0 = pt.begin();
-        CK(launch_apg(d, act_ub, h->sms, scap, st, &nl));
-        pt.end(5, e0);
-        e0 = pt.begin();
-        CK(launch_residual(d, act_ub, st, &nl));
-        pt.end(6, e0);
-        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
         const bool last = t + 1 >= hard_cap;
         if ((t + 1) % h->sync_every == 0 || last) {
             CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
-            act_ub = h->cnt_h->act_n[cur ^ 1];
+            act_ub = h->cnt_h->act_n[(t & 1) ^ 1];
+            if (graph && h->profile) {
+                for (size_t gi : window)
+                    for (auto& mk : h->graphs[gi].marks) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, mk.second.first, mk.second.second);
+                        graph_phase[mk.first] += ms;
+                    }
+            }
+            window.clear();
         }
     }
     CK(cudaMemsetAsync(Xd, 0, (size_t)m * p * sizeof(float), st));
@@ -481,9 +603,13 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         CK(cudaMemcpyAsync(dvv.data() + (size_t)k * p, dsrc[k], (size_t)p * sizeof(double), cudaMemcpyDeviceToHost, st));
     std::vector<float> lamh((size_t)p);
     CK(cudaMemcpyAsync(lamh.data(), lamd, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->ev_out, st));
+    CK(cudaStreamWaitEvent(caller, h->ev_out, 0));
     CK(cudaStreamSynchronize(st));
     pt.collect();
+    for (int k = 1; k < 7; ++k) h->phase_ms[k] += graph_phase[k];
     h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
+    h->phase_ms[8] = (double)h->cnt_h->fin_flops;  // algorithmic FLOPs of the exact finish
     h->launches = nl;
     bool all_ok = true;
     for (int i = 0; i < p; ++i) {
@@ -578,7 +704,7 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
 
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
     if (!h || !ms_out) return 0;
-    const int k = std::min(cap, 8);
+    const int k = std::min(cap, 9);
     for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
     return k;
 }

@@ -26,6 +26,7 @@ struct Counters {
     int err;         // first device-side error code (0 = none)
     int sel_fallback;// candidate-buffer overflows in the selection
     unsigned long long cols;  // signal columns processed by the correlation (all iterations)
+    unsigned long long fin_flops;  // algorithmic FLOPs of the exact finish (factor, solves, residual sums)
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 
@@ -105,6 +106,12 @@ cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, 
 cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
                            cudaStream_t s, int64_t* nl);
 cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl);
+
+// One-time kernel attribute set-up (call before any stream capture).
+cudaError_t prepare_select();
+cudaError_t prepare_apg();
+cudaError_t prepare_finish();
+cudaError_t prepare_corr_bf16();
 
 // Device-side error codes written to Counters::err.
 enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SHAPE = 3 };

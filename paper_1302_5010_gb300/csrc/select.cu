@@ -57,12 +57,14 @@ __device__ __forceinline__ double warp_dot_f64(const float* __restrict__ a, cons
     return acc;
 }
 
+constexpr int SEL_ROWCACHE = 8192;  // score rows up to this length stay in shared memory
+
 struct SelSmem {
     unsigned hist[2048];
     unsigned long long key[SEL_KCAP];  // sort keys of the violators
     int idx[SEL_KCAP];                 // candidate atoms
-    float sc[SEL_KCAP];                // their re-scores
-    int vflag[SEL_KCAP];               // 1 = violator
+    float sc[SEL_KCAP];                // their re-scores, negated for non-violators
+    float row[SEL_ROWCACHE];           // the signal's score row (when m fits)
     unsigned kc;                       // candidates collected
     unsigned vc;                       // violators
     unsigned bin, need;
@@ -83,7 +85,7 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
 
 // Key of the kth largest score (1-based) among the m keys, by 3 radix passes
 // over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.
-__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh, bool fill) {
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned prefix = 0, pmask = 0;
     unsigned need = (unsigned)kth;
@@ -95,8 +97,10 @@ __device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int 
         for (int b = tid; b < nb; b += nt) sh.hist[b] = 0;
         __syncthreads();
         int nf = 0;
+        const float* src = (pass > 0 && fill) ? sh.row : row;
         for (int j = tid; j < m; j += nt) {
-            const unsigned kj = key_of(row, msk, j, &nf);
+            if (pass == 0 && fill) sh.row[j] = row[j];
+            const unsigned kj = key_of(src, msk, j, &nf);
             if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
         }
         if (nf) sh.nonfinite = 1;
@@ -212,12 +216,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     unsigned kc = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const float D = exact_scores ? 0.f : delta + delta32;
-        const unsigned kkey = radix_kth(row, msk, m, kth, sh);
+        const bool cache = m <= SEL_ROWCACHE;
+        const unsigned kkey = radix_kth(row, msk, m, kth, sh, cache);
         const float s_rho = __uint_as_float(kkey);
         float tau = fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
-        kc = collect(row, msk, m, tkey, sh);
+        kc = collect(cache ? sh.row : row, msk, m, tkey, sh);
         if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
         // Too many candidates in the band: re-score every atom outside S in place
         // (this row is private to the signal) and select on the re-scores.
@@ -250,10 +255,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
             viol = c64 > lam_hi;
             certb = (float)(c64 * (1.0 + 1e-12));
         }
-        if (lane == 0) {
-            sh.sc[c] = score;
-            sh.vflag[c] = viol;
-        }
+        if (lane == 0) sh.sc[c] = viol ? score : -score;
         offmax = fmaxf(offmax, certb);
     }
     if (lane == 0 && offmax > 0.f) atomicMax(reinterpret_cast<unsigned*>(&sh.offmax), __float_as_uint(offmax));
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     // Sort keys: (re-score bits, inverted index) so that larger scores come
     // first and the lower index wins ties.
     for (unsigned c = tid; c < kc; c += blockDim.x) {
-        if (sh.vflag[c]) {
+        if (sh.sc[c] > 0.f) {
             const unsigned pos = atomicAdd(&sh.vc, 1u);
             sh.key[pos] = ((unsigned long long)__float_as_uint(sh.sc[c]) << 32) |
                           (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
@@ -379,15 +381,19 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
 
 }  // namespace
 
+cudaError_t prepare_select() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SelSmem));
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
     const size_t sm = sizeof(SelSmem);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = prepare_select();
+    if (e != cudaSuccess) return e;
     k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow);
     ++*nl;
     return cudaGetLastError();

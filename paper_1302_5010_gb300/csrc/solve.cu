@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->err = 0;
             d.cnt->sel_fallback = 0;
             d.cnt->cols = 0ull;
+            d.cnt->fin_flops = 0ull;
         }
     }
 }
@@ -107,67 +108,67 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
 constexpr int GBM = 64, GBN = 32, GBK = 32;
 
 template <bool VEC>
+__device__ __forceinline__ float4 gram_load(const float* row, int k, int n) {
+    if (row == nullptr || k >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (VEC) return __ldg(reinterpret_cast<const float4*>(row + k));
+    float t[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) t[e] = (k + e < n) ? __ldg(row + k + e) : 0.f;
+    return make_float4(t[0], t[1], t[2], t[3]);
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_gram(Dev d) {
     const int g = blockIdx.x;
     if (g >= d.cnt->grow_n) return;
     const int i = d.list_grow[g];
     const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
     const int a0 = blockIdx.y * GBM;
-    if (a0 >= s) return;
+    if (a0 >= s || q == 0) return;  // q == 0: a refine pass, the block is complete
     const int n = d.n, smax = d.smax;
     const int* Si = d.S + (size_t)i * smax;
     float* Gi = d.G + (size_t)i * smax * smax;
-    __shared__ __align__(16) float As[GBK][GBM + 4];
-    __shared__ __align__(16) float Bs[GBK][GBN + 4];
+    // two K-slices: the next slice's loads are in flight while this one is used
+    __shared__ __align__(16) float As[2][GBK][GBM + 4];
+    __shared__ __align__(16) float Bs[2][GBK][GBN + 4];
     const int tid = threadIdx.x;
     const int ty = tid >> 3, tx = tid & 7;
     const int lr = tid >> 3, lk = (tid & 7) * 4;
 
-    for (int b0 = 0; b0 < q; b0 += GBN) {
+    // columns 0..q-1 are the new atoms, column q is the signal b itself (gives h = A_S^T b)
+    for (int b0 = 0; b0 <= q; b0 += GBN) {
         float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         const int ra0 = a0 + lr, ra1 = a0 + lr + 32;
         const float* pa0 = (ra0 < s) ? d.A32 + (size_t)Si[ra0] * n : nullptr;
         const float* pa1 = (ra1 < s) ? d.A32 + (size_t)Si[ra1] * n : nullptr;
         const int rb = b0 + lr;
-        const float* pb = (rb < q) ? d.A32 + (size_t)Si[s0 + rb] * n : nullptr;
-        for (int k0 = 0; k0 < n; k0 += GBK) {
-            const int kk = k0 + lk;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, vb = v0;
-            if (VEC) {
-                if (kk < n) {
-                    if (pa0) v0 = __ldg(reinterpret_cast<const float4*>(pa0 + kk));
-                    if (pa1) v1 = __ldg(reinterpret_cast<const float4*>(pa1 + kk));
-                    if (pb) vb = __ldg(reinterpret_cast<const float4*>(pb + kk));
-                }
-            } else {
-                float t0[4] = {0, 0, 0, 0}, t1[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
-                for (int e = 0; e < 4; ++e) {
-                    if (kk + e < n) {
-                        if (pa0) t0[e] = pa0[kk + e];
-                        if (pa1) t1[e] = pa1[kk + e];
-                        if (pb) tb[e] = pb[kk + e];
-                    }
-                }
-                v0 = make_float4(t0[0], t0[1], t0[2], t0[3]);
-                v1 = make_float4(t1[0], t1[1], t1[2], t1[3]);
-                vb = make_float4(tb[0], tb[1], tb[2], tb[3]);
-            }
-            As[lk + 0][lr] = v0.x; As[lk + 1][lr] = v0.y; As[lk + 2][lr] = v0.z; As[lk + 3][lr] = v0.w;
-            As[lk + 0][lr + 32] = v1.x; As[lk + 1][lr + 32] = v1.y;
-            As[lk + 2][lr + 32] = v1.z; As[lk + 3][lr + 32] = v1.w;
-            Bs[lk + 0][lr] = vb.x; Bs[lk + 1][lr] = vb.y; Bs[lk + 2][lr] = vb.z; Bs[lk + 3][lr] = vb.w;
+        const float* pb = (rb < q) ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+        float4 v0 = gram_load<VEC>(pa0, lk, n), v1 = gram_load<VEC>(pa1, lk, n), vb = gram_load<VEC>(pb, lk, n);
+        const int nsl = (n + GBK - 1) / GBK;
+        for (int sl = 0; sl < nsl; ++sl) {
+            const int buf = sl & 1;
+            As[buf][lk + 0][lr] = v0.x; As[buf][lk + 1][lr] = v0.y; As[buf][lk + 2][lr] = v0.z; As[buf][lk + 3][lr] = v0.w;
+            As[buf][lk + 0][lr + 32] = v1.x; As[buf][lk + 1][lr + 32] = v1.y;
+            As[buf][lk + 2][lr + 32] = v1.z; As[buf][lk + 3][lr + 32] = v1.w;
+            Bs[buf][lk + 0][lr] = vb.x; Bs[buf][lk + 1][lr] = vb.y; Bs[buf][lk + 2][lr] = vb.z; Bs[buf][lk + 3][lr] = vb.w;
             __syncthreads();
+            if (sl + 1 < nsl) {
+                const int kk = (sl + 1) * GBK + lk;
+                v0 = gram_load<VEC>(pa0, kk, n);
+                v1 = gram_load<VEC>(pa1, kk, n);
+                vb = gram_load<VEC>(pb, kk, n);
+            }
 #pragma unroll 8
             for (int k = 0; k < GBK; ++k) {
-                const float x0 = As[k][ty * 2], x1 = As[k][ty * 2 + 1];
-                const float4 y = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+                const float x0 = As[buf][k][ty * 2], x1 = As[buf][k][ty * 2 + 1];
+                const float4 y = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
                 acc[0][0] = fmaf(x0, y.x, acc[0][0]); acc[0][1] = fmaf(x0, y.y, acc[0][1]);
                 acc[0][2] = fmaf(x0, y.z, acc[0][2]); acc[0][3] = fmaf(x0, y.w, acc[0][3]);
                 acc[1][0] = fmaf(x1, y.x, acc[1][0]); acc[1][1] = fmaf(x1, y.y, acc[1][1]);
                 acc[1][2] = fmaf(x1, y.z, acc[1][2]); acc[1][3] = fmaf(x1, y.w, acc[1][3]);
             }
-            __syncthreads();
         }
+        __syncthreads();
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int a = a0 + ty * 2 + u;
@@ -175,24 +176,15 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int bb = b0 + tx * 4 + v;
-                if (bb >= q) continue;
+                if (bb > q) continue;
+                if (bb == q) {
+                    if (a >= s0) d.h[(size_t)i * smax + a] = acc[u][v];  // h of the new atoms
+                    continue;
+                }
                 const int col = s0 + bb;
                 Gi[(size_t)a * smax + col] = acc[u][v];
                 Gi[(size_t)col * smax + a] = acc[u][v];
             }
-        }
-    }
-    // h for the new atoms (fixed-order warp dots), once per signal
-    if (blockIdx.y == 0) {
-        const int lane = tid & 31, warp = tid >> 5;
-        const float* b = d.B + (size_t)i * n;
-        for (int bb = warp; bb < q; bb += (blockDim.x >> 5)) {
-            const float* aj = d.A32 + (size_t)Si[s0 + bb] * n;
-            float acc = 0.f;
-            for (int k = lane; k < n; k += 32) acc = fmaf(aj[k], b[k], acc);
-#pragma unroll
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) d.h[(size_t)i * smax + s0 + bb] = acc;
         }
     }
 }
@@ -490,19 +482,23 @@ cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     return cudaGetLastError();
 }
 
+cudaError_t prepare_apg() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    const int mx = (int)(((size_t)APG_SMEM_S * APG_SMEM_S + 6 * 1024) * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_apg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
 cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     vcap = ((vcap + 31) / 32) * 32;
     if (vcap > d.smax) vcap = d.smax;
     const int gcap = vcap < APG_SMEM_S ? vcap : APG_SMEM_S;
     const size_t dyn = ((size_t)gcap * gcap + 6 * (size_t)vcap) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        const int mx = (int)(((size_t)APG_SMEM_S * APG_SMEM_S + 6 * 1024) * sizeof(float));
-        cudaError_t e = cudaFuncSetAttribute(k_apg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t ep = prepare_apg();
+    if (ep != cudaSuccess) return ep;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apg, APG_THREADS, dyn);
     if (e != cudaSuccess) return e;

@@ -36,6 +36,7 @@ MPL_OPT_INNER_MAX = 5
 MPL_OPT_WARM_START = 6
 MPL_OPT_SYNC_EVERY = 7
 MPL_OPT_PROFILE = 8
+MPL_OPT_GRAPH = 9
 
 # limits of the allocation-free entry point (include/mpl.h)
 MPL_NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -210,8 +211,8 @@ def mpl_get_solution_f64(h, p: int, X64) -> None:
 
 
 def mpl_get_phase_times(h) -> list:
-    buf = (ctypes.c_double * 8)()
-    k = load().mpl_get_phase_times(h, buf, 8)
+    buf = (ctypes.c_double * 9)()
+    k = load().mpl_get_phase_times(h, buf, 9)
     return [buf[i] for i in range(k)]
 
 
@@ -219,7 +220,8 @@ def mpl_get_launch_count(h) -> int:
     return int(load().mpl_get_launch_count(h))
 
 
-PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "spare")
+PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "corr_columns",
+          "finish_flops")
 
 
 @dataclass
@@ -239,7 +241,8 @@ class Solver:
         mpl_set_option(self.h, MPL_OPT_RHO, rho)
         mpl_set_option(self.h, MPL_OPT_PRECISION, precision)
         keys = dict(max_outer=MPL_OPT_MAX_OUTER, smax=MPL_OPT_SMAX, eps_in=MPL_OPT_EPS_IN,
-                    inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE)
+                    inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE,
+                    sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 

@@ -1,0 +1,35 @@
+"""Parity on subsets of the large workloads (the oracle solves a handful of
+their signals in seconds):
+  face-shaped [D I] dictionary (1024 x 10024, coherent class atoms + identity),
+  2048 x 32768 streaming-batch dictionary, mixed precision,
+  4096 x 65536 dictionary, mixed precision (the oracle's 64-signal subset
+  is reported by the benchmark; a few signals here)."""
+import numpy as np
+import pytest
+
+from paper_1302_5010_gb300 import synth
+from parity import check_against_oracle
+from test_gpu_parity import assert_certified, oracle_solve, solve_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_face_dictionary_subset():
+    P = synth.make_config("c4", p=32)
+    X, X64, res = solve_gpu(P, smax=512)
+    assert_certified(res)
+    check_against_oracle(P, X64, oracle_solve(P))
+
+
+def test_c5_shape_mixed_subset():
+    P = synth.make_config("c5", p=12)
+    X, X64, res = solve_gpu(P, precision=1, smax=512)
+    assert_certified(res)
+    check_against_oracle(P, X64, oracle_solve(P))
+
+
+def test_c3_shape_mixed_subset():
+    P = synth.make_config("c3", p=6)
+    X, X64, res = solve_gpu(P, precision=1, smax=1024)
+    assert_certified(res)
+    check_against_oracle(P, X64, oracle_solve(P))

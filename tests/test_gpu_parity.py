@@ -153,3 +153,21 @@ def test_empty_batch_and_bad_lambda():
     assert r.stats["status"][1] == mpl.MPL_SIG_NONFINITE
     assert r.stats["status"][0] == mpl.MPL_SIG_CERTIFIED
     s.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    """Captured-and-replayed outer iterations give the same solutions as
+    direct launches (first solve captures, second replays)."""
+    P = synth.make_config("c2", p=40)
+    Xd, X64d, rd = solve_gpu(P, graph=0)
+    torch = _torch()
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, graph=1)
+    B = torch.from_numpy(P.B).cuda()
+    lam = torch.from_numpy(P.lam).cuda()
+    for _ in range(3):
+        X = torch.empty((P.p, P.m), dtype=torch.float32, device="cuda")
+        r = s.solve(B, lam, X, TOL)
+        torch.cuda.synchronize()
+        assert_certified(r)
+        np.testing.assert_array_equal(X.cpu().numpy(), Xd)
+    s.close()
