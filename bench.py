@@ -149,40 +149,36 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="c2")
-    ap.add_argument("--path", default="plain", choices=["plain", "mixed"])
-    ap.add_argument("--ref-signals", type=int, default=64)
-    ap.add_argument("--cpu-signals", type=int, default=256)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-
+def correlation_microbench(args) -> None:
+    """The correlation GEMM alone (worst-case analysis product A^T R) on an
+    n x m dictionary and p residuals, through mpl_correlate; for profiling."""
     import torch
-    from paper_1302_5010_gb300 import mpl, synth
+    from paper_1302_5010_gb300 import mpl
+    n, m, p = args.corr_shape
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((m, n), device="cuda", generator=g)
+    A /= A.norm(dim=1, keepdim=True)
+    R = torch.randn((p, n), device="cuda", generator=g) * 0.3
+    s = mpl.Solver(A, precision=1 if args.path == "mixed" else 0)
+    C = torch.empty((p, m), device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        s.correlate(R, C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.correlate(R, C)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"microbench": "correlation", "path": args.path, "n": n, "m": m, "p": p,
+                      "ms_per_call": ms, "tflops_incl_staging": 2.0 * n * m * p / ms / 1e9}))
+    s.close()
 
-    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
 
-    # each rank its own batch of independent signals (weak scaling)
-    P = synth.make_config(args.config) if rank == 0 else synth.make_config(args.config, seed_shift=1000 * rank)
-    precision = 1 if args.path == "mixed" else 0
+def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local: int) -> dict:
+    """Warm up, then time exactly args.steps solves of the whole batch (device events, L2
+    flushed between steps), then the same through the C ABI with pinned host buffers."""
     At = torch.from_numpy(P.At).to(dev)
     B = torch.from_numpy(P.B).to(dev)
     lam = torch.from_numpy(P.lam).to(dev)
@@ -190,7 +186,6 @@ def main():
     solver = mpl.Solver(At, rho=P.rho, precision=precision)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-
     # phase timing events ride inside the captured iteration graphs; warm up with
     # the same setting so that the timed steps only replay graphs
     solver.set(mpl.MPL_OPT_PROFILE, 1)
@@ -240,7 +235,9 @@ def main():
     nbytes = lambda t: t.numel() * t.element_size()
     e2e = {"value": P.p * args.steps / e2e_s * world, "unit": UNIT,
            "h2d_bytes_per_step": int(nbytes(Bh) + nbytes(lamh)), "d2h_bytes_per_step": int(nbytes(Xh))}
-
+    stats = mpl.mpl_get_stats(solver.h, P.p)
+    solver.close()
+    del flush
     # roofline: the correlation GEMM and the exact finish are timed by events inside the
     # captured iteration graphs during the timed steps; the slower one is the dominant kernel
     pk = peaks()
@@ -272,16 +269,72 @@ def main():
         roof = dict(gemm, traffic=None)
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if k in ("correlation", "finish")}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+    return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk,
+            "certified": certified, "roofline": roof, "gemm": gemm,
+            "outer_iters_mean": float(np.mean(stats["outer_iters"])),
+            "active_size_mean": float(np.mean(stats["active_size"]))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--path", default="mixed", choices=["plain", "mixed"],
+                    help="path reported as value; the other one is timed alongside for comparison")
+    ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
+    ap.add_argument("--ref-signals", type=int, default=64)
+    ap.add_argument("--cpu-signals", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--corr-shape", type=int, nargs=3, metavar=("N", "M", "P"), default=None,
+                    help="profile the correlation GEMM alone on this shape instead of the benchmark")
+    args = ap.parse_args()
+    if args.corr_shape:
+        correlation_microbench(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1302_5010_gb300 import mpl, synth
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    # each rank its own batch of independent signals (weak scaling)
+    P = synth.make_config(args.config) if rank == 0 else synth.make_config(args.config, seed_shift=1000 * rank)
+    precision = 1 if args.path == "mixed" else 0
+    main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local)
+    names = {1: "mixed-bf16", 0: "plain-fp32"}
+    line = {"metric": METRIC, "value": main_run["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main_run["tot_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if precision == 0 else "bf16+f32", "data": "synthetic",
-            "config": workload_desc(args.config, P, "plain-fp32" if precision == 0 else "mixed-bf16"),
-            "certified_all": certified, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "roofline": roof, "correlation_gemm": gemm}
+            "config": workload_desc(args.config, P, names[precision]),
+            "certified_all": main_run["certified"], "e2e": main_run["e2e"],
+            "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
+            "roofline": main_run["roofline"], "correlation_gemm": main_run["gemm"],
+            "outer_iters_mean": main_run["outer_iters_mean"]}
+    if not args.no_compare:
+        other = timed_path(args, mpl, torch, P, dev, 1 - precision, world, dist, local)
+        line[names[1 - precision].replace("-", "_")] = {
+            "value": other["value"], "ms_per_step": other["tot_ms"] / args.steps, "e2e": other["e2e"]["value"],
+            "certified_all": other["certified"], "roofline": other["roofline"],
+            "correlation_gemm": other["gemm"], "clocks": other["clocks"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, P, args.cpu_signals)
-    solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
