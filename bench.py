@@ -176,7 +176,28 @@ def correlation_microbench(args) -> None:
     s.close()
 
 
-def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local: int) -> dict:
+def train_proposal(args, mpl, torch, solver, P_train, dev) -> dict:
+    """Offline (untimed): solve a disjoint training stream of signals with the cold
+    solver, then train the warm-start proposal on their supports."""
+    t0 = time.perf_counter()
+    Bt = torch.from_numpy(P_train.B).to(dev)
+    lt = torch.from_numpy(P_train.lam).to(dev)
+    Xt = torch.zeros((P_train.p, P_train.m), dtype=torch.float32, device=dev)
+    res = solver.solve(Bt, lt, Xt, TOL)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = solver.train_proposal(Bt, lt, Xt, epochs=args.train_epochs)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"signals": P_train.p, "solve_s": t1 - t0, "train_s": t2 - t1, "epochs": args.train_epochs,
+            "loss_first": float(losses[0]) if len(losses) else None,
+            "loss_last": float(losses[-1]) if len(losses) else None,
+            "labels_certified": bool(np.all(res.stats["status"] == mpl.MPL_SIG_CERTIFIED)),
+            "outer_iters_cold_mean": float(np.mean(res.stats["outer_iters"]))}
+
+
+def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local: int, warm: bool = False,
+               P_train=None) -> dict:
     """Warm up, then time exactly args.steps solves of the whole batch (device events, L2
     flushed between steps), then the same through the C ABI with pinned host buffers."""
     At = torch.from_numpy(P.At).to(dev)
@@ -184,6 +205,10 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     lam = torch.from_numpy(P.lam).to(dev)
     X = torch.empty((P.p, P.m), dtype=torch.float32, device=dev)
     solver = mpl.Solver(At, rho=P.rho, precision=precision)
+    training = None
+    if warm:
+        training = train_proposal(args, mpl, torch, solver, P_train, dev)
+        solver.set(mpl.MPL_OPT_WARM_START, 2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
     # phase timing events ride inside the captured iteration graphs; warm up with
@@ -270,7 +295,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if k in ("correlation", "finish")}
 
     return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk,
-            "certified": certified, "roofline": roof, "gemm": gemm,
+            "certified": certified, "roofline": roof, "gemm": gemm, "training": training,
             "outer_iters_mean": float(np.mean(stats["outer_iters"])),
             "active_size_mean": float(np.mean(stats["active_size"]))}
 
@@ -284,6 +309,9 @@ def main():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--path", default="mixed", choices=["plain", "mixed"],
                     help="path reported as value; the other one is timed alongside for comparison")
+    ap.add_argument("--no-warm", action="store_true", help="report the reported path without the learned warm start")
+    ap.add_argument("--train-signals", type=int, default=16384)
+    ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
     ap.add_argument("--ref-signals", type=int, default=64)
     ap.add_argument("--cpu-signals", type=int, default=256)
@@ -316,22 +344,25 @@ def main():
     # each rank its own batch of independent signals (weak scaling)
     P = synth.make_config(args.config) if rank == 0 else synth.make_config(args.config, seed_shift=1000 * rank)
     precision = 1 if args.path == "mixed" else 0
-    main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local)
+    warm = not args.no_warm
+    # disjoint training stream for the proposal network (same generator, other signal seed)
+    P_train = synth.make_config(args.config, p=args.train_signals, seed_shift=9000 + 1000 * rank) if warm else None
+    main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local, warm=warm, P_train=P_train)
     names = {1: "mixed-bf16", 0: "plain-fp32"}
     line = {"metric": METRIC, "value": main_run["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["tot_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if precision == 0 else "bf16+f32", "data": "synthetic",
-            "config": workload_desc(args.config, P, names[precision]),
+            "config": workload_desc(args.config, P, names[precision] + ("+warm-start" if warm else "")),
             "certified_all": main_run["certified"], "e2e": main_run["e2e"],
             "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
             "roofline": main_run["roofline"], "correlation_gemm": main_run["gemm"],
-            "outer_iters_mean": main_run["outer_iters_mean"]}
+            "outer_iters_mean": main_run["outer_iters_mean"], "warm_start_training": main_run["training"]}
     if not args.no_compare:
         other = timed_path(args, mpl, torch, P, dev, 1 - precision, world, dist, local)
         line[names[1 - precision].replace("-", "_")] = {
             "value": other["value"], "ms_per_step": other["tot_ms"] / args.steps, "e2e": other["e2e"]["value"],
-            "certified_all": other["certified"], "roofline": other["roofline"],
+            "certified_all": other["certified"], "roofline": other["roofline"], "outer_iters_mean": other["outer_iters_mean"],
             "correlation_gemm": other["gemm"], "clocks": other["clocks"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, P, args.cpu_signals)

@@ -63,8 +63,12 @@ typedef enum {
     MPL_OPT_SYNC_EVERY = 7, /* outer iterations launched per host/device handshake. default 2 */
     MPL_OPT_PROFILE = 8,    /* 1: record per-phase device times (mpl_get_phase_times) with
                                timing events, inside the captured graphs too. default 0 */
-    MPL_OPT_GRAPH = 9       /* 1: each outer iteration is replayed from a captured CUDA graph
+    MPL_OPT_GRAPH = 9,      /* 1: each outer iteration is replayed from a captured CUDA graph
                                (captured on first use per batch size and iteration). default 1 */
+    MPL_OPT_WARM_CANDIDATES = 10, /* W: atoms per signal scored by the proposal network (the W
+                                     largest |a_j^T b| of the first correlation). default 64 */
+    MPL_OPT_WARM_MAX = 11,        /* most atoms a proposal adds to a signal's set. default 3 rho */
+    MPL_OPT_WARM_THRESHOLD = 12   /* accept a candidate when its logit exceeds this. default -1 */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -162,6 +166,34 @@ mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void
 #define MPL_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define MPL_NOALLOC_MAX_SIGNALS ((int)((MPL_NOALLOC_SCRATCH_BYTES - 256u) / 4u))
 mpl_status_t mpl_correlate_noalloc(const float* A, int n, int m, const float* R, int p, float* C, void* stream);
+
+/*
+ * Learned warm start (MPL_OPT_WARM_START = 2).  A per-atom network scores the
+ * W candidates of each signal from the first correlation c = A^T b:
+ *   features (|c_j|/lambda, log(||b||/lambda), ||A^T a_j|| / sqrt(1 + m/n)),
+ *   standardised, then 64 ReLU -> 64 ReLU -> 1 logit; BF16 weights, FP32 arithmetic.
+ * The first outer iteration then adds MPL's own rho largest violators (Alg. 1,
+ * step 3) plus every candidate whose logit exceeds MPL_OPT_WARM_THRESHOLD; the
+ * loop continues unchanged to the KKT tolerance, so solutions do not depend on
+ * the proposal (atoms are never deleted, Sec. 2.2).
+ * Parameter vector (MPL_PROPOSAL_NPARAM floats): mean[3], std[3], W1[64][3],
+ * b1[64], W2[64][64], b2[64], w3[64], b3.
+ */
+#define MPL_PROPOSAL_NPARAM 4487
+mpl_status_t mpl_proposal_set_weights(mpl_handle_t h, const float* w, int count);
+mpl_status_t mpl_proposal_get_weights(mpl_handle_t h, float* w, int count);
+/* Train the network on p signals with reference solutions Xref (m x p column-major,
+ * labels = nonzeros), on the device with hand-written kernels: minibatch Adam on the
+ * binary cross-entropy, features standardised with the training set's mean and
+ * deviation.  B, lambda, Xref: device or host.  loss_out: host, epochs values (mean
+ * loss per epoch) or NULL.  Initialisation and shuffling are seeded. */
+mpl_status_t mpl_proposal_train(mpl_handle_t h, const float* B, int p, const float* lambda, const float* Xref,
+                                int epochs, double lr, int batch, uint64_t seed, float* loss_out);
+/* Mean loss and its gradient (host, MPL_PROPOSAL_NPARAM floats; zero for the
+ * normalisation constants) over the examples of (B, lambda, Xref) with the current
+ * FP32 weights; for gradient checks. */
+mpl_status_t mpl_proposal_loss_grad(mpl_handle_t h, const float* B, int p, const float* lambda, const float* Xref,
+                                    double* loss, float* grad);
 
 /* Release the handle and all its device memory.  NULL-safe. */
 void mpl_destroy(mpl_handle_t h);

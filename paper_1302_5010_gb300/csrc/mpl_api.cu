@@ -14,6 +14,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <numeric>
+#include <random>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -59,6 +61,17 @@ struct mpl_ctx {
     std::vector<GraphEntry> graphs;  // captured outer iterations, valid for the current workspace
     float* Bint = nullptr;           // fixed internal copies of B and lambda (graph parameters)
     float* lamint = nullptr;
+    // proposal network (learned warm start)
+    float* pw = nullptr;    // FP32 parameters
+    float* pwb = nullptr;   // BF16-rounded copy used for inference
+    float* pm1 = nullptr;   // Adam moments
+    float* pm2 = nullptr;
+    float* pgrad = nullptr; // gradient accumulator
+    float* pacc = nullptr;  // [0] loss sum, [1] (int) live examples
+    float* rn = nullptr;    // ||A^T a_j|| estimates (m)
+    bool prop_ready = false, rn_ready = false;
+    int warm_w = 64, warm_max = -1;  // -1: 3 rho
+    double warm_thr = -1.0;
     double eps_in = 1e-4;
     // workspace
     int cap_p = 0, cap_smax = 0;
@@ -336,6 +349,7 @@ void mpl_destroy(mpl_handle_t h) {
     cudaFree(h->Bst);
     cudaFree(h->lamst);
     cudaFree(h->Xst);
+    for (float* q : {h->pw, h->pwb, h->pm1, h->pm2, h->pgrad, h->pacc, h->rn}) cudaFree(q);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
     clear_graphs(h);
     if (h->side) cudaStreamDestroy(h->side);
@@ -378,8 +392,19 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             h->inner_max = (int)v;
             return MPL_OK;
         case MPL_OPT_WARM_START:
-            if (v != 0) return MPL_ERR_UNSUPPORTED;
-            h->warm = 0;
+            if (v != 0 && v != 2) return MPL_ERR_ARG;
+            h->warm = (int)v;
+            return MPL_OK;
+        case MPL_OPT_WARM_CANDIDATES:
+            if (v < 1 || v > SEL_THREADS) return MPL_ERR_ARG;
+            h->warm_w = (int)v;
+            return MPL_OK;
+        case MPL_OPT_WARM_MAX:
+            if (v < 1 || v > 1024) return MPL_ERR_ARG;
+            h->warm_max = (int)v;
+            return MPL_OK;
+        case MPL_OPT_WARM_THRESHOLD:
+            h->warm_thr = v;
             return MPL_OK;
         case MPL_OPT_SYNC_EVERY:
             if (v < 1 || v > 64) return MPL_ERR_ARG;
@@ -410,6 +435,9 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_SYNC_EVERY: *v = h->sync_every; return MPL_OK;
         case OPT_PROFILE: *v = h->profile; return MPL_OK;
         case MPL_OPT_GRAPH: *v = h->use_graph; return MPL_OK;
+        case MPL_OPT_WARM_CANDIDATES: *v = h->warm_w; return MPL_OK;
+        case MPL_OPT_WARM_MAX: *v = h->warm_max; return MPL_OK;
+        case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         default: return MPL_ERR_ARG;
     }
 }
@@ -430,12 +458,27 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     }
     if (pt) pt->end(1, e0, run);
     e0 = pt ? pt->begin_if(2, run) : nullptr;
-    if ((e = launch_select(d, cur, no_grow, act_ub, run, nl)) != cudaSuccess) return e;
+    if (t == 0 && h->warm == 2) {
+        // learned warm start: the first worst-case analysis also admits the atoms the
+        // proposal network accepts among the W largest correlations
+        PropArgs pa{};
+        pa.mode = SEL_PROPOSE;
+        pa.W = std::min(h->warm_w, d.m);
+        pa.cap = h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax);
+        pa.thr = (float)h->warm_thr;
+        pa.w = h->pwb;
+        pa.rn = h->rn;
+        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa)) != cudaSuccess) return e;
+    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl)) != cudaSuccess) {
+        return e;
+    }
     if ((e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(2, e0, run);
     // the exact finish touches only signals without violators: overlap it
     // with the Gram growth / master problem / residual of the others
-    const int scap = std::min(d.smax, (t + 1) * d.rho);
+    // bound on |S| after this iteration's growth: rho per iteration, plus what a warm start admits
+    const int warm_add = h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax)) : 0;
+    const int scap = std::min(d.smax, (t + 1) * d.rho + warm_add);
     if ((e = cudaEventRecord(h->ev_fork, run)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     e0 = pt ? pt->begin_if(4, h->side) : nullptr;
@@ -458,7 +501,7 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
 // active-set bound saturates share one graph per parity.
 static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, double tol, cudaStream_t run,
                                    size_t* out, int64_t* nl) {
-    const int tsat = (d.smax + d.rho - 1) / d.rho;
+    const int tsat = (d.smax + d.rho - 1) / d.rho;  // beyond this the active-set bound is smax
     const int tk = std::min(t, tsat + 1);
     const int par = t & 1, nog = t >= h->max_outer ? 1 : 0, prof = h->profile ? 1 : 0;
     for (size_t gi = 0; gi < h->graphs.size(); ++gi) {
@@ -553,6 +596,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     }
     const float* lamd = h->lamint;
 
+    if (h->warm == 2 && !h->prop_ready) return MPL_ERR_ARG;  // no proposal weights loaded
     PhaseTimer pt{h, st, {}, 0};
     cudaEvent_t t_all = pt.begin();
     CK(launch_init(d, st, &nl));
@@ -672,6 +716,239 @@ mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void
     CK(cudaStreamSynchronize(st));
     h->launches = nl;
     if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
+    return MPL_OK;
+}
+
+// ---------------------------------------------------------------- proposal network
+static cudaError_t prop_alloc(mpl_ctx* h) {
+    if (h->pw) return cudaSuccess;
+    float** bufs[] = {&h->pw, &h->pwb, &h->pm1, &h->pm2, &h->pgrad};
+    for (float** q : bufs) {
+        cudaError_t e = cudaMalloc(q, PROP_NPARAM * sizeof(float));
+        if (e != cudaSuccess) return e;
+        cudaMemset(*q, 0, PROP_NPARAM * sizeof(float));
+    }
+    cudaError_t e = cudaMalloc(&h->pacc, 4 * sizeof(float));
+    if (e != cudaSuccess) return e;
+    return cudaMalloc(&h->rn, (size_t)h->m * sizeof(float));
+}
+
+// ||A^T a_j|| by a 256-vector Rademacher sketch through the FP32 correlation kernel.
+static mpl_status_t ensure_rownorms(mpl_ctx* h, cudaStream_t st) {
+    static const int T = 256;
+    CK(prop_alloc(h));
+    if (h->rn_ready) return MPL_OK;
+    mpl_status_t ws = ensure_ws(h, std::max(h->cap_p, T));
+    if (ws != MPL_OK) return ws;
+    int64_t nl = 0;
+    Dev d = h->dv;
+    d.p = T;
+    d.A32 = h->A32;
+    CK(launch_sketch_rownorm(h->A32, h->n, h->m, T, d.R32, st, &nl));
+    CK(launch_prep_correlate(d, d.R32, st, &nl));  // identity column list (R32 copies onto itself)
+    CK(launch_corr_f32(d, 0, T, st, &nl));
+    CK(launch_rownorm(d.Cs, h->m, T, h->rn, st, &nl));
+    CK(cudaStreamSynchronize(st));
+    h->rn_ready = true;
+    return MPL_OK;
+}
+
+// Training examples for p signals: the W candidates of the first correlation with
+// their features and labels (support of the reference solutions), p x W x 4 floats.
+static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const float* lambda, const float* Xref,
+                                   std::vector<float>& ex_host, float** ex_dev) {
+    cudaStream_t st = h->main;
+    const int n = h->n, m = h->m, W = std::min(h->warm_w, m);
+    const int chunk = std::max(1, std::min(p, 1024));
+    mpl_status_t ws = ensure_ws(h, chunk);
+    if (ws != MPL_OK) return ws;
+    float* ex = nullptr;
+    float* xref = nullptr;
+    CK(cudaMalloc(&ex, (size_t)p * W * 4 * sizeof(float)));
+    CK(cudaMalloc(&xref, (size_t)chunk * m * sizeof(float)));
+    int64_t nl = 0;
+    for (int c0 = 0; c0 < p; c0 += chunk) {
+        const int pc = std::min(chunk, p - c0);
+        CK(cudaMemcpyAsync(h->Bint, B + (size_t)c0 * n, (size_t)pc * n * sizeof(float), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(h->lamint, lambda + c0, (size_t)pc * sizeof(float), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(xref, Xref + (size_t)c0 * m, (size_t)pc * m * sizeof(float), cudaMemcpyDefault, st));
+        Dev d = h->dv;
+        d.p = pc;
+        d.rho = std::min(h->rho, m);
+        d.precision = h->precision;
+        d.tol = 1e-6;
+        d.colmax = h->colmax;
+        d.A32 = h->A32;
+        d.A16 = h->A16;
+        d.B = h->Bint;
+        d.lam = h->lamint;
+        set_bounds(h, d);
+        CK(launch_init(d, st, &nl));
+        if (h->precision == 1) {
+            if (h->tmap_p != h->cap_p) {
+                CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
+                h->tmap_p = h->cap_p;
+            }
+            CK(launch_gather_r16(d, 0, pc, st, &nl));
+            CK(launch_corr_bf16(d, 0, h->tmap, pc, h->sms, st, &nl));
+        } else {
+            CK(launch_corr_f32(d, 0, pc, st, &nl));
+        }
+        PropArgs pa{};
+        pa.mode = SEL_EXAMPLES;
+        pa.W = W;
+        pa.w = h->pw;
+        pa.rn = h->rn;
+        pa.ex = ex + (size_t)c0 * W * 4;
+        pa.xref = xref;
+        CK(launch_select(d, 0, 0, pc, st, &nl, &pa));
+    }
+    ex_host.resize((size_t)p * W * 4);
+    CK(cudaMemcpyAsync(ex_host.data(), ex, ex_host.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(xref);
+    *ex_dev = ex;
+    return MPL_OK;
+}
+
+static mpl_status_t prop_setup(mpl_ctx* h) {
+    CK(cudaSetDevice(h->dev));
+    if (!h->side) {
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->main, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    }
+    if (h->precision == 1 && !h->A16) {
+        int64_t nl = 0;
+        CK(cudaMalloc(&h->A16, (size_t)h->n * h->m * sizeof(__nv_bfloat16)));
+        CK(launch_colnorm(h->A32, h->n, h->m, h->colnorm, h->A16, h->main, &nl));
+    }
+    return ensure_rownorms(h, h->main);
+}
+
+mpl_status_t mpl_proposal_set_weights(mpl_handle_t h, const float* w, int count) {
+    if (!h || !w || count != PROP_NPARAM) return MPL_ERR_ARG;
+    mpl_status_t st = prop_setup(h);
+    if (st != MPL_OK) return st;
+    int64_t nl = 0;
+    CK(cudaMemcpy(h->pw, w, PROP_NPARAM * sizeof(float), cudaMemcpyDefault));
+    CK(launch_round_bf16(h->pw, h->pwb, h->main, &nl));
+    CK(cudaStreamSynchronize(h->main));
+    h->prop_ready = true;
+    return MPL_OK;
+}
+
+mpl_status_t mpl_proposal_get_weights(mpl_handle_t h, float* w, int count) {
+    if (!h || !w || count != PROP_NPARAM || !h->pw) return MPL_ERR_ARG;
+    CK(cudaMemcpy(w, h->pw, PROP_NPARAM * sizeof(float), cudaMemcpyDefault));
+    return MPL_OK;
+}
+
+mpl_status_t mpl_proposal_train(mpl_handle_t h, const float* B, int p, const float* lambda, const float* Xref,
+                                int epochs, double lr, int batch, uint64_t seed, float* loss_out) {
+    if (!h || !B || !lambda || !Xref || p < 1 || epochs < 0 || !(lr >= 0.0) || batch < 1) return MPL_ERR_ARG;
+    mpl_status_t stt = prop_setup(h);
+    if (stt != MPL_OK) return stt;
+    cudaStream_t st = h->main;
+    std::vector<float> ex;
+    float* exd = nullptr;
+    stt = build_examples(h, B, p, lambda, Xref, ex, &exd);
+    if (stt != MPL_OK) return stt;
+    // standardisation from the live examples, seeded initialisation
+    const size_t ne = ex.size() / 4;
+    double mu[3] = {0, 0, 0}, sd[3] = {0, 0, 0};
+    std::vector<int> live;
+    double pos = 0;
+    for (size_t e = 0; e < ne; ++e) {
+        if (ex[e * 4 + 3] < 0.f) continue;
+        live.push_back((int)e);
+        for (int q = 0; q < 3; ++q) mu[q] += ex[e * 4 + q];
+        pos += ex[e * 4 + 3];
+    }
+    if (live.empty()) { cudaFree(exd); return MPL_ERR_ARG; }
+    for (int q = 0; q < 3; ++q) mu[q] /= (double)live.size();
+    for (int e : live)
+        for (int q = 0; q < 3; ++q) sd[q] += (ex[(size_t)e * 4 + q] - mu[q]) * (ex[(size_t)e * 4 + q] - mu[q]);
+    std::vector<float> w(PROP_NPARAM, 0.f);
+    for (int q = 0; q < 3; ++q) {
+        w[P_MEAN + q] = (float)mu[q];
+        w[P_STD + q] = (float)std::max(std::sqrt(sd[q] / (double)live.size()), 1e-6);
+    }
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int t = 0; t < PROP_H * 3; ++t) w[P_W1 + t] = nd(rng) * std::sqrt(2.f / 3.f);
+    for (int t = 0; t < PROP_H * PROP_H; ++t) w[P_W2 + t] = nd(rng) * std::sqrt(2.f / PROP_H);
+    for (int t = 0; t < PROP_H; ++t) w[P_W3 + t] = nd(rng) * std::sqrt(1.f / PROP_H);
+    const double prior = std::min(std::max(pos / (double)live.size(), 1e-4), 1.0 - 1e-4);
+    w[P_B3] = (float)std::log(prior / (1.0 - prior));
+    CK(cudaMemcpy(h->pw, w.data(), PROP_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemset(h->pm1, 0, PROP_NPARAM * sizeof(float)));
+    CK(cudaMemset(h->pm2, 0, PROP_NPARAM * sizeof(float)));
+    CK(cudaMemset(h->pgrad, 0, PROP_NPARAM * sizeof(float)));
+    int* perm = nullptr;
+    CK(cudaMalloc(&perm, live.size() * sizeof(int)));
+    int64_t nl = 0;
+    int step = 0;
+    const int nlive = (int)live.size();
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(live.begin(), live.end(), rng);
+        CK(cudaMemcpyAsync(perm, live.data(), live.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(h->pacc, 0, 4 * sizeof(float), st));
+        for (int off = 0; off < nlive; off += batch) {
+            const int cnt = std::min(batch, nlive - off);
+            CK(launch_train_step(h->pw, exd, perm, off, cnt, 1.f / (float)cnt, h->pgrad, h->pacc,
+                                 reinterpret_cast<int*>(h->pacc + 1), st, &nl));
+            CK(launch_adam(h->pw, h->pgrad, h->pm1, h->pm2, (float)lr, ++step, st, &nl));
+        }
+        float acc[2];
+        CK(cudaMemcpyAsync(acc, h->pacc, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int cntl;
+        std::memcpy(&cntl, &acc[1], sizeof(int));
+        if (loss_out) loss_out[ep] = cntl > 0 ? acc[0] / (float)cntl : 0.f;
+    }
+    CK(launch_round_bf16(h->pw, h->pwb, st, &nl));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(perm);
+    cudaFree(exd);
+    h->prop_ready = true;
+    clear_graphs(h);
+    return MPL_OK;
+}
+
+mpl_status_t mpl_proposal_loss_grad(mpl_handle_t h, const float* B, int p, const float* lambda, const float* Xref,
+                                    double* loss, float* grad) {
+    if (!h || !B || !lambda || !Xref || p < 1 || !loss || !grad || !h->pw) return MPL_ERR_ARG;
+    mpl_status_t stt = prop_setup(h);
+    if (stt != MPL_OK) return stt;
+    cudaStream_t st = h->main;
+    std::vector<float> ex;
+    float* exd = nullptr;
+    stt = build_examples(h, B, p, lambda, Xref, ex, &exd);
+    if (stt != MPL_OK) return stt;
+    std::vector<int> live;
+    for (size_t e = 0; e < ex.size() / 4; ++e)
+        if (ex[e * 4 + 3] >= 0.f) live.push_back((int)e);
+    int* perm = nullptr;
+    CK(cudaMalloc(&perm, std::max<size_t>(1, live.size()) * sizeof(int)));
+    CK(cudaMemcpyAsync(perm, live.data(), live.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->pgrad, 0, PROP_NPARAM * sizeof(float), st));
+    CK(cudaMemsetAsync(h->pacc, 0, 4 * sizeof(float), st));
+    int64_t nl = 0;
+    const int nlive = (int)live.size();
+    CK(launch_train_step(h->pw, exd, perm, 0, nlive, nlive > 0 ? 1.f / (float)nlive : 0.f, h->pgrad, h->pacc,
+                         reinterpret_cast<int*>(h->pacc + 1), st, &nl));
+    float acc[2];
+    CK(cudaMemcpyAsync(acc, h->pacc, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(grad, h->pgrad, PROP_NPARAM * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemset(h->pgrad, 0, PROP_NPARAM * sizeof(float)));
+    *loss = nlive > 0 ? (double)acc[0] / (double)nlive : 0.0;
+    cudaFree(perm);
+    cudaFree(exd);
     return MPL_OK;
 }
 

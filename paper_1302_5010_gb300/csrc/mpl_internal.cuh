@@ -84,6 +84,28 @@ struct Dev {
     __device__ const int* act_of(int c) const { return act[c]; }
 };
 
+// ---------------------------------------------------------------- proposal network
+// Per-atom warm-start proposal: features (|c_j|/lambda, log(||r||/lambda), ||A^T a_j|| /
+// sqrt(1 + m/n)) -> standardised -> 64 ReLU -> 64 ReLU -> 1 logit.  Parameter vector
+// layout (FP32 master copy; inference reads the BF16-rounded values):
+constexpr int PROP_H = 64;
+constexpr int P_MEAN = 0, P_STD = 3, P_W1 = 6, P_B1 = P_W1 + PROP_H * 3, P_W2 = P_B1 + PROP_H,
+              P_B2 = P_W2 + PROP_H * PROP_H, P_W3 = P_B2 + PROP_H, P_B3 = P_W3 + PROP_H,
+              PROP_NPARAM = P_B3 + 1;  // 4487
+constexpr int PROP_FIRST_TRAINABLE = P_W1;
+
+enum SelMode : int { SEL_NORMAL = 0, SEL_PROPOSE = 1, SEL_EXAMPLES = 2 };
+struct PropArgs {
+    int mode;          // SelMode
+    int W;             // candidates per signal (top-W by the re-scored |c_j|)
+    int cap;           // most atoms a proposal may add
+    float thr;         // accept when logit > thr
+    const float* w;    // parameters (PROP_NPARAM), BF16-rounded for inference
+    const float* rn;   // ||A^T a_j|| (m)
+    float* ex;         // examples out: p x W x 4 (features, label; label -1 = empty slot)
+    const float* xref; // reference solutions (p x m), labels = nonzeros
+};
+
 // ---------------------------------------------------------------- launchers
 // Each returns the CUDA error of its launch and adds its launches to *nl.
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
@@ -94,7 +116,8 @@ cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16,
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms,
                              cudaStream_t s, int64_t* nl);
 cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
-cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl);
+cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
+                          const PropArgs* pa = nullptr);
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
@@ -106,6 +129,14 @@ cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, 
 cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
                            cudaStream_t s, int64_t* nl);
 cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl);
+
+// Proposal network support (proposal.cu).
+cudaError_t launch_sketch_rownorm(const float* A32, int n, int m, int T, float* Z, cudaStream_t s, int64_t* nl);
+cudaError_t launch_rownorm(const float* C, int m, int T, float* rn, cudaStream_t s, int64_t* nl);
+cudaError_t launch_train_step(const float* w, const float* ex, const int* perm, int off, int count, float inv_batch,
+                              float* grad, float* loss_acc, int* n_acc, cudaStream_t s, int64_t* nl);
+cudaError_t launch_adam(float* w, float* grad, float* m1, float* m2, float lr, int step, cudaStream_t s, int64_t* nl);
+cudaError_t launch_round_bf16(const float* w, float* wb, cudaStream_t s, int64_t* nl);
 
 // One-time kernel attribute set-up (call before any stream capture).
 cudaError_t prepare_select();

@@ -186,7 +186,34 @@ __device__ void sort_desc(SelSmem& sh, int len) {
     }
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_grow) {
+// Proposal network forward pass for one candidate (weights in shared memory).
+__device__ float prop_logit(const float* w, float f0, float f1, float f2) {
+    const float x0 = (f0 - w[P_MEAN + 0]) / w[P_STD + 0];
+    const float x1 = (f1 - w[P_MEAN + 1]) / w[P_STD + 1];
+    const float x2 = (f2 - w[P_MEAN + 2]) / w[P_STD + 2];
+    float h1[PROP_H];
+#pragma unroll
+    for (int o = 0; o < PROP_H; ++o) {
+        const float* r = w + P_W1 + o * 3;
+        h1[o] = fmaxf(w[P_B1 + o] + r[0] * x0 + r[1] * x1 + r[2] * x2, 0.f);
+    }
+    float z = w[P_B3];
+    for (int o = 0; o < PROP_H; ++o) {
+        const float* r = w + P_W2 + o * PROP_H;
+        float a = w[P_B2 + o];
+#pragma unroll
+        for (int q = 0; q < PROP_H; ++q) a = fmaf(r[q], h1[q], a);
+        z = fmaf(w[P_W3 + o], fmaxf(a, 0.f), z);
+    }
+    return z;
+}
+
+__device__ __forceinline__ unsigned ordered_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_grow, PropArgs pa) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -211,7 +238,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     __syncthreads();
 
     const int ss = d.ssize[i];
-    const int kth = min(d.rho, m);
+    const bool prop = pa.mode != SEL_NORMAL;
+    const int kth = prop ? min(pa.W, m) : min(d.rho, m);
     bool exact_scores = false;  // row holds re-scores themselves (overflow fallback)
     unsigned kc = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -219,7 +247,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
         const bool cache = m <= SEL_ROWCACHE;
         const unsigned kkey = radix_kth(row, msk, m, kth, sh, cache);
         const float s_rho = __uint_as_float(kkey);
-        float tau = fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
+        float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
         kc = collect(cache ? sh.row : row, msk, m, tkey, sh);
@@ -260,6 +288,91 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     }
     if (lane == 0 && offmax > 0.f) atomicMax(reinterpret_cast<unsigned*>(&sh.offmax), __float_as_uint(offmax));
     __syncthreads();
+    if (prop) {
+        // --- warm-start proposal / training examples: the top-W candidates by re-score
+        float* wsm = reinterpret_cast<float*>(smem_raw + sizeof(SelSmem));
+        for (int t = tid; t < PROP_NPARAM; t += blockDim.x) wsm[t] = pa.w ? pa.w[t] : 0.f;
+        for (unsigned c = tid; c < kc; c += blockDim.x)
+            sh.key[c] = ((unsigned long long)__float_as_uint(fabsf(sh.sc[c])) << 32) |
+                        (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
+        int len2 = 1;
+        while (len2 < (int)kc) len2 <<= 1;
+        for (int t = kc + tid; t < len2; t += blockDim.x) sh.key[t] = 0ull;
+        __syncthreads();
+        if (kc > 1) sort_desc(sh, len2);
+        const int W = min((int)kc, pa.W);
+        const float f1 = logf(fmaxf(rn, 1e-30f) / lam);
+        const float gscale = rsqrtf(1.f + (float)m / (float)n);
+        // logits (or examples) for the W candidates, in score order
+        for (int r = tid; r < W; r += blockDim.x) {
+            const unsigned long long k = sh.key[r];
+            const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+            const float c32 = __uint_as_float((unsigned)(k >> 32));
+            const float f0 = c32 / lam, f2 = (pa.rn ? pa.rn[j] : 1.f) * gscale;
+            if (pa.mode == SEL_EXAMPLES) {
+                float* e = pa.ex + ((size_t)i * pa.W + r) * 4;
+                e[0] = f0; e[1] = f1; e[2] = f2;
+                e[3] = pa.xref[(size_t)i * m + j] != 0.f ? 1.f : 0.f;
+            } else {
+                sh.sc[r] = prop_logit(wsm, f0, f1, f2);
+                sh.idx[r] = j;
+            }
+        }
+        if (pa.mode == SEL_EXAMPLES) {
+            for (int r = W + tid; r < pa.W; r += blockDim.x) pa.ex[((size_t)i * pa.W + r) * 4 + 3] = -1.f;
+            return;
+        }
+        __syncthreads();
+        // tier 1: MPL's own rho largest violators (the first candidates with c > lambda);
+        // tier 2: the others the network accepts, by logit
+        int nv = 0;
+        for (int r = 0; r < W && nv < d.rho; ++r)
+            if (__uint_as_float((unsigned)(sh.key[r] >> 32)) > lam_sel) ++nv; else break;
+        __syncthreads();
+        if (tid == 0) sh.vc = 0;
+        __syncthreads();
+        for (int r = nv + tid; r < W; r += blockDim.x) {
+            if (sh.sc[r] > pa.thr) {
+                const unsigned pos = atomicAdd(&sh.vc, 1u);
+                sh.key[SEL_KCAP / 2 + pos] = ((unsigned long long)ordered_bits(sh.sc[r]) << 32) |
+                                             (unsigned long long)(0xffffffffu - (unsigned)sh.idx[r]);
+            }
+        }
+        __syncthreads();
+        // tier-1 atoms into the front of key[] (score order), tier 2 sorted by logit
+        unsigned long long t1key[1];
+        (void)t1key;
+        const int n2 = (int)sh.vc;
+        int len3 = 1;
+        while (len3 < n2) len3 <<= 1;
+        // move tier 2 into key[0..] for sorting, tier-1 indices saved in idx[] copies
+        for (int t = tid; t < nv; t += blockDim.x) sh.sc[SEL_KCAP / 2 + t] = __int_as_float(sh.idx[t]);
+        __syncthreads();
+        for (int t = tid; t < len3; t += blockDim.x) sh.key[t] = t < n2 ? sh.key[SEL_KCAP / 2 + t] : 0ull;
+        __syncthreads();
+        if (n2 > 1) sort_desc(sh, len3);
+        if (tid == 0) {
+            d.outer[i] += 1;
+            int q = 0;
+            const int room = min(d.smax - ss, pa.cap);
+            int* Si = d.S + (size_t)i * d.smax;
+            float* xi = d.xS + (size_t)i * d.smax;
+            uint32_t* mw = d.mask + (size_t)i * d.mw;
+            for (int t = 0; t < nv + n2 && q < room; ++t) {
+                const int j = t < nv ? __float_as_int(sh.sc[SEL_KCAP / 2 + t])
+                                     : (int)(0xffffffffu - (unsigned)(sh.key[t - nv] & 0xffffffffull));
+                Si[ss + q] = j;
+                xi[ss + q] = 0.f;
+                mw[j >> 5] |= 1u << (j & 31);
+                ++q;
+            }
+            d.ssize[i] = ss + q;
+            d.snew[i] = q;
+            d.state[i] = q > 0 ? ST_GROW : ST_FINALIZE;
+            if (q > 0) d.finalized[i] = 0;
+        }
+        return;
+    }
     // Sort keys: (re-score bits, inverted index) so that larger scores come
     // first and the lower index wins ties.
     for (unsigned c = tid; c < kc; c += blockDim.x) {
@@ -384,17 +497,21 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
 cudaError_t prepare_select() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SelSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(SelSmem) + PROP_NPARAM * sizeof(float)));
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
-cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl) {
+cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
+                          const PropArgs* pa) {
     if (act_n_ub <= 0) return cudaSuccess;
-    const size_t sm = sizeof(SelSmem);
+    PropArgs a{};
+    if (pa) a = *pa;
+    const size_t sm = sizeof(SelSmem) + (a.mode != SEL_NORMAL ? PROP_NPARAM * sizeof(float) : 0);
     cudaError_t e = prepare_select();
     if (e != cudaSuccess) return e;
-    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow);
+    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a);
     ++*nl;
     return cudaGetLastError();
 }

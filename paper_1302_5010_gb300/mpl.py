@@ -37,6 +37,10 @@ MPL_OPT_WARM_START = 6
 MPL_OPT_SYNC_EVERY = 7
 MPL_OPT_PROFILE = 8
 MPL_OPT_GRAPH = 9
+MPL_OPT_WARM_CANDIDATES = 10
+MPL_OPT_WARM_MAX = 11
+MPL_OPT_WARM_THRESHOLD = 12
+MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
 MPL_NOALLOC_SCRATCH_BYTES = 1 << 20
@@ -51,7 +55,8 @@ MPL_SIG_NONFINITE = 4
 
 EXPORTED = ("mpl_create", "bmpl_solve", "mpl_correlate", "mpl_destroy", "mpl_set_option", "mpl_get_option",
             "mpl_get_stats", "mpl_get_solution_f64", "mpl_get_phase_times", "mpl_get_launch_count",
-            "mpl_status_string", "mpl_correlate_noalloc")
+            "mpl_status_string", "mpl_correlate_noalloc", "mpl_proposal_set_weights",
+            "mpl_proposal_get_weights", "mpl_proposal_train", "mpl_proposal_loss_grad")
 
 
 class SignalStats(ctypes.Structure):
@@ -93,6 +98,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mpl_correlate.restype = i32
     lib.mpl_correlate_noalloc.argtypes = [vp, i32, i32, vp, i32, vp, vp]
     lib.mpl_correlate_noalloc.restype = i32
+    lib.mpl_proposal_set_weights.argtypes = [vp, vp, i32]
+    lib.mpl_proposal_set_weights.restype = i32
+    lib.mpl_proposal_get_weights.argtypes = [vp, vp, i32]
+    lib.mpl_proposal_get_weights.restype = i32
+    lib.mpl_proposal_train.argtypes = [vp, vp, i32, vp, vp, i32, f64, i32, ctypes.c_uint64, vp]
+    lib.mpl_proposal_train.restype = i32
+    lib.mpl_proposal_loss_grad.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(f64), vp]
+    lib.mpl_proposal_loss_grad.restype = i32
     lib.mpl_destroy.argtypes = [vp]
     lib.mpl_destroy.restype = None
     lib.mpl_set_option.argtypes = [vp, i32, f64]
@@ -196,6 +209,39 @@ def mpl_correlate_noalloc(A, n: int, m: int, R, p: int, C, stream=None) -> int:
                                             _stream_ptr(stream)))
 
 
+def mpl_proposal_set_weights(h, w) -> None:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    rc = load().mpl_proposal_set_weights(h, _ptr(w), int(w.size))
+    if rc != MPL_OK:
+        raise MplError(rc, "mpl_proposal_set_weights")
+
+
+def mpl_proposal_get_weights(h) -> np.ndarray:
+    w = np.zeros(MPL_PROPOSAL_NPARAM, dtype=np.float32)
+    rc = load().mpl_proposal_get_weights(h, _ptr(w), int(w.size))
+    if rc != MPL_OK:
+        raise MplError(rc, "mpl_proposal_get_weights")
+    return w
+
+
+def mpl_proposal_train(h, B, p: int, lam, Xref, epochs: int, lr: float, batch: int, seed: int) -> np.ndarray:
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    rc = load().mpl_proposal_train(h, _ptr(B), int(p), _ptr(lam), _ptr(Xref), int(epochs), float(lr), int(batch),
+                                   ctypes.c_uint64(seed), _ptr(losses))
+    if rc != MPL_OK:
+        raise MplError(rc, "mpl_proposal_train")
+    return losses[:epochs]
+
+
+def mpl_proposal_loss_grad(h, B, p: int, lam, Xref):
+    g = np.zeros(MPL_PROPOSAL_NPARAM, dtype=np.float32)
+    loss = ctypes.c_double()
+    rc = load().mpl_proposal_loss_grad(h, _ptr(B), int(p), _ptr(lam), _ptr(Xref), ctypes.byref(loss), _ptr(g))
+    if rc != MPL_OK:
+        raise MplError(rc, "mpl_proposal_loss_grad")
+    return loss.value, g
+
+
 def mpl_get_stats(h, p: int) -> dict:
     arr = (SignalStats * max(p, 1))()
     rc = load().mpl_get_stats(h, int(p), arr)
@@ -242,7 +288,8 @@ class Solver:
         mpl_set_option(self.h, MPL_OPT_PRECISION, precision)
         keys = dict(max_outer=MPL_OPT_MAX_OUTER, smax=MPL_OPT_SMAX, eps_in=MPL_OPT_EPS_IN,
                     inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE,
-                    sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH)
+                    sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
+                    warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 
@@ -253,6 +300,12 @@ class Solver:
         p = B.shape[0]
         rc = bmpl_solve(self.h, B, p, lam, X, tol, stream)
         return SolveResult(rc, mpl_get_stats(self.h, p))
+
+    def train_proposal(self, B, lam, Xref, epochs: int = 4, lr: float = 3e-3, batch: int = 2048,
+                       seed: int = 9000) -> np.ndarray:
+        """Train the warm-start proposal on signals B (p, n) with reference solutions
+        Xref (p, m); returns the mean loss per epoch."""
+        return mpl_proposal_train(self.h, B, B.shape[0], lam, Xref, epochs, lr, batch, seed)
 
     def correlate(self, R, C, stream=None) -> None:
         mpl_correlate(self.h, R, R.shape[0], C, stream)
