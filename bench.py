@@ -96,6 +96,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_problem(synth, cfg: str, rank: int, p=None, seed_shift: int = 0):
+    """Rank r's batch: the shared dictionary and its own signals (the generator's signal
+    seed moves by 1000 per rank), so the ranks solve disjoint independent problems."""
+    return synth.make_config(cfg, p=p, seed_shift=seed_shift + 1000 * rank)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """Slowest rank's figure (seconds or ms); x itself on one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, p: int, steps: int, seconds: float) -> float:
+    """Whole-job signals/s: every rank solved p signals per step."""
+    return world * p * steps / seconds
+
+
 def peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -240,12 +261,8 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    tot_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * P.p * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
+    value = aggregate_rate(world, P.p, args.steps, tot_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     Bh = torch.from_numpy(P.B).pin_memory()
@@ -253,12 +270,14 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     Xh = torch.zeros((P.p, P.m), dtype=torch.float32).pin_memory()
     mpl.bmpl_solve(solver.h, Bh, P.p, lamh, Xh, TOL, stream)  # same graphs, staged inputs
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         mpl.bmpl_solve(solver.h, Bh, P.p, lamh, Xh, TOL, stream)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     nbytes = lambda t: t.numel() * t.element_size()
-    e2e = {"value": P.p * args.steps / e2e_s * world, "unit": UNIT,
+    e2e = {"value": aggregate_rate(world, P.p, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(nbytes(Bh) + nbytes(lamh)), "d2h_bytes_per_step": int(nbytes(Xh))}
     stats = mpl.mpl_get_stats(solver.h, P.p)
     solver.close()
@@ -292,7 +311,8 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
                 "ms_per_step": fin_ms, "flop_per_step": fin_flops}
     else:
         roof = dict(gemm, traffic=None)
-    roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if k in ("correlation", "finish")}
+    # summed event times per phase (the finish runs on a second stream, so phases overlap)
+    roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items()}
 
     return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk,
             "certified": certified, "roofline": roof, "gemm": gemm, "training": training,
@@ -342,11 +362,11 @@ def main():
     dev = torch.device("cuda", local)
 
     # each rank its own batch of independent signals (weak scaling)
-    P = synth.make_config(args.config) if rank == 0 else synth.make_config(args.config, seed_shift=1000 * rank)
+    P = rank_problem(synth, args.config, rank)
     precision = 1 if args.path == "mixed" else 0
     warm = not args.no_warm
     # disjoint training stream for the proposal network (same generator, other signal seed)
-    P_train = synth.make_config(args.config, p=args.train_signals, seed_shift=9000 + 1000 * rank) if warm else None
+    P_train = rank_problem(synth, args.config, rank, p=args.train_signals, seed_shift=9000) if warm else None
     main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local, warm=warm, P_train=P_train)
     names = {1: "mixed-bf16", 0: "plain-fp32"}
     line = {"metric": METRIC, "value": main_run["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -340,8 +340,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
         }
         __syncthreads();
         // tier-1 atoms into the front of key[] (score order), tier 2 sorted by logit
-        unsigned long long t1key[1];
-        (void)t1key;
         const int n2 = (int)sh.vc;
         int len3 = 1;
         while (len3 < n2) len3 <<= 1;
