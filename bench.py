@@ -312,7 +312,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     else:
         roof = dict(gemm, traffic=None)
     # summed event times per phase (the finish runs on a second stream, so phases overlap)
-    roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items()}
+    roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if v > 0}
 
     return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk,
             "certified": certified, "roofline": roof, "gemm": gemm, "training": training,

@@ -203,6 +203,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     d.mw = mw;
     CK(prepare_select());
     CK(prepare_apg());
+    CK(prepare_gram());
     CK(prepare_finish());
     CK(prepare_corr_bf16());
     h->cap_p = P;

@@ -141,6 +141,7 @@ cudaError_t launch_round_bf16(const float* w, float* wb, cudaStream_t s, int64_t
 // One-time kernel attribute set-up (call before any stream capture).
 cudaError_t prepare_select();
 cudaError_t prepare_apg();
+cudaError_t prepare_gram();
 cudaError_t prepare_finish();
 cudaError_t prepare_corr_bf16();
 

@@ -32,6 +32,7 @@ __device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const
                                               int n, int lane) {
     float acc = 0.f;
     if ((n & 3) == 0) {
+#pragma unroll 8
         for (int k = lane * 4; k < n; k += 128) {
             const float4 av = __ldg(reinterpret_cast<const float4*>(a + k));
             const float4 rv = __ldg(reinterpret_cast<const float4*>(r + k));
@@ -65,6 +66,8 @@ struct SelSmem {
     int idx[SEL_KCAP];                 // candidate atoms
     float sc[SEL_KCAP];                // their re-scores, negated for non-violators
     float row[SEL_ROWCACHE];           // the signal's score row (when m fits)
+    uint32_t mk[SEL_ROWCACHE / 32];    // and its membership bitmap
+    unsigned wsum[32];                 // per-warp partial sums of the histogram scan
     unsigned kc;                       // candidates collected
     unsigned vc;                       // violators
     unsigned bin, need;
@@ -83,59 +86,74 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
     return u;
 }
 
-// Key of the kth largest score (1-based) among the m keys, by 3 radix passes
-// over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.
-__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh, bool fill) {
+// Copy the score row and the membership bitmap into shared memory (loads
+// batched eight deep so that they are in flight together).
+__device__ void fill_cache(const float* row, const uint32_t* msk, int m, int mw, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j0 = tid; j0 < m; j0 += 8 * nt) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u * nt;
+            v[u] = j < m ? row[j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u * nt;
+            if (j < m) sh.row[j] = v[u];
+        }
+    }
+    for (int w = tid; w < mw; w += nt) sh.mk[w] = msk[w];
+    __syncthreads();
+}
+
+// Key of the kth largest score (1-based) among the m keys, by 3 radix passes
+// over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.  The bin
+// holding the kth key is found by a block-wide suffix sum over the histogram
+// (each thread owns nb / blockDim.x consecutive bins).
+__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     unsigned prefix = 0, pmask = 0;
     unsigned need = (unsigned)kth;
-    const int shifts[3] = {21, 10, 0};
-    const int widths[3] = {11, 11, 10};
     for (int pass = 0; pass < 3; ++pass) {
-        const int nb = 1 << widths[pass];
-        const int sh_ = shifts[pass];
+        const int nb = pass < 2 ? 2048 : 1024;          // 11, 11, 10 bits
+        const int sh_ = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
         for (int b = tid; b < nb; b += nt) sh.hist[b] = 0;
         __syncthreads();
         int nf = 0;
-        const float* src = (pass > 0 && fill) ? sh.row : row;
+#pragma unroll 4
         for (int j = tid; j < m; j += nt) {
-            if (pass == 0 && fill) sh.row[j] = row[j];
-            const unsigned kj = key_of(src, msk, j, &nf);
+            const unsigned kj = key_of(row, msk, j, &nf);
             if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
         }
         if (nf) sh.nonfinite = 1;
         __syncthreads();
-        if (tid < 32) {
-            const int lane = tid;
-            const int per = nb / 32;
-            unsigned own = 0;
-            for (int b = 0; b < per; ++b) own += sh.hist[lane * per + b];
-            // inclusive suffix sum over lanes (lane 31 holds the largest bins)
-            unsigned suf = own;
+        const int per = nb / nt;  // 4 or 2 consecutive bins per thread
+        unsigned own = 0;
+        for (int b = 0; b < per; ++b) own += sh.hist[tid * per + b];
+        // inclusive suffix sum over the block (higher threads hold larger keys)
+        unsigned suf = own;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
-                if (lane + o < 32) suf += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
+            if (lane + o < 32) suf += v;
+        }
+        if (lane == 0) sh.wsum[warp] = suf;  // the warp's total
+        __syncthreads();
+        for (int w = warp + 1; w < nw; ++w) suf += sh.wsum[w];
+        const unsigned above = suf - own;  // keys in bins above this thread's
+        if (tid == 0) { sh.bin = 0; sh.need = need; }
+        __syncthreads();
+        if (above < need && suf >= need) {  // at most one thread
+            unsigned cum = above;
+            int b = per - 1;
+            for (; b > 0; --b) {
+                const unsigned c = sh.hist[tid * per + b];
+                if (cum + c >= need) break;
+                cum += c;
             }
-            const unsigned above = suf - own;  // counts in lanes > lane
-            const bool hit = (above < need) && (suf >= need);
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (bal == 0u) {
-                if (lane == 0) { sh.bin = 0; sh.need = need; }
-            } else {
-                const int hl = 31 - __clz(bal);  // the unique hitting lane
-                if (lane == hl) {
-                    unsigned cum = above;
-                    int b = per - 1;
-                    for (; b > 0; --b) {
-                        const unsigned c = sh.hist[lane * per + b];
-                        if (cum + c >= need) break;
-                        cum += c;
-                    }
-                    sh.bin = (unsigned)(lane * per + b);
-                    sh.need = need - cum;
-                }
-            }
+            sh.bin = (unsigned)(tid * per + b);
+            sh.need = need - cum;
         }
         __syncthreads();
         prefix |= sh.bin << sh_;
@@ -186,24 +204,39 @@ __device__ void sort_desc(SelSmem& sh, int len) {
     }
 }
 
-// Proposal network forward pass for one candidate (weights in shared memory).
-__device__ float prop_logit(const float* w, float f0, float f1, float f2) {
+// Proposal network forward pass for one candidate by one warp (weights in
+// shared memory, W2 stored transposed so that lane o reads W2[o][q] without
+// bank conflicts).  Lane l holds hidden units l and l + 32; every lane returns
+// the logit, summed in the unit order 0..63.
+__device__ float prop_logit_warp(const float* w, float f0, float f1, float f2, int lane) {
     const float x0 = (f0 - w[P_MEAN + 0]) / w[P_STD + 0];
     const float x1 = (f1 - w[P_MEAN + 1]) / w[P_STD + 1];
     const float x2 = (f2 - w[P_MEAN + 2]) / w[P_STD + 2];
-    float h1[PROP_H];
+    float h1[2], a2[2];
 #pragma unroll
-    for (int o = 0; o < PROP_H; ++o) {
+    for (int u = 0; u < 2; ++u) {
+        const int o = lane + 32 * u;
         const float* r = w + P_W1 + o * 3;
-        h1[o] = fmaxf(w[P_B1 + o] + r[0] * x0 + r[1] * x1 + r[2] * x2, 0.f);
+        h1[u] = fmaxf(w[P_B1 + o] + r[0] * x0 + r[1] * x1 + r[2] * x2, 0.f);
+        a2[u] = w[P_B2 + o];
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) {
+            const int q = 32 * u + l;
+            const float hq = __shfl_sync(0xffffffffu, h1[u], l);
+            a2[0] = fmaf(w[P_W2 + q * PROP_H + lane], hq, a2[0]);
+            a2[1] = fmaf(w[P_W2 + q * PROP_H + lane + 32], hq, a2[1]);
+        }
     }
     float z = w[P_B3];
-    for (int o = 0; o < PROP_H; ++o) {
-        const float* r = w + P_W2 + o * PROP_H;
-        float a = w[P_B2 + o];
 #pragma unroll
-        for (int q = 0; q < PROP_H; ++q) a = fmaf(r[q], h1[q], a);
-        z = fmaf(w[P_W3 + o], fmaxf(a, 0.f), z);
+    for (int u = 0; u < 2; ++u) {
+        for (int l = 0; l < 32; ++l) {
+            const float ao = __shfl_sync(0xffffffffu, a2[u], l);
+            z = fmaf(w[P_W3 + 32 * u + l], fmaxf(ao, 0.f), z);
+        }
     }
     return z;
 }
@@ -213,7 +246,7 @@ __device__ __forceinline__ unsigned ordered_bits(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_grow, PropArgs pa) {
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -245,12 +278,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     for (int attempt = 0; attempt < 2; ++attempt) {
         const float D = exact_scores ? 0.f : delta + delta32;
         const bool cache = m <= SEL_ROWCACHE;
-        const unsigned kkey = radix_kth(row, msk, m, kth, sh, cache);
+        if (cache) fill_cache(row, msk, m, d.mw, sh);
+        const uint32_t* mskc = cache ? sh.mk : msk;
+        const unsigned kkey = radix_kth(cache ? sh.row : row, mskc, m, kth, sh);
         const float s_rho = __uint_as_float(kkey);
         float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
-        kc = collect(cache ? sh.row : row, msk, m, tkey, sh);
+        kc = collect(cache ? sh.row : row, mskc, m, tkey, sh);
         if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
         // Too many candidates in the band: re-score every atom outside S in place
         // (this row is private to the signal) and select on the re-scores.
@@ -291,7 +326,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
     if (prop) {
         // --- warm-start proposal / training examples: the top-W candidates by re-score
         float* wsm = reinterpret_cast<float*>(smem_raw + sizeof(SelSmem));
-        for (int t = tid; t < PROP_NPARAM; t += blockDim.x) wsm[t] = pa.w ? pa.w[t] : 0.f;
+        for (int t = tid; t < PROP_NPARAM; t += blockDim.x) {
+            int dst = t;
+            if (t >= P_W2 && t < P_W2 + PROP_H * PROP_H) {  // W2 transposed
+                const int o = (t - P_W2) / PROP_H, q = (t - P_W2) % PROP_H;
+                dst = P_W2 + q * PROP_H + o;
+            }
+            wsm[dst] = pa.w ? pa.w[t] : 0.f;
+        }
         for (unsigned c = tid; c < kc; c += blockDim.x)
             sh.key[c] = ((unsigned long long)__float_as_uint(fabsf(sh.sc[c])) << 32) |
                         (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
@@ -304,18 +346,22 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Dev d, int cur, int no_g
         const float f1 = logf(fmaxf(rn, 1e-30f) / lam);
         const float gscale = rsqrtf(1.f + (float)m / (float)n);
         // logits (or examples) for the W candidates, in score order
-        for (int r = tid; r < W; r += blockDim.x) {
-            const unsigned long long k = sh.key[r];
-            const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
-            const float c32 = __uint_as_float((unsigned)(k >> 32));
-            const float f0 = c32 / lam, f2 = (pa.rn ? pa.rn[j] : 1.f) * gscale;
-            if (pa.mode == SEL_EXAMPLES) {
+        if (pa.mode == SEL_EXAMPLES) {
+            for (int r = tid; r < W; r += blockDim.x) {
+                const unsigned long long k = sh.key[r];
+                const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+                const float c32 = __uint_as_float((unsigned)(k >> 32));
                 float* e = pa.ex + ((size_t)i * pa.W + r) * 4;
-                e[0] = f0; e[1] = f1; e[2] = f2;
+                e[0] = c32 / lam; e[1] = f1; e[2] = (pa.rn ? pa.rn[j] : 1.f) * gscale;
                 e[3] = pa.xref[(size_t)i * m + j] != 0.f ? 1.f : 0.f;
-            } else {
-                sh.sc[r] = prop_logit(wsm, f0, f1, f2);
-                sh.idx[r] = j;
+            }
+        } else {
+            for (int r = warp; r < W; r += nwarps) {
+                const unsigned long long k = sh.key[r];
+                const int j = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
+                const float c32 = __uint_as_float((unsigned)(k >> 32));
+                const float z = prop_logit_warp(wsm, c32 / lam, f1, (pa.rn ? pa.rn[j] : 1.f) * gscale, lane);
+                if (lane == 0) { sh.sc[r] = z; sh.idx[r] = j; }
             }
         }
         if (pa.mode == SEL_EXAMPLES) {

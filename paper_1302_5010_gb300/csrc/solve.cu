@@ -189,6 +189,104 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
     }
 }
 
+// Same tile and per-output summation order (k ascending, one FMA chain) as
+// k_gram, with the K slices staged by cp.async in a GS-deep ring so that
+// GS - 1 slices are in flight while one is consumed (the kernel is bound by the
+// latency of its L2 reads, not by its FLOPs).  Needs n % 4 == 0 (16-byte rows).
+constexpr int GS = 4, GPAD = GBK + 4;
+constexpr size_t GRAM_SMEM = (size_t)GS * (GBM + GBN) * GPAD * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(256) k_gram_async(Dev d) {
+    const int g = blockIdx.x;
+    if (g >= d.cnt->grow_n) return;
+    const int i = d.list_grow[g];
+    const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
+    const int a0 = blockIdx.y * GBM;
+    if (a0 >= s || q == 0) return;
+    const int n = d.n, smax = d.smax;
+    const int* Si = d.S + (size_t)i * smax;
+    float* Gi = d.G + (size_t)i * smax * smax;
+    extern __shared__ __align__(16) float gsm[];
+    float* As = gsm;                          // [GS][GBM][GPAD]
+    float* Bs = gsm + (size_t)GS * GBM * GPAD;  // [GS][GBN][GPAD]
+    const int tid = threadIdx.x;
+    const int ty = tid >> 3, tx = tid & 7;
+    // the three 16-byte chunks this thread stages per slice: A rows lr and lr + 32, B row lr
+    const int lr = tid >> 3, kc = (tid & 7) * 4;
+    const int nsl = (n + GBK - 1) / GBK;
+    for (int b0 = 0; b0 <= q; b0 += GBN) {
+        const int ra0 = a0 + lr, ra1 = a0 + lr + 32, rb = b0 + lr;
+        const float* pa0 = ra0 < s ? d.A32 + (size_t)Si[ra0] * n : nullptr;
+        const float* pa1 = ra1 < s ? d.A32 + (size_t)Si[ra1] * n : nullptr;
+        const float* pb = rb < q ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+        auto issue = [&](int sl) {
+            const int st = sl % GS, k = sl * GBK + kc;
+            const bool kin = k < n;
+            float* da = As + ((size_t)st * GBM + lr) * GPAD + kc;
+            float* db = Bs + ((size_t)st * GBN + lr) * GPAD + kc;
+            cp_async16(da, (pa0 && kin) ? pa0 + k : d.A32, (pa0 && kin) ? 16 : 0);
+            cp_async16(da + 32 * GPAD, (pa1 && kin) ? pa1 + k : d.A32, (pa1 && kin) ? 16 : 0);
+            cp_async16(db, (pb && kin) ? pb + k : d.A32, (pb && kin) ? 16 : 0);
+        };
+#pragma unroll
+        for (int sl = 0; sl < GS - 1; ++sl) {
+            if (sl < nsl) issue(sl);
+            cp_async_commit();
+        }
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int sl = 0; sl < nsl; ++sl) {
+            cp_async_wait<GS - 2>();
+            __syncthreads();
+            if (sl + GS - 1 < nsl) issue(sl + GS - 1);
+            cp_async_commit();
+            const int st = sl % GS;
+            const float* Ar0 = As + ((size_t)st * GBM + ty * 2) * GPAD;
+            const float* Ar1 = Ar0 + GPAD;
+            const float* Bt = Bs + ((size_t)st * GBN + tx) * GPAD;
+#pragma unroll
+            for (int k = 0; k < GBK; k += 4) {
+                const float4 x0 = *reinterpret_cast<const float4*>(Ar0 + k);
+                const float4 x1 = *reinterpret_cast<const float4*>(Ar1 + k);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float4 y = *reinterpret_cast<const float4*>(Bt + (size_t)v * 8 * GPAD + k);
+                    acc[0][v] = fmaf(x0.x, y.x, acc[0][v]); acc[0][v] = fmaf(x0.y, y.y, acc[0][v]);
+                    acc[0][v] = fmaf(x0.z, y.z, acc[0][v]); acc[0][v] = fmaf(x0.w, y.w, acc[0][v]);
+                    acc[1][v] = fmaf(x1.x, y.x, acc[1][v]); acc[1][v] = fmaf(x1.y, y.y, acc[1][v]);
+                    acc[1][v] = fmaf(x1.z, y.z, acc[1][v]); acc[1][v] = fmaf(x1.w, y.w, acc[1][v]);
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // the ring is reused by the next column chunk
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int a = a0 + ty * 2 + u;
+            if (a >= s) continue;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int bb = b0 + tx + 8 * v;
+                if (bb > q) continue;
+                if (bb == q) {
+                    if (a >= s0) d.h[(size_t)i * smax + a] = acc[u][v];
+                    continue;
+                }
+                const int col = s0 + bb;
+                Gi[(size_t)a * smax + col] = acc[u][v];
+                Gi[(size_t)col * smax + a] = acc[u][v];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ APG
 // Gram block in shared memory when s <= gcap (<= APG_SMEM_S), else read from
 // global memory (L2).  Dynamic shared memory: [G gcap^2 | 6 vectors of vcap].
@@ -510,11 +608,24 @@ cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl) {
     return cudaGetLastError();
 }
 
+cudaError_t prepare_gram() {
+    static bool attr = false;
+    if (attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_gram_async, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAM_SMEM);
+    if (e == cudaSuccess) attr = true;
+    return e;
+}
+
 cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     dim3 grid(ub, (d.smax + GBM - 1) / GBM);
-    if ((d.n & 3) == 0) k_gram<true><<<grid, 256, 0, s>>>(d);
-    else k_gram<false><<<grid, 256, 0, s>>>(d);
+    if ((d.n & 3) == 0) {
+        cudaError_t ep = prepare_gram();
+        if (ep != cudaSuccess) return ep;
+        k_gram_async<<<grid, 256, GRAM_SMEM, s>>>(d);
+    } else {
+        k_gram<false><<<grid, 256, 0, s>>>(d);
+    }
     ++*nl;
     return cudaGetLastError();
 }
