@@ -244,7 +244,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, phase_tot, launches, certified = [], np.zeros(9), 0, True
+    step_ms, phase_tot, launches, certified = [], np.zeros(10), 0, True
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -287,7 +287,8 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     pk = peaks()
     names = ["total", "correlation", "selection", "gram", "finish", "master", "residual"]
     phase = {nm: phase_tot[i] / args.steps for i, nm in enumerate(names)}
-    cols = phase_tot[7] / args.steps        # signal columns the correlation processed per step
+    # signal columns the correlation GEMM processed per step (the identity route's excluded)
+    cols = (phase_tot[7] - phase_tot[9]) / args.steps
     fin_flops = phase_tot[8] / args.steps   # algorithmic FLOPs of the exact finish per step
     corr_ms, fin_ms = phase["correlation"], phase["finish"]
     fp32_peak = 152 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12

@@ -68,7 +68,16 @@ typedef enum {
     MPL_OPT_WARM_CANDIDATES = 10, /* W: atoms per signal scored by the proposal network (the W
                                      largest |a_j^T b| of the first correlation). default 64 */
     MPL_OPT_WARM_MAX = 11,        /* most atoms a proposal adds to a signal's set. default 3 rho */
-    MPL_OPT_WARM_THRESHOLD = 12   /* accept a candidate when its logit exceeds this. default -1 */
+    MPL_OPT_WARM_THRESHOLD = 12,  /* accept a candidate when its logit exceeds this. default -1 */
+    MPL_OPT_QROUTE = 13           /* identity route of the worst-case analysis (Sec. 3, eq.
+                                     "batchQ"): g_i = beta_i - Q_S x_S with Q = A^T A (m x m
+                                     FP32, built on first use, 4 m^2 bytes held by the handle)
+                                     and beta_i = A^T b_i (kept from the first iteration, which
+                                     then runs the FP32 GEMM).  Taken at outer iterations whose
+                                     bound on |S| (t rho plus warm-start additions) is at most
+                                     this value; 0 = never (default).  The selection widens its
+                                     re-score band to the route's error bound, so the atoms
+                                     chosen, and the solution, are the same on either route. */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -217,9 +226,34 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
  * the correlation and the exact finish are timed).  Entry 7 is the number of
  * signal columns the correlation processed, summed over outer iterations;
  * entry 8 the algorithmic FLOPs of the exact finish (factorisations, solves,
- * residual and correlation sums); both always filled.  Returns the number of
- * values written (<= cap, <= 9). */
+ * residual and correlation sums); entry 9 how many of the entry-7 columns the
+ * identity route (MPL_OPT_QROUTE) scored instead of the GEMM; 7..9 always
+ * filled.  Returns the number of values written (<= cap, <= 10). */
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
+
+/* Autotuner of the batched solve (no counterpart in the paper, which has no
+ * batching layer to tune).  Times complete solves of the caller's batch
+ * (B, p, lambda, tol as for bmpl_solve; device or host memory) under each
+ * candidate setting -- the identity route for the first k = 0, 1, 2, 4 outer
+ * iterations after the first (MPL_OPT_QROUTE = k rho plus the warm-start
+ * additions; k > 0 only when Q = A^T A fits in a quarter of the free device
+ * memory) and MPL_OPT_SYNC_EVERY in {1, 2, 4} -- and keeps the fastest on the
+ * handle.  Every candidate computes the same solution, so only time is
+ * compared.  Each candidate runs once untimed (graph capture, Q build) and
+ * three times timed with events on `stream`; the median counts.  The solutions
+ * go to a scratch buffer the call allocates and frees; the handle's last-solve
+ * statistics are those of the final timed run.  `out` (may be NULL) receives
+ * the choice.  Synchronises `stream`.  Errors: those of bmpl_solve (the first
+ * candidate's), MPL_ERR_OOM for the scratch buffer. */
+typedef struct {
+    int qroute;          /* chosen MPL_OPT_QROUTE */
+    int sync_every;      /* chosen MPL_OPT_SYNC_EVERY */
+    double ms;           /* median solve time of the choice */
+    double ms_default;   /* median solve time with qroute 0 and sync_every 2 */
+    int candidates;      /* settings timed */
+} mpl_tune_result_t;
+mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* lambda, double tol,
+                          void* stream, mpl_tune_result_t* out);
 
 /* Number of CUDA kernel launches issued by the last bmpl_solve. */
 int64_t mpl_get_launch_count(mpl_handle_t h);

@@ -457,7 +457,7 @@ __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
     return factor(sh.F, np, &sh.ival[0]);
 }
 
-__global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm, int rsm) {
+__global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int msm, int rsm) {
     const int g = blockIdx.x;
     if (g >= d.cnt->fin_n) return;
     const int i = d.list_fin[g];
@@ -763,6 +763,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finish(Dev d, int scap, int msm
             d.rr[i] = RR;
             d.rb[i] = RB;
             d.rnorm[i] = (float)(sqrt(RS) * (1.0 + 1e-5));
+            if (d.xl1) d.xl1[i] = __double2float_ru(L1 * (1.0 + 1e-6));
             d.kkt_in[i] = kkt_on;
             d.ginf[i] = fmax(CM, cmax_s);
             d.nnz[i] = np;

@@ -53,8 +53,9 @@ struct mpl_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
     int use_graph = 1;
     struct GraphEntry {
-        int p, tk, par, nog, prof;
+        int p, tk, par, nog, prof, route;
         double tol;
+        int64_t kernels;  // kernel launches captured in the graph
         cudaGraphExec_t exec;
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;  // phase timing nodes
     };
@@ -73,6 +74,11 @@ struct mpl_ctx {
     int warm_w = 64, warm_max = -1;  // -1: 3 rho
     double warm_thr = -1.0;
     double eps_in = 1e-4;
+    // identity route (eq. batchQ): taken at outer iterations whose bound on |S| is <= qroute
+    int qroute = 0;
+    float* Q = nullptr;      // m x m Gram matrix, built on first use, freed with the handle
+    float* beta = nullptr;   // beta_cap x m
+    int beta_cap = 0;
     // workspace
     int cap_p = 0, cap_smax = 0;
     bool cap_r16 = false;
@@ -91,7 +97,7 @@ struct mpl_ctx {
     int last_p = 0;
     std::vector<mpl_signal_stats_t> stats;
     int64_t launches = 0;
-    double phase_ms[9] = {0};
+    double phase_ms[10] = {0};
     std::vector<cudaEvent_t> evpool;
 };
 
@@ -189,6 +195,8 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
                     &d.list_apg};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
+    CK(alloc(h, &d.bnorm, (size_t)P));
+    CK(alloc(h, &d.xl1, (size_t)P));
     CK(alloc(h, &d.eps, (size_t)P));
     double** dbl[] = {&d.obj, &d.kkt_in, &d.kkt_out, &d.ginf, &d.rr, &d.rb};
     for (double** q : dbl) CK(alloc(h, q, (size_t)P));
@@ -229,6 +237,14 @@ void set_bounds(mpl_ctx* h, Dev& d) {
     const double gam = nu / (1.0 - nu);
     const double c32 = 2.0 * (gam + u);  // sequential FP32 dot vs exact, incl. rounding of r
     d.bound_c32 = (float)(c32 * 1.01);
+    d.bound_f32 = (float)(c32 * 1.01);
+    // identity route: FP32 beta and Q entries (gamma_n each, relative to colmax ||b|| and
+    // colmax^2 ||x||_1), the FP32 sum over at most smax terms, and the FP32 residual the
+    // re-score reads (gamma_smax each)
+    const int smax = h->smax > 0 ? h->smax : default_smax(h);
+    const double su = (double)(smax + 1) * u;
+    const double gs = su / (1.0 - su);
+    d.bound_q = (float)((gam + 2.0 * gs * (1.0 + gam) + u) * 1.01);
     if (h->precision == 1) {
         // BF16 operands (relative 2^-8 each) with an FP32 accumulator assumed to
         // keep at least 22 bits per addition; plus the FP32 terms above.
@@ -343,6 +359,8 @@ mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
 void mpl_destroy(mpl_handle_t h) {
     if (!h) return;
     free_ws(h);
+    cudaFree(h->Q);
+    cudaFree(h->beta);
     cudaFree(h->A32);
     cudaFree(h->A16);
     cudaFree(h->colnorm);
@@ -418,6 +436,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v != 0 && v != 1) return MPL_ERR_ARG;
             h->use_graph = (int)v;
             return MPL_OK;
+        case MPL_OPT_QROUTE:
+            if (v < 0 || v > 1024) return MPL_ERR_ARG;
+            h->qroute = (int)v;
+            return MPL_OK;
         default:
             return MPL_ERR_ARG;
     }
@@ -439,8 +461,52 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_CANDIDATES: *v = h->warm_w; return MPL_OK;
         case MPL_OPT_WARM_MAX: *v = h->warm_max; return MPL_OK;
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
+        case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
         default: return MPL_ERR_ARG;
     }
+}
+
+// Q = A^T A (once per handle) and the beta rows for p signals, for the identity route.
+static mpl_status_t ensure_identity_route(mpl_ctx* h, int p, cudaStream_t st, int64_t* nl) {
+    const int n = h->n, m = h->m;
+    if (!h->Q) {
+        CK(cudaMalloc(&h->Q, (size_t)m * m * sizeof(float)));
+        int* act = nullptr;
+        Counters* cnt = nullptr;
+        CK(cudaMalloc(&act, (size_t)m * sizeof(int)));
+        CK(cudaMalloc(&cnt, sizeof(Counters)));
+        const cudaError_t e = build_gram_q(h->A32, n, m, h->Q, act, cnt, st, nl);
+        const cudaError_t es = cudaStreamSynchronize(st);
+        cudaFree(act);
+        cudaFree(cnt);
+        CK(e);
+        CK(es);
+        clear_graphs(h);
+    }
+    if (h->beta_cap < p) {
+        cudaFree(h->beta);
+        h->beta = nullptr;
+        h->beta_cap = 0;
+        CK(cudaMalloc(&h->beta, (size_t)p * m * sizeof(float)));
+        h->beta_cap = p;
+        clear_graphs(h);
+    }
+    return MPL_OK;
+}
+
+// Atoms a warm start may add at the first iteration (bounds |S| on the host).
+static int warm_additions(const mpl_ctx* h, const Dev& d) {
+    return h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax)) : 0;
+}
+
+// Correlation route of outer iteration t.  With the identity route enabled, the
+// first iteration (x = 0, residual b) runs the FP32 GEMM and keeps its scores as
+// beta; later iterations whose bound on |S| is at most qroute read Q instead.
+static int iteration_route(const mpl_ctx* h, const Dev& d, int t) {
+    if (h->qroute <= 0) return ROUTE_GEMM;
+    if (t == 0) return h->precision == 1 ? ROUTE_GEMM_F32 : ROUTE_GEMM;
+    const int sb = std::min(d.smax, t * d.rho + warm_additions(h, d));
+    return sb <= h->qroute ? ROUTE_Q : ROUTE_GEMM;
 }
 
 // One outer iteration of Algorithm 1 for every active signal (kernels only).
@@ -449,14 +515,18 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
                                     PhaseTimer* pt, int64_t* nl) {
     const int cur = t & 1;
     const int no_grow = t >= h->max_outer;
+    const int route = iteration_route(h, d, t);
     cudaError_t e;
     cudaEvent_t e0 = pt ? pt->begin_if(1, run) : nullptr;
-    if (h->precision == 1) {
+    if (route == ROUTE_Q) {
+        if ((e = launch_corr_q(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+    } else if (h->precision == 1 && route == ROUTE_GEMM) {
         if ((e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
         if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
     } else {
         if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     }
+    if (t == 0 && h->qroute > 0 && (e = launch_save_beta(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(1, e0, run);
     e0 = pt ? pt->begin_if(2, run) : nullptr;
     if (t == 0 && h->warm == 2) {
@@ -469,8 +539,8 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
         pa.thr = (float)h->warm_thr;
         pa.w = h->pwb;
         pa.rn = h->rn;
-        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa)) != cudaSuccess) return e;
-    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl)) != cudaSuccess) {
+        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa, route)) != cudaSuccess) return e;
+    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, nullptr, route)) != cudaSuccess) {
         return e;
     }
     if ((e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
@@ -478,8 +548,7 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     // the exact finish touches only signals without violators: overlap it
     // with the Gram growth / master problem / residual of the others
     // bound on |S| after this iteration's growth: rho per iteration, plus what a warm start admits
-    const int warm_add = h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax)) : 0;
-    const int scap = std::min(d.smax, (t + 1) * d.rho + warm_add);
+    const int scap = std::min(d.smax, (t + 1) * d.rho + warm_additions(h, d));
     if ((e = cudaEventRecord(h->ev_fork, run)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     e0 = pt ? pt->begin_if(4, h->side) : nullptr;
@@ -505,9 +574,11 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, doubl
     const int tsat = (d.smax + d.rho - 1) / d.rho;  // beyond this the active-set bound is smax
     const int tk = std::min(t, tsat + 1);
     const int par = t & 1, nog = t >= h->max_outer ? 1 : 0, prof = h->profile ? 1 : 0;
+    const int route = iteration_route(h, d, t) + 4 * (t == 0 && h->qroute > 0 ? 1 : 0);
     for (size_t gi = 0; gi < h->graphs.size(); ++gi) {
         const auto& g = h->graphs[gi];
-        if (g.p == p && g.tk == tk && g.par == par && g.nog == nog && g.prof == prof && g.tol == tol) {
+        if (g.p == p && g.tk == tk && g.par == par && g.nog == nog && g.prof == prof && g.route == route &&
+            g.tol == tol) {
             *out = gi;
             return cudaSuccess;
         }
@@ -530,7 +601,7 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, doubl
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
-    h->graphs.push_back({p, tk, par, nog, prof, tol, exec, gpt.marks});
+    h->graphs.push_back({p, tk, par, nog, prof, route, tol, cnt, exec, gpt.marks});
     *out = h->graphs.size() - 1;
     (void)nl;
     return cudaSuccess;
@@ -596,6 +667,12 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         h->tmap_p = h->cap_p;
     }
     const float* lamd = h->lamint;
+    if (h->qroute > 0) {
+        mpl_status_t qs = ensure_identity_route(h, p, st, &nl);
+        if (qs != MPL_OK) return qs;
+        d.Q = h->Q;
+        d.beta = h->beta;
+    }
 
     if (h->warm == 2 && !h->prop_ready) return MPL_ERR_ARG;  // no proposal weights loaded
     PhaseTimer pt{h, st, {}, 0};
@@ -610,7 +687,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
             size_t gi = 0;
             CK(iteration_graph(h, d, t, p, tol, st, &gi, &nl));
             CK(cudaGraphLaunch(h->graphs[gi].exec, st));
-            nl += (h->precision == 1 ? 8 : 7);
+            nl += h->graphs[gi].kernels;
             window.push_back(gi);
         } else {
             CK(launch_iteration(h, d, t, act_ub, st, &pt, &nl));
@@ -655,6 +732,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     for (int k = 1; k < 7; ++k) h->phase_ms[k] += graph_phase[k];
     h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
     h->phase_ms[8] = (double)h->cnt_h->fin_flops;  // algorithmic FLOPs of the exact finish
+    h->phase_ms[9] = (double)h->cnt_h->qcols;      // of those columns, scored by the identity route
     h->launches = nl;
     bool all_ok = true;
     for (int i = 0; i < p; ++i) {
@@ -982,11 +1060,82 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
 
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
     if (!h || !ms_out) return 0;
-    const int k = std::min(cap, 9);
+    const int k = std::min(cap, 10);
     for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
     return k;
 }
 
 int64_t mpl_get_launch_count(mpl_handle_t h) { return h ? h->launches : 0; }
+
+mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* lambda, double tol, void* stream,
+                          mpl_tune_result_t* out) {
+    if (!h || p <= 0 || !B || !lambda || !(tol > 0.0) || !(tol < 1.0)) return MPL_ERR_ARG;
+    CK(cudaSetDevice(h->dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int m = h->m;
+    const int smax = h->smax > 0 ? h->smax : default_smax(h);
+    const int rho = std::min(h->rho, m);
+    const int warm_add = h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * rho, smax)) : 0;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const bool q_fits = h->Q != nullptr || (double)m * m * sizeof(float) <= 0.25 * (double)free_b;
+    std::vector<int> qcands = {0};
+    if (q_fits)
+        for (int k : {1, 2, 4}) {
+            const int v = std::min(smax, k * rho + warm_add);
+            if (v > qcands.back()) qcands.push_back(v);
+        }
+    const int se_cands[] = {1, 2, 4};
+    float* X = nullptr;
+    CK(cudaMalloc(&X, (size_t)m * p * sizeof(float)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int keep_q = h->qroute, keep_se = h->sync_every, keep_prof = h->profile;
+    h->profile = 0;
+    mpl_tune_result_t best{keep_q, keep_se, 1e300, 0.0, 0};
+    mpl_status_t first_err = MPL_OK;
+    for (int qr : qcands) {
+        for (int se : se_cands) {
+            h->qroute = qr;
+            h->sync_every = se;
+            clear_graphs(h);
+            mpl_status_t rc = bmpl_solve(h, B, p, lambda, X, tol, stream);  // capture + warm-up
+            std::vector<float> t;
+            for (int r = 0; r < 3 && (rc == MPL_OK || rc == MPL_ERR_NOT_CONVERGED); ++r) {
+                cudaEventRecord(e0, st);
+                rc = bmpl_solve(h, B, p, lambda, X, tol, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t.push_back(ms);
+            }
+            if (rc != MPL_OK && rc != MPL_ERR_NOT_CONVERGED) {
+                if (first_err == MPL_OK) first_err = rc;
+                continue;
+            }
+            std::sort(t.begin(), t.end());
+            const double med = t[t.size() / 2];
+            ++best.candidates;
+            if (qr == 0 && se == 2) best.ms_default = med;
+            if (med < best.ms) { best.ms = med; best.qroute = qr; best.sync_every = se; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(X);
+    h->profile = keep_prof;
+    clear_graphs(h);
+    if (best.candidates == 0) {
+        h->qroute = keep_q;
+        h->sync_every = keep_se;
+        return first_err != MPL_OK ? first_err : MPL_ERR_CUDA;
+    }
+    h->qroute = best.qroute;
+    h->sync_every = best.sync_every;
+    if (out) *out = best;
+    return MPL_OK;
+}
 
 }  // extern "C"

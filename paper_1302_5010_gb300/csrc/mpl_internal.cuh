@@ -27,6 +27,7 @@ struct Counters {
     int sel_fallback;// candidate-buffer overflows in the selection
     unsigned long long cols;  // signal columns processed by the correlation (all iterations)
     unsigned long long fin_flops;  // algorithmic FLOPs of the exact finish (factor, solves, residual sums)
+    unsigned long long qcols;  // signal columns scored by the identity route beta - Q_S x_S
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 
@@ -40,6 +41,12 @@ struct Dev {
     float colmax;                // max_j ||a_j|| (rounded up)
     float bound_c;               // |score_gemm - a_j^T r| <= bound_c * colmax * ||r||
     float bound_c32;             // same for the fixed-order FP32 re-score
+    float bound_f32;             // FP32 correlation GEMM (either precision)
+    float bound_q;               // identity route: |score - a_j^T r| <= bound_q*colmax*(||b|| + colmax*||x||_1)
+    const float* Q;              // m x m Gram matrix A^T A (row k = A^T a_k), identity route only
+    float* beta;                 // p x m beta = A^T b (FP32), identity route only
+    float* bnorm;                // p ||b|| upper bound
+    float* xl1;                  // p ||x_S||_1 upper bound of the FP32 iterate
     const float* A32;            // m x n atom-major
     const __nv_bfloat16* A16;    // m x n atom-major (mixed)
     const float* B;              // p x n signals (device)
@@ -116,8 +123,16 @@ cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16,
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms,
                              cudaStream_t s, int64_t* nl);
 cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+// Correlation routes of one outer iteration (selects the selection kernel's error band).
+enum CorrRoute : int { ROUTE_GEMM = 0, ROUTE_GEMM_F32 = 1, ROUTE_Q = 2 };
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa = nullptr);
+                          const PropArgs* pa = nullptr, int route = ROUTE_GEMM);
+// Identity route (eq. batchQ): scores beta_i - Q_S x_S into the compacted score rows.
+cudaError_t launch_corr_q(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+// beta_i = score row of signal i (after an FP32 correlation of the residual b_i).
+cudaError_t launch_save_beta(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+cudaError_t build_gram_q(const float* A32, int n, int m, float* Q, int* act, Counters* cnt, cudaStream_t s,
+                         int64_t* nl);
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
@@ -156,7 +171,7 @@ constexpr int APG_SMEM_S = 200;
 constexpr int APG_THREADS = 256;
 // Exact finish: FP32 factor in shared memory up to this support size (global beyond).
 constexpr int FIN_SMEM_P = 128;
-constexpr int FIN_THREADS = 512;
+constexpr int FIN_THREADS = 256;
 constexpr int FIN_MAX_PIVOTS = 16;
 constexpr int FIN_MAX_FAILS = 6;
 

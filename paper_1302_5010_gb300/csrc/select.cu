@@ -246,7 +246,7 @@ __device__ __forceinline__ unsigned ordered_bits(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa) {
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa, int route) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     const float lam_sel = (float)lam_hi;                // selection threshold
     const float rn = d.rnorm[i];
     const float delta32 = d.bound_c32 * d.colmax * rn;  // |rescore - a^T r|
-    float delta = d.bound_c * d.colmax * rn;            // |gemm score - a^T r|
+    // |score - a^T r| for the route that produced this iteration's scores
+    float delta = route == ROUTE_Q ? d.bound_q * d.colmax * (d.bnorm[i] + d.colmax * d.xl1[i])
+                                   : (route == ROUTE_GEMM_F32 ? d.bound_f32 : d.bound_c) * d.colmax * rn;
     if (tid == 0) sh.nonfinite = 0;
     __syncthreads();
 
@@ -548,14 +550,14 @@ cudaError_t prepare_select() {
 }
 
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa) {
+                          const PropArgs* pa, int route) {
     if (act_n_ub <= 0) return cudaSuccess;
     PropArgs a{};
     if (pa) a = *pa;
     const size_t sm = sizeof(SelSmem) + (a.mode != SEL_NORMAL ? PROP_NPARAM * sizeof(float) : 0);
     cudaError_t e = prepare_select();
     if (e != cudaSuccess) return e;
-    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a);
+    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a, route);
     ++*nl;
     return cudaGetLastError();
 }

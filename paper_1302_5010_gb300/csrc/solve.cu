@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.fails[i] = 0;
         d.nnz[i] = 0;
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
+        if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
         d.eps[i] = d.eps_in;
         d.obj[i] = 0.5 * bb;
         d.rr[i] = bb;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->sel_fallback = 0;
             d.cnt->cols = 0ull;
             d.cnt->fin_flops = 0ull;
+            d.cnt->qcols = 0ull;
         }
     }
 }
@@ -466,6 +468,13 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     }
     __syncthreads();
     const int nz = cntnz;
+    if (d.Q) {  // ||x_S||_1 for the identity route's error band (FP32 sum, rounded up by gamma_1024)
+        float l1 = 0.f;
+        for (int a = threadIdx.x; a < nz; a += blockDim.x) l1 += fabsf(nzv[a]);
+        const float t1 = block_sum(l1, red);
+        if (threadIdx.x == 0) d.xl1[i] = t1 * (1.f + 2e-4f);
+        __syncthreads();
+    }
     const float* b = d.B + (size_t)i * n;
     float* r32 = d.R32 + (size_t)i * n;
     float ss = 0.f;

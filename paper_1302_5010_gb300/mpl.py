@@ -40,6 +40,7 @@ MPL_OPT_GRAPH = 9
 MPL_OPT_WARM_CANDIDATES = 10
 MPL_OPT_WARM_MAX = 11
 MPL_OPT_WARM_THRESHOLD = 12
+MPL_OPT_QROUTE = 13
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -56,7 +57,7 @@ MPL_SIG_NONFINITE = 4
 EXPORTED = ("mpl_create", "bmpl_solve", "mpl_correlate", "mpl_destroy", "mpl_set_option", "mpl_get_option",
             "mpl_get_stats", "mpl_get_solution_f64", "mpl_get_phase_times", "mpl_get_launch_count",
             "mpl_status_string", "mpl_correlate_noalloc", "mpl_proposal_set_weights",
-            "mpl_proposal_get_weights", "mpl_proposal_train", "mpl_proposal_loss_grad")
+            "mpl_proposal_get_weights", "mpl_proposal_train", "mpl_proposal_loss_grad", "mpl_autotune")
 
 
 class SignalStats(ctypes.Structure):
@@ -64,6 +65,11 @@ class SignalStats(ctypes.Structure):
                 ("active_size", ctypes.c_int32), ("nnz", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("finishes", ctypes.c_int32), ("objective", ctypes.c_double), ("kkt", ctypes.c_double),
                 ("gap", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("qroute", ctypes.c_int32), ("sync_every", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32)]
 
 
 class MplError(RuntimeError):
@@ -120,6 +126,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.mpl_get_phase_times.restype = i32
     lib.mpl_get_launch_count.argtypes = [vp]
     lib.mpl_get_launch_count.restype = ctypes.c_int64
+    lib.mpl_autotune.argtypes = [vp, vp, i32, vp, f64, vp, ctypes.POINTER(TuneResult)]
+    lib.mpl_autotune.restype = i32
     lib.mpl_status_string.argtypes = [i32]
     lib.mpl_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -257,9 +265,18 @@ def mpl_get_solution_f64(h, p: int, X64) -> None:
 
 
 def mpl_get_phase_times(h) -> list:
-    buf = (ctypes.c_double * 9)()
-    k = load().mpl_get_phase_times(h, buf, 9)
+    buf = (ctypes.c_double * 10)()
+    k = load().mpl_get_phase_times(h, buf, 10)
     return [buf[i] for i in range(k)]
+
+
+def mpl_autotune(h, B, p: int, lam, tol: float, stream=None) -> dict:
+    """Time the candidate settings on this batch and keep the fastest (include/mpl.h)."""
+    out = TuneResult()
+    rc = load().mpl_autotune(h, _ptr(B), int(p), _ptr(lam), float(tol), _stream_ptr(stream), ctypes.byref(out))
+    if rc != MPL_OK:
+        raise MplError(rc, "mpl_autotune")
+    return {f: getattr(out, f) for f, _ in TuneResult._fields_}
 
 
 def mpl_get_launch_count(h) -> int:
@@ -267,7 +284,7 @@ def mpl_get_launch_count(h) -> int:
 
 
 PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "corr_columns",
-          "finish_flops")
+          "finish_flops", "qroute_columns")
 
 
 @dataclass
@@ -289,7 +306,7 @@ class Solver:
         keys = dict(max_outer=MPL_OPT_MAX_OUTER, smax=MPL_OPT_SMAX, eps_in=MPL_OPT_EPS_IN,
                     inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE,
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
-                    warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD)
+                    warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 
@@ -306,6 +323,9 @@ class Solver:
         """Train the warm-start proposal on signals B (p, n) with reference solutions
         Xref (p, m); returns the mean loss per epoch."""
         return mpl_proposal_train(self.h, B, B.shape[0], lam, Xref, epochs, lr, batch, seed)
+
+    def autotune(self, B, lam, tol: float = 1e-6, stream=None) -> dict:
+        return mpl_autotune(self.h, B, B.shape[0], lam, tol, stream)
 
     def correlate(self, R, C, stream=None) -> None:
         mpl_correlate(self.h, R, R.shape[0], C, stream)
