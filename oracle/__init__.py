@@ -27,7 +27,8 @@ _lib = None
 class Opts(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_int), ("max_outer", ctypes.c_int), ("s_max", ctypes.c_int),
                 ("max_attempts", ctypes.c_int), ("exact_finish", ctypes.c_int),
-                ("corr_route", ctypes.c_int), ("eps_in", ctypes.c_double)]
+                ("corr_route", ctypes.c_int), ("eps_in", ctypes.c_double), ("omega", ctypes.c_int),
+                ("stop_rinf", ctypes.c_double), ("stop_r2", ctypes.c_double), ("stop_eps", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):

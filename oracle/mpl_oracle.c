@@ -42,6 +42,20 @@
  * With lambda = 0 and rho = 1 the loop is orthogonal matching pursuit
  * (Sec. 2.3, last paragraph): the restricted problem is least squares and the
  * finish solves G z = h directly.
+ *
+ * Subspace exploratory matching (SMPL, Algorithm 2; omega > 1): step 2 takes
+ * the omega*rho largest violators J_omega instead, the master problem is
+ * solved on I u J_omega (warm started, new entries at zero), and only the rho
+ * atoms of J_omega with the largest |u_i| stay (ties to the earlier-selected
+ * atom); the others leave I with their entries, and x^t is u on what remains.
+ *
+ * Early stopping (Sec. 2.5), each rule off when its threshold is negative:
+ *   eq. (stop1): before the selection, stop when ||A^T xi||_inf <= r_inf or
+ *                ||xi|| <= r_2;
+ *   eq. (stop_con): after the master problem of outer iteration t, stop when
+ *                delta_t / |rho f(x^0)| <= eps, delta_t = f(x^{t-1}) - f(x^t),
+ *                f(x^0) = 0.5 ||b||^2.
+ * An early stop leaves status 3 and x = x^t.
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,6 +73,10 @@ typedef struct {
     int exact_finish; /* 1 = run the sign-fixed Cholesky finish */
     int corr_route;   /* 0 = g = A^T xi, 1 = g = beta - Q_I x_I (eq. batchQ) */
     double eps_in;    /* relative-decrease tolerance of eq. (inner) */
+    int omega;        /* subspace search length of Algorithm 2 (1 = Algorithm 1) */
+    double stop_rinf; /* eq. (stop1): r_inf (< 0: off) */
+    double stop_r2;   /* eq. (stop1): r_2 (< 0: off) */
+    double stop_eps;  /* eq. (stop_con): eps (< 0: off) */
 } mpl_oracle_opts;
 
 typedef struct {
@@ -66,7 +84,8 @@ typedef struct {
     int n_inner;      /* PG iterations over all outer iterations */
     int S_size;       /* |I| at exit */
     int status;       /* 0 = stopping condition met, 1 = max_outer reached,
-                         2 = met, but some restricted solve was not finished exactly */
+                         2 = met, but some restricted solve was not finished exactly,
+                         3 = early stop (eq. stop1 or stop_con) */
     int nnz;          /* nonzeros of x */
     double objective; /* lambda*||x||_1 + 0.5*||b - A x||^2 */
     double kkt;       /* max KKT violation / lambda (absolute when lambda == 0) */
@@ -422,10 +441,51 @@ static void certify(const double* At, int n, int m, const double* b, double lam,
     *nnz = nz;
 }
 
+typedef struct { double key; int pos; } keep_t;
+
+static int keep_cmp(const void* pa, const void* pb) {
+    const keep_t* a = pa;
+    const keep_t* b = pb;
+    if (a->key > b->key) return -1;
+    if (a->key < b->key) return 1;
+    return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+/* Algorithm 2, last steps: of the q atoms appended at positions s0..s0+q-1,
+ * keep the `keep` with the largest |u| (ties to the earlier position); the
+ * others leave I.  I, u, h and G are compacted in place, order preserved.
+ * Returns the new |I|. */
+static int smpl_prune(work_t* w, int s0, int q, int keep) {
+    const int ld = w->cap;
+    keep_t* k = malloc(sizeof(keep_t) * (size_t)q);
+    char* stay = calloc((size_t)q, 1);
+    int* from = malloc(sizeof(int) * (size_t)(s0 + q));
+    if (!k || !stay || !from) { free(k); free(stay); free(from); return -1; }
+    for (int a = 0; a < q; ++a) { k[a].key = fabs(w->u[s0 + a]); k[a].pos = a; }
+    qsort(k, (size_t)q, sizeof(keep_t), keep_cmp);
+    for (int a = 0; a < keep; ++a) stay[k[a].pos] = 1;
+    int ns = 0;
+    for (int a = 0; a < s0 + q; ++a)
+        if (a < s0 || stay[a - s0]) from[ns++] = a;
+        else w->inI[w->I[a]] = 0;
+    /* forward copies: from[a] >= a, so no source is overwritten before it is read */
+    for (int a = 0; a < ns; ++a) {
+        const int fa = from[a];
+        w->I[a] = w->I[fa];
+        w->u[a] = w->u[fa];
+        w->h[a] = w->h[fa];
+        for (int c = 0; c < ns; ++c) w->G[(size_t)a * ld + c] = w->G[(size_t)fa * ld + from[c]];
+    }
+    for (int a = ns; a < s0 + q; ++a) w->u[a] = 0.0;
+    free(k); free(stay); free(from);
+    return ns;
+}
+
 static int solve_one(const double* At, int n, int m, const double* Q, const double* beta_in,
                      const double* b, double lam, const mpl_oracle_opts* o, work_t* w,
                      double* x, mpl_oracle_result* res, mpl_oracle_trace* tr) {
     const int rho = o->rho > 0 ? o->rho : 1;
+    const int omega = o->omega > 1 ? o->omega : 1;
     const int max_outer = o->max_outer > 0 ? o->max_outer : m / rho + 2;
     memset(w->inI, 0, (size_t)m);
     for (int k = 0; k < n; ++k) w->r[k] = b[k];
@@ -440,6 +500,18 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
     double f_cur = 0.5 * bb;
     for (outer = 0; outer < max_outer; ++outer) {
         worst_case_g(At, n, m, Q, beta, w, s, o->corr_route, w->g);
+        /* early stopping, eq. (stop1) */
+        if (o->stop_rinf >= 0.0 || o->stop_r2 >= 0.0) {
+            double ginf = 0.0;
+            for (int j = 0; j < m; ++j) ginf = fmax(ginf, fabs(w->g[j]));
+            const double rn = sqrt(dotd(w->r, w->r, n));
+            if ((o->stop_rinf >= 0.0 && ginf <= o->stop_rinf) || (o->stop_r2 >= 0.0 && rn <= o->stop_r2)) {
+                if (tr && outer < tr->cap) { tr->n_added[outer] = 0; tr->f_prev[outer] = f_cur; }
+                status = 3;
+                ++outer;
+                break;
+            }
+        }
         /* rank the violators outside I */
         int nc = 0;
         rank_t* rk = (rank_t*)malloc(sizeof(rank_t) * (size_t)m);
@@ -450,15 +522,9 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
             if (a > lam) { rk[nc].key = a; rk[nc].idx = j; ++nc; }
         }
         qsort(rk, (size_t)nc, sizeof(rank_t), rank_cmp);
-        int q = nc < rho ? nc : rho;
-        if (tr && outer < tr->cap) {
-            tr->n_added[outer] = q;
-            tr->f_prev[outer] = f_cur;
-            for (int a = 0; a < q && a < tr->rho_cap; ++a) {
-                tr->added[outer * tr->rho_cap + a] = rk[a].idx;
-                tr->gsel[outer * tr->rho_cap + a] = rk[a].key;
-            }
-        }
+        const int want = omega * rho;
+        int q = nc < want ? nc : want;
+        if (tr && outer < tr->cap) tr->f_prev[outer] = f_cur;
         if (q == 0) {
             free(rk);
             status = 0;
@@ -484,12 +550,26 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
                 w->G[(size_t)c * ld + a] = v;
             }
         }
-        s += q;
         double f_first = 0.0, L_first = 0.0;
         int exact = 0;
-        int it = master_problem(w, s, lam, o, bb, &f_first, &L_first, &exact);
+        int it = master_problem(w, s + q, lam, o, bb, &f_first, &L_first, &exact);
         inner_total += it;
         if (!exact) inexact = 1;
+        const int keep = q < rho ? q : rho;
+        const int s0 = s;
+        if (omega > 1 && q > keep) {
+            s = smpl_prune(w, s0, q, keep);
+            if (s < 0) return -1;
+        } else {
+            s += q;
+        }
+        if (tr && outer < tr->cap) {  /* J_t: the atoms that joined I, in selection order */
+            tr->n_added[outer] = s - s0;
+            for (int a = s0; a < s && a - s0 < tr->rho_cap; ++a) {
+                tr->added[outer * tr->rho_cap + a - s0] = w->I[a];
+                tr->gsel[outer * tr->rho_cap + a - s0] = fabs(w->g[w->I[a]]);
+            }
+        }
         /* xi = b - A_I x_I */
         for (int k = 0; k < n; ++k) w->r[k] = b[k];
         for (int a = 0; a < s; ++a) {
@@ -498,12 +578,19 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
             const double* aj = At + (size_t)w->I[a] * n;
             for (int k = 0; k < n; ++k) w->r[k] -= aj[k] * v;
         }
+        const double f_before = f_cur;
         f_cur = lam * l1(w->u, s) + 0.5 * dotd(w->r, w->r, n);
         if (tr && outer < tr->cap) {
             tr->f_first[outer] = f_first;
             tr->L_first[outer] = L_first;
             tr->f_iter[outer] = f_cur;
             tr->inner[outer] = it;
+        }
+        /* early stopping, eq. (stop_con) */
+        if (o->stop_eps >= 0.0 && (f_before - f_cur) / fabs((double)rho * 0.5 * bb) <= o->stop_eps) {
+            status = 3;
+            ++outer;
+            break;
         }
     }
     for (int j = 0; j < m; ++j) x[j] = 0.0;
@@ -519,6 +606,7 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
 static void default_opts(mpl_oracle_opts* o) {
     o->rho = 1; o->max_outer = 0; o->s_max = 100000; o->max_attempts = 6;
     o->exact_finish = 1; o->corr_route = 0; o->eps_in = 1e-10;
+    o->omega = 1; o->stop_rinf = -1.0; o->stop_r2 = -1.0; o->stop_eps = -1.0;
 }
 
 void oracle_default_opts(mpl_oracle_opts* o) { default_opts(o); }
