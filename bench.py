@@ -232,6 +232,9 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         solver.set(mpl.MPL_OPT_WARM_START, 2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
+    # one-time tuning on the batch (identity route, handshake cadence), like the layout
+    # work of mpl_create it is outside the timed region
+    tune = None if args.no_autotune else solver.autotune(B, lam, TOL, stream)
     # phase timing events ride inside the captured iteration graphs; warm up with
     # the same setting so that the timed steps only replay graphs
     solver.set(mpl.MPL_OPT_PROFILE, 1)
@@ -315,7 +318,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     # summed event times per phase (the finish runs on a second stream, so phases overlap)
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if v > 0}
 
-    return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk,
+    return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk, "autotune": tune,
             "certified": certified, "roofline": roof, "gemm": gemm, "training": training,
             "outer_iters_mean": float(np.mean(stats["outer_iters"])),
             "active_size_mean": float(np.mean(stats["active_size"]))}
@@ -334,6 +337,7 @@ def main():
     ap.add_argument("--train-signals", type=int, default=16384)
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default route and handshake cadence")
     ap.add_argument("--ref-signals", type=int, default=64)
     ap.add_argument("--cpu-signals", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -378,13 +382,14 @@ def main():
             "certified_all": main_run["certified"], "e2e": main_run["e2e"],
             "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
             "roofline": main_run["roofline"], "correlation_gemm": main_run["gemm"],
-            "outer_iters_mean": main_run["outer_iters_mean"], "warm_start_training": main_run["training"]}
+            "outer_iters_mean": main_run["outer_iters_mean"], "warm_start_training": main_run["training"],
+            "autotune": main_run["autotune"]}
     if not args.no_compare:
         other = timed_path(args, mpl, torch, P, dev, 1 - precision, world, dist, local)
         line[names[1 - precision].replace("-", "_")] = {
             "value": other["value"], "ms_per_step": other["tot_ms"] / args.steps, "e2e": other["e2e"]["value"],
             "certified_all": other["certified"], "roofline": other["roofline"], "outer_iters_mean": other["outer_iters_mean"],
-            "correlation_gemm": other["gemm"], "clocks": other["clocks"]}
+            "correlation_gemm": other["gemm"], "clocks": other["clocks"], "autotune": other["autotune"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, P, args.cpu_signals)
     if rank == 0:

@@ -69,7 +69,7 @@ typedef enum {
                                      largest |a_j^T b| of the first correlation). default 64 */
     MPL_OPT_WARM_MAX = 11,        /* most atoms a proposal adds to a signal's set. default 3 rho */
     MPL_OPT_WARM_THRESHOLD = 12,  /* accept a candidate when its logit exceeds this. default -1 */
-    MPL_OPT_QROUTE = 13           /* identity route of the worst-case analysis (Sec. 3, eq.
+    MPL_OPT_QROUTE = 13,          /* identity route of the worst-case analysis (Sec. 3, eq.
                                      "batchQ"): g_i = beta_i - Q_S x_S with Q = A^T A (m x m
                                      FP32, built on first use, 4 m^2 bytes held by the handle)
                                      and beta_i = A^T b_i (kept from the first iteration, which
@@ -78,6 +78,12 @@ typedef enum {
                                      this value; 0 = never (default).  The selection widens its
                                      re-score band to the route's error bound, so the atoms
                                      chosen, and the solution, are the same on either route. */
+    MPL_OPT_OMEGA = 14            /* subspace exploratory matching (Algorithm 2, SMPL): each
+                                     outer iteration takes the omega*rho largest violators, solves
+                                     the master problem with all of them, and keeps the rho with
+                                     the largest |u| (ties to the larger correlation); the others
+                                     leave S and may return later.  1 = Algorithm 1 (default),
+                                     at most 16. */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */

@@ -76,6 +76,7 @@ struct mpl_ctx {
     double eps_in = 1e-4;
     // identity route (eq. batchQ): taken at outer iterations whose bound on |S| is <= qroute
     int qroute = 0;
+    int omega = 1;           // subspace search length (Algorithm 2); 1 = Algorithm 1
     float* Q = nullptr;      // m x m Gram matrix, built on first use, freed with the handle
     float* beta = nullptr;   // beta_cap x m
     int beta_cap = 0;
@@ -192,7 +193,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin,
-                    &d.list_apg};
+                    &d.list_apg, &d.explore};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
     CK(alloc(h, &d.bnorm, (size_t)P));
@@ -209,6 +210,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     d.m = m;
     d.smax = smax;
     d.mw = mw;
+    d.omega = 1;
     CK(prepare_select());
     CK(prepare_apg());
     CK(prepare_gram());
@@ -440,6 +442,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v < 0 || v > 1024) return MPL_ERR_ARG;
             h->qroute = (int)v;
             return MPL_OK;
+        case MPL_OPT_OMEGA:
+            if (v < 1 || v > 16) return MPL_ERR_ARG;
+            h->omega = (int)v;
+            return MPL_OK;
         default:
             return MPL_ERR_ARG;
     }
@@ -462,6 +468,7 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_MAX: *v = h->warm_max; return MPL_OK;
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
+        case MPL_OPT_OMEGA: *v = h->omega; return MPL_OK;
         default: return MPL_ERR_ARG;
     }
 }
@@ -548,7 +555,9 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     // the exact finish touches only signals without violators: overlap it
     // with the Gram growth / master problem / residual of the others
     // bound on |S| after this iteration's growth: rho per iteration, plus what a warm start admits
-    const int scap = std::min(d.smax, (t + 1) * d.rho + warm_additions(h, d));
+    // bound on |S| after this iteration's growth: omega*rho explored atoms on top of rho per
+    // earlier iteration (Algorithm 2 prunes back to rho), plus what a warm start admits
+    const int scap = std::min(d.smax, t * d.rho + d.omega * d.rho + warm_additions(h, d));
     if ((e = cudaEventRecord(h->ev_fork, run)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     e0 = pt ? pt->begin_if(4, h->side) : nullptr;
@@ -560,6 +569,7 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     if (pt) pt->end(3, e0, run);
     e0 = pt ? pt->begin_if(5, run) : nullptr;
     if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) return e;
+    if (d.omega > 1 && (e = launch_smpl_prune(d, act_ub, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(5, e0, run);
     e0 = pt ? pt->begin_if(6, run) : nullptr;
     if ((e = launch_residual(d, act_ub, run, nl)) != cudaSuccess) return e;
@@ -652,6 +662,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     Dev d = h->dv;
     d.p = p;
     d.rho = std::min(h->rho, m);
+    d.omega = h->omega;
     d.precision = h->precision;
     d.inner_max = h->inner_max;
     d.eps_in = (float)h->eps_in;

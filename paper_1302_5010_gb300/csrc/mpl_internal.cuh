@@ -35,6 +35,7 @@ struct Counters {
 struct Dev {
     int n, m, p, smax, rho, mw;  // mw = words of the per-signal membership bitmap
     int precision;               // 0 plain FP32, 1 mixed BF16
+    int omega;                   // subspace search length of Algorithm 2 (1 = Algorithm 1)
     int inner_max;
     float eps_in;
     double tol;
@@ -74,6 +75,7 @@ struct Dev {
     int* finishes;               // p exact-finish attempts
     int* fails;                  // p consecutive failed finishes
     int* sstatus;                // p mpl_signal_status_t
+    int* explore;                // p atoms explored this iteration (Algorithm 2), 0 = keep all
     int* nnz;                    // p
     float* rnorm;                // p ||r|| upper bound
     float* eps;                  // p current eq. (inner) tolerance
@@ -138,6 +140,8 @@ cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+// Algorithm 2: keep the rho explored atoms with the largest |u| (compacts S, x_S, h, G).
+cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl);
 cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, int64_t* nl);
 cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl);

@@ -274,7 +274,10 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
 
     const int ss = d.ssize[i];
     const bool prop = pa.mode != SEL_NORMAL;
-    const int kth = prop ? min(pa.W, m) : min(d.rho, m);
+    // Algorithm 1 takes rho atoms; Algorithm 2 (subspace exploratory matching)
+    // takes omega*rho, of which the master problem's largest |u| stay
+    const int want = d.rho * d.omega;
+    const int kth = prop ? min(pa.W, m) : min(want, m);
     bool exact_scores = false;  // row holds re-scores themselves (overflow fallback)
     unsigned kc = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
             }
             d.ssize[i] = ss + q;
             d.snew[i] = q;
+            if (d.explore) d.explore[i] = 0;
             d.state[i] = q > 0 ? ST_GROW : ST_FINALIZE;
             if (q > 0) d.finalized[i] = 0;
         }
@@ -446,9 +450,10 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
             // certified bound on |a_j^T r| over atoms outside S
             const float outside = (sh.outmax ? __uint_as_float(sh.outmax) : 0.f) + delta;
             const double offb = fmax((double)outside, (double)sh.offmax);
-            int q = min(vc, d.rho);
+            int q = min(vc, want);
             if (q > d.smax - ss) q = d.smax - ss;
             if (no_grow) q = 0;
+            if (d.explore) d.explore[i] = q > d.rho ? q : 0;  // prune to rho after the master problem
             if (q > 0) {
                 int* Si = d.S + (size_t)i * d.smax;
                 float* xi = d.xS + (size_t)i * d.smax;

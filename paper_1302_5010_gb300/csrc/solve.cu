@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.nnz[i] = 0;
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
         if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
+        if (d.explore) d.explore[i] = 0;
         d.eps[i] = d.eps_in;
         d.obj[i] = 0.5 * bb;
         d.rr[i] = bb;
@@ -529,6 +530,102 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     }
 }
 
+// ------------------------------------------------------------------ Algorithm 2
+// Subspace exploratory matching: of the q explored atoms (positions s0..s-1,
+// appended by this iteration's selection) keep the rho with the largest
+// |u| after the master problem, ties to the earlier position; the others
+// leave S with their entries.  S, x_S, h, the power-iteration vector and the
+// Gram block are compacted with the order of the remaining entries kept; the
+// signal's FP64 factor workspace (idle while it grows) stages the Gram block.
+__global__ void __launch_bounds__(256) k_smpl_prune(Dev d) {
+    const int g = blockIdx.x;
+    if (g >= d.cnt->grow_n) return;
+    const int i = d.list_grow[g];
+    const int q = d.explore[i];
+    if (q == 0) return;
+    const int smax = d.smax, s = d.ssize[i], s0 = s - q, keep = d.rho;
+    __shared__ int from[1024];
+    __shared__ int ns_sh;
+    int* Si = d.S + (size_t)i * smax;
+    float* xi = d.xS + (size_t)i * smax;
+    float* hi = d.h + (size_t)i * smax;
+    float* ri = d.ritz + (size_t)i * smax;
+    float* Gi = d.G + (size_t)i * smax * smax;
+    uint32_t* mw = d.mask + (size_t)i * d.mw;
+    // rank of each explored atom by |u| (descending, ties to the lower position)
+    for (int a = threadIdx.x; a < q; a += blockDim.x) {
+        const float ua = fabsf(xi[s0 + a]);
+        int rank = 0;
+        for (int b = 0; b < q; ++b) {
+            const float ub = fabsf(xi[s0 + b]);
+            rank += (ub > ua || (ub == ua && b < a)) ? 1 : 0;
+        }
+        from[s0 + a] = rank < keep ? 1 : 0;  // flag for now
+    }
+    __syncthreads();
+    // ordered list of the surviving positions (one warp)
+    if (threadIdx.x < 32) {
+        int base = s0;
+        for (int a0 = 0; a0 < q; a0 += 32) {
+            const int a = a0 + threadIdx.x;
+            const bool on = a < q && from[s0 + a] == 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, on);
+            const int pos = base + __popc(bal & ((1u << threadIdx.x) - 1u));
+            __syncwarp();
+            if (on) from[pos] = s0 + a;
+            base += __popc(bal);
+        }
+        if (threadIdx.x == 0) ns_sh = base;
+    }
+    __syncthreads();
+    const int ns = ns_sh;
+    for (int a = threadIdx.x; a < s0; a += blockDim.x) from[a] = a;
+    __syncthreads();
+    // removed atoms leave the membership bitmap (positions not in from[s0..ns))
+    for (int a = threadIdx.x; a < q; a += blockDim.x) {
+        bool kept = false;
+        for (int b = s0; b < ns; ++b) kept |= from[b] == s0 + a;
+        if (!kept) {
+            const int j = Si[s0 + a];
+            atomicAnd(&mw[j >> 5], ~(1u << (j & 31)));
+        }
+    }
+    // stage everything that moves, then write it back
+    float* stage = reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
+    const int nk = ns - s0;  // kept explored atoms
+    int Sk[4];
+    float xk[4], hk[4], rk[4];
+    for (int u = 0; u < 4; ++u) {
+        const int a = s0 + threadIdx.x + u * blockDim.x;
+        if (a < ns) { Sk[u] = Si[from[a]]; xk[u] = xi[from[a]]; hk[u] = hi[from[a]]; rk[u] = ri[from[a]]; }
+    }
+    // rows a >= s0 (all columns) and columns c >= s0 of rows a < s0
+    const int moved = nk * ns + s0 * nk;
+    for (int e = threadIdx.x; e < moved; e += blockDim.x) {
+        int a, c;
+        if (e < nk * ns) { a = s0 + e / ns; c = e % ns; }
+        else { const int f = e - nk * ns; a = f / nk; c = s0 + f % nk; }
+        stage[e] = Gi[(size_t)from[a] * smax + from[c]];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < moved; e += blockDim.x) {
+        int a, c;
+        if (e < nk * ns) { a = s0 + e / ns; c = e % ns; }
+        else { const int f = e - nk * ns; a = f / nk; c = s0 + f % nk; }
+        Gi[(size_t)a * smax + c] = stage[e];
+    }
+    for (int u = 0; u < 4; ++u) {
+        const int a = s0 + threadIdx.x + u * blockDim.x;
+        if (a < ns) { Si[a] = Sk[u]; xi[a] = xk[u]; hi[a] = hk[u]; ri[a] = rk[u]; }
+    }
+    for (int a = ns + threadIdx.x; a < s; a += blockDim.x) xi[a] = 0.f;
+    if (threadIdx.x == 0) {
+        d.ssize[i] = ns;
+        d.snew[i] = nk;
+        d.explore[i] = 0;
+    }
+}
+
 // ------------------------------------------------------------------ output
 __global__ void k_scatter(Dev d, float* X, double* X64) {
     const int i = blockIdx.x;
@@ -669,6 +766,13 @@ cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, 
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     k_residual<<<ub, 256, 0, s>>>(d);
+    ++*nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    k_smpl_prune<<<ub, 256, 0, s>>>(d);
     ++*nl;
     return cudaGetLastError();
 }

@@ -41,6 +41,7 @@ MPL_OPT_WARM_CANDIDATES = 10
 MPL_OPT_WARM_MAX = 11
 MPL_OPT_WARM_THRESHOLD = 12
 MPL_OPT_QROUTE = 13
+MPL_OPT_OMEGA = 14
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -306,7 +307,8 @@ class Solver:
         keys = dict(max_outer=MPL_OPT_MAX_OUTER, smax=MPL_OPT_SMAX, eps_in=MPL_OPT_EPS_IN,
                     inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE,
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
-                    warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE)
+                    warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE,
+                    omega=MPL_OPT_OMEGA)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 
