@@ -78,12 +78,25 @@ typedef enum {
                                      this value; 0 = never (default).  The selection widens its
                                      re-score band to the route's error bound, so the atoms
                                      chosen, and the solution, are the same on either route. */
-    MPL_OPT_OMEGA = 14            /* subspace exploratory matching (Algorithm 2, SMPL): each
+    MPL_OPT_OMEGA = 14,           /* subspace exploratory matching (Algorithm 2, SMPL): each
                                      outer iteration takes the omega*rho largest violators, solves
                                      the master problem with all of them, and keeps the rho with
                                      the largest |u| (ties to the larger correlation); the others
                                      leave S and may return later.  1 = Algorithm 1 (default),
                                      at most 16. */
+    MPL_OPT_STOP_RINF = 15,       /* early stopping, eq. (stop1) of Sec. 2.5: a signal stops at
+                                     the worst-case analysis once the certified bound on
+                                     |a_j^T xi| over the atoms outside S is <= this value.
+                                     Negative = off (default) */
+    MPL_OPT_STOP_R2 = 16,         /* eq. (stop1): stop once ||xi|| <= this value.  Negative =
+                                     off (default) */
+    MPL_OPT_STOP_EPS = 17         /* eq. (stop_con): stop after a master problem whose decrease
+                                     of the objective, f(x^{t-1}) - f(x^t), is <= this value
+                                     times |rho f(x^0)|, f(x^0) = ||b||^2 / 2.  Negative = off
+                                     (default).  A stopped signal gets the exact restricted
+                                     solution on its S and status MPL_SIG_EARLY_STOP; lambda = 0
+                                     (least squares, the OMP reduction of Sec. 2.5 with rho = 1)
+                                     needs one of these rules or MPL_OPT_MAX_OUTER to end. */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -92,7 +105,10 @@ typedef enum {
     MPL_SIG_MAX_OUTER = 1,      /* stopped by MPL_OPT_MAX_OUTER */
     MPL_SIG_CAPACITY = 2,       /* active set reached MPL_OPT_SMAX */
     MPL_SIG_UNCERTIFIED = 3,    /* exact finish failed repeatedly */
-    MPL_SIG_NONFINITE = 4       /* NaN/Inf met in the data or iterates */
+    MPL_SIG_NONFINITE = 4,      /* NaN/Inf met in the data or iterates */
+    MPL_SIG_EARLY_STOP = 5      /* stopped by an early-stopping rule (MPL_OPT_STOP_*); x is the
+                                   exact minimiser of eq. 2 restricted to the final S, the
+                                   atoms outside S are not certified */
 } mpl_signal_status_t;
 
 typedef struct {

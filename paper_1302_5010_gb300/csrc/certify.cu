@@ -106,42 +106,12 @@ __device__ __forceinline__ double bsum(double v, double* red) {
 }
 
 
-// Supports up to this size are factored and solved by one warp (no CTA barriers).
+// Supports up to this size are factored right-looking (chol_block_rl) and solved by one warp.
 constexpr int WARP_FACTOR_MAX = 64;
 
 // Left-looking (dot-product form) Cholesky, in place on the lower triangle of
-// M: column j is L_rj = (G_rj - sum_{q<j} L_rq L_jq) / L_jj.  The inner sums
-// read only finished columns, so their loads pipeline; rdiag receives 1/L_jj.
-// One warp (lanes over rows).  Returns 0, or -1 on a non-positive pivot.
-template <typename T>
-__device__ int chol_warp(T* M, int ld, int np, T* rdiag) {
-    const int lane = threadIdx.x & 31;
-    for (int j = 0; j < np; ++j) {
-        const T* Lj = M + (size_t)j * ld;
-        for (int r = j + lane; r < np; r += 32) {
-            const T* Lr = M + (size_t)r * ld;
-            T a0 = Lr[j], a1 = T(0);
-            int q = 0;
-            for (; q + 1 < j; q += 2) {
-                a0 -= Lr[q] * Lj[q];
-                a1 -= Lr[q + 1] * Lj[q + 1];
-            }
-            if (q < j) a0 -= Lr[q] * Lj[q];
-            M[(size_t)r * ld + j] = a0 + a1;
-        }
-        __syncwarp();
-        const T sj = M[(size_t)j * ld + j];
-        if (!(sj > T(0))) return -1;
-        const T dg = sqrt(sj), inv = T(1) / dg;
-        __syncwarp();
-        for (int r = j + lane; r < np; r += 32) M[(size_t)r * ld + j] = (r == j) ? dg : M[(size_t)r * ld + j] * inv;
-        if (lane == 0) rdiag[j] = inv;
-        __syncwarp();
-    }
-    return 0;
-}
-
-// Same, one row per thread across the CTA.
+// M, one row per thread across the CTA: column j is
+// L_rj = (G_rj - sum_{q<j} L_rq L_jq) / L_jj; rdiag receives 1/L_jj.
 template <typename T>
 __device__ int chol_block(T* M, int ld, int np, T* rdiag, int* flag) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -171,6 +141,40 @@ __device__ int chol_block(T* M, int ld, int np, T* rdiag, int* flag) {
         __syncthreads();
     }
     if (tid == 0) *flag = 0;
+    return 0;
+}
+
+// Right-looking Cholesky by the whole CTA for np <= 64 (lower triangle of M in
+// shared memory): per column, one thread takes the pivot, the column is scaled,
+// and the trailing triangle gets the rank-1 update with four threads per row
+// (every fourth column each).  Two CTA barriers per column instead of a serial
+// chain of dot products.  Returns 0 or -1 (non-positive pivot); flag likewise.
+template <typename T>
+__device__ int chol_block_rl(T* M, int ld, int np, T* rdiag, int* flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rq = tid & 63, cq = tid >> 6, cstep = nt >> 6;  // 64 row slots x (nt / 64) column phases
+    for (int j = 0; j < np; ++j) {
+        if (tid == 0) {
+            const T sj = M[(size_t)j * ld + j];
+            *flag = (sj > T(0)) ? 0 : 1;
+            if (sj > T(0)) {
+                const T dg = sqrt(sj);
+                M[(size_t)j * ld + j] = dg;
+                rdiag[j] = T(1) / dg;
+            }
+        }
+        __syncthreads();
+        if (*flag) return -1;
+        const T inv = rdiag[j];
+        for (int r = j + 1 + tid; r < np; r += nt) M[(size_t)r * ld + j] *= inv;
+        __syncthreads();
+        const int r = j + 1 + rq;
+        if (r < np) {
+            const T lr = M[(size_t)r * ld + j];
+            for (int c = j + 1 + cq; c <= r; c += cstep) M[(size_t)r * ld + c] -= lr * M[(size_t)c * ld + j];
+        }
+    }
+    __syncthreads();
     return 0;
 }
 
@@ -252,20 +256,10 @@ struct Factor {
 __device__ int factor(Factor& F, int np, int* flag) {
     if (!F.fp64) {
         if (np > WARP_FACTOR_MAX) return chol_block(F.Mf, F.ldf, np, F.rdf, flag);
-        if (threadIdx.x < 32) {
-            const int f = chol_warp(F.Mf, F.ldf, np, F.rdf);
-            if (threadIdx.x == 0) *flag = f;
-        }
-        __syncthreads();
-        return *flag;
+        return chol_block_rl(F.Mf, F.ldf, np, F.rdf, flag);
     }
     if (np > WARP_FACTOR_MAX) return chol_block(F.Md, F.ldd, np, F.rdd, flag);
-    if (threadIdx.x < 32) {
-        const int f = chol_warp(F.Md, F.ldd, np, F.rdd);
-        if (threadIdx.x == 0) *flag = f;
-    }
-    __syncthreads();
-    return *flag;
+    return chol_block_rl(F.Md, F.ldd, np, F.rdd, flag);
 }
 
 // v <- G_PP^{-1} v with the current factor (FP32 factor: solved in FP32).
@@ -299,6 +293,7 @@ struct FinShared {
     double red[32];
     int ival[4];
     double dval[4];
+    df part[FIN_THREADS / 32][32];  // per-warp partial dot products (dots_df_block)
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -426,6 +421,91 @@ __device__ double dot_ff(const float* __restrict__ a, const float* __restrict__ 
     return to_d(warp_df_sum(df_add(c0, c1)));
 }
 
+// r = b - A_P x in double-FP32 for n % 4 == 0: thread t owns the four entries
+// 4t + 4 nt c; the atom columns are read as float4, eight atoms per round so
+// that eight loads are in flight.  Each entry sums the atoms in order of P, as
+// residual_df does.
+__device__ void residual_df4(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
+                             const float* __restrict__ b, float* rh, float* rl) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = tid * 4; k < n; k += nt * 4) {
+        const float4 bv = __ldg(reinterpret_cast<const float4*>(b + k));
+        df c0{bv.x, 0.f}, c1{bv.y, 0.f}, c2{bv.z, 0.f}, c3{bv.w, 0.f};
+        int a = 0;
+        for (; a + 7 < np; a += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(A + (size_t)Pi[a + u] * n + k));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const df x = xd[a + u];
+                c0 = df_fma(c0, -v[u].x, x);
+                c1 = df_fma(c1, -v[u].y, x);
+                c2 = df_fma(c2, -v[u].z, x);
+                c3 = df_fma(c3, -v[u].w, x);
+            }
+        }
+        for (; a < np; ++a) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(A + (size_t)Pi[a] * n + k));
+            const df x = xd[a];
+            c0 = df_fma(c0, -v.x, x);
+            c1 = df_fma(c1, -v.y, x);
+            c2 = df_fma(c2, -v.z, x);
+            c3 = df_fma(c3, -v.w, x);
+        }
+        *reinterpret_cast<float4*>(rh + k) = make_float4(c0.hi, c1.hi, c2.hi, c3.hi);
+        *reinterpret_cast<float4*>(rl + k) = make_float4(c0.lo, c1.lo, c2.lo, c3.lo);
+    }
+}
+
+// out[a] = a_{idx[a]}^T r for a < cnt, in double-FP32, by the whole CTA
+// (n % 4 == 0): every thread takes its float4 slices of eight atoms at a time,
+// the warps reduce their partial sums, and the per-warp partials of each
+// group of 32 atoms are added in warp order (a fixed summation order).
+__device__ void dots_df_block(const float* __restrict__ A, int n, const int* idx, int cnt, const float* rh,
+                              const float* rl, double* out, df (*part)[32]) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int g0 = 0; g0 < cnt; g0 += 32) {
+        const int gc = min(32, cnt - g0);
+        for (int b0 = 0; b0 < gc; b0 += 8) {
+            const int bc = min(8, gc - b0);
+            df acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = df{0.f, 0.f};
+            for (int k = tid * 4; k < n; k += nt * 4) {
+                const float4 h4 = *reinterpret_cast<const float4*>(rh + k);
+                const float4 l4 = *reinterpret_cast<const float4*>(rl + k);
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = u < bc ? __ldg(reinterpret_cast<const float4*>(A + (size_t)idx[g0 + b0 + u] * n + k))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    acc[u] = df_fma(acc[u], v[u].x, df{h4.x, l4.x});
+                    acc[u] = df_fma(acc[u], v[u].y, df{h4.y, l4.y});
+                    acc[u] = df_fma(acc[u], v[u].z, df{h4.z, l4.z});
+                    acc[u] = df_fma(acc[u], v[u].w, df{h4.w, l4.w});
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u < bc) {
+                    const df t = warp_df_sum(acc[u]);
+                    if (lane == 0) part[warp][b0 + u] = t;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < gc) {
+            df t = part[0][tid];
+            for (int w = 1; w < nw; ++w) t = df_add(t, part[w][tid]);
+            out[g0 + tid] = to_d(t);
+        }
+        __syncthreads();
+    }
+}
+
 // Last resort for ill-conditioned blocks: G_PP recomputed from the atoms in
 // double-FP32 into the FP64 factor storage, then factored in FP64.
 __device__ int exact_factor(FinShared& sh, const float* A, int n, int np) {
@@ -444,14 +524,17 @@ __device__ int exact_factor(FinShared& sh, const float* A, int n, int np) {
 
 // Copy the lower triangle of G_PP into the current factor storage and factor it.
 __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < np; r += nw) {
-        const float* grow = Gi + (size_t)sh.P[r] * smax;
-        for (int c = lane; c <= r; c += 32) {
-            const float v = grow[sh.P[c]];
-            if (sh.F.fp64) sh.F.Md[(size_t)r * sh.F.ldd + c] = (double)v;
-            else sh.F.Mf[(size_t)r * sh.F.ldf + c] = v;
-        }
+    // the np x np lower triangle as one flat range of independent loads (row r holds
+    // entries r(r+1)/2 .. r(r+1)/2 + r)
+    const int tot = np * (np + 1) / 2;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        while (r * (r + 1) / 2 > e) --r;
+        const int c = e - r * (r + 1) / 2;
+        const float v = Gi[(size_t)sh.P[r] * smax + sh.P[c]];
+        if (sh.F.fp64) sh.F.Md[(size_t)r * sh.F.ldd + c] = (double)v;
+        else sh.F.Mf[(size_t)r * sh.F.ldf + c] = v;
     }
     __syncthreads();
     return factor(sh.F, np, &sh.ival[0]);
@@ -496,6 +579,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
     __syncthreads();
     const double lam = (double)d.lam[i];
     const double tol = d.tol;
+    const bool vec4 = (n & 3) == 0;  // float4 rows: block-cooperative residual and correlations
+    const bool lam0 = !(lam > 0.0);
+    // scale of the optimality conditions on S: lambda, or a bound on |a_j^T b| when lambda = 0
+    const double lsc = lam0 ? fmax((double)d.colmax * (double)d.bnorm[i], 1e-300) : lam;
     const int* Si = d.S + (size_t)i * smax;
     const float* Gi = d.G + (size_t)i * smax * smax;
     const float* hi = d.h + (size_t)i * smax;
@@ -507,7 +594,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
     for (int a = tid; a < s; a += nt) {
         const float v = xS[a];
         sh.x[a] = (double)v;
-        sh.sg[a] = v > 0.f ? 1 : (v < 0.f ? -1 : 0);
+        // lambda = 0 (least squares): every atom of S stays, signs play no part
+        sh.sg[a] = lam0 ? 1 : (v > 0.f ? 1 : (v < 0.f ? -1 : 0));
     }
     __syncthreads();
 
@@ -548,7 +636,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         __syncthreads();
         if (tid == 0) { sh.dval[1] = 2.0; sh.ival[2] = -1; sh.ival[3] = 0; }
         __syncthreads();
-        if (!exact_entry) {
+        if (!exact_entry && !lam0) {
           for (int a = tid; a < np; a += nt) {
             const int pa = sh.P[a];
             const double xa = sh.x[pa], za = sh.z[a];
@@ -629,14 +717,24 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         for (int ref = 0; ref < 24; ++ref) {
             for (int a = tid; a < np; a += nt) xd[a] = to_df(sh.x[sh.P[a]]);
             __syncthreads();
-            residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+            if (vec4) residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+            else residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
             __syncthreads();
             flops += 4ull * n * np;  // residual and on-support correlations
             double lmax = 0.0;
-            for (int a = warp; a < np; a += nw) {
-                const double dv = dot_df(d.A32 + (size_t)sh.Pi[a] * n, rh, rl, n) - lam * (double)sh.sg[sh.P[a]];
-                if (lane == 0) sh.w[a] = dv;
-                lmax = fmax(lmax, fabs(dv));
+            if (vec4) {
+                dots_df_block(d.A32, n, sh.Pi, np, rh, rl, sh.w, sh.part);
+                for (int a = tid; a < np; a += nt) {
+                    const double dv = sh.w[a] - lam * (double)sh.sg[sh.P[a]];
+                    sh.w[a] = dv;
+                    lmax = fmax(lmax, fabs(dv));
+                }
+            } else {
+                for (int a = warp; a < np; a += nw) {
+                    const double dv = dot_df(d.A32 + (size_t)sh.Pi[a] * n, rh, rl, n) - lam * (double)sh.sg[sh.P[a]];
+                    if (lane == 0) sh.w[a] = dv;
+                    lmax = fmax(lmax, fabs(dv));
+                }
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -645,7 +743,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             __syncthreads();
             dmax = 0.0;
             for (int q = 0; q < nw; ++q) dmax = fmax(dmax, sh.red[q]);
-            if (np == 0 || dmax <= 0.1 * tol * lam) break;
+            if (np == 0 || dmax <= 0.1 * tol * lsc) break;
             if (ref > 0 && dmax > 0.25 * dprev) {
                 // slow contraction: the FP32 factor limits it, refactor once in FP64
                 if (!sh.F.fp64) {
@@ -674,7 +772,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         __syncthreads();
         for (int a = tid; a < np; a += nt) {
             const int pa = sh.P[a];
-            if (!(sh.x[pa] * (double)sh.sg[pa] > 0.0)) { sh.sg[pa] = 0; sh.x[pa] = 0.0; sh.ival[0] = 1; }
+            if (!lam0 && !(sh.x[pa] * (double)sh.sg[pa] > 0.0)) { sh.sg[pa] = 0; sh.x[pa] = 0.0; sh.ival[0] = 1; }
         }
         __syncthreads();
         if (sh.ival[0]) continue;
@@ -682,19 +780,44 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         // exact check of the zero entries of S
         double cmax = 0.0;
         int worst = -1;
-        double worst_c = 0.0;
-        for (int a = warp; a < s; a += nw) {
-            if (sh.sg[a] != 0) continue;
-            const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
-            if (fabs(ca) > cmax) { cmax = fabs(ca); worst = a; worst_c = ca; }
+        if (vec4) {
+            // zero entries of S: atom indices after those of P in Pi, positions in z (free now)
+            int* zpos = reinterpret_cast<int*>(sh.z);
+            if (warp == 0) {
+                int base = 0;
+                for (int a0 = 0; a0 < s; a0 += 32) {
+                    const int a = a0 + lane;
+                    const bool z0 = a < s && sh.sg[a] == 0;
+                    const unsigned bal = __ballot_sync(0xffffffffu, z0);
+                    if (z0) {
+                        const int k = base + __popc(bal & ((1u << lane) - 1u));
+                        zpos[k] = a;
+                        sh.Pi[np + k] = Si[a];
+                    }
+                    base += __popc(bal);
+                }
+                if (lane == 0) sh.ival[2] = base;
+            }
+            __syncthreads();
+            const int nz = sh.ival[2];
+            dots_df_block(d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np, sh.part);
+            for (int k = tid; k < nz; k += nt) {
+                const double ca = sh.w[np + k];
+                if (fabs(ca) > cmax) { cmax = fabs(ca); worst = zpos[k]; }
+            }
+        } else {
+            for (int a = warp; a < s; a += nw) {
+                if (sh.sg[a] != 0) continue;
+                const double ca = dot_df(d.A32 + (size_t)Si[a] * n, rh, rl, n);
+                if (fabs(ca) > cmax) { cmax = fabs(ca); worst = a; }
+            }
         }
         if (tid == 0) sh.dval[3] = 0.0;
         __syncthreads();
-        if (lane == 0 && worst >= 0 && cmax > lam * (1.0 + tol)) {
+        if ((vec4 || lane == 0) && worst >= 0 && cmax > lam * (1.0 + tol)) {
             unsigned long long key = ((unsigned long long)__double_as_longlong(cmax) & ~0xFFFull) |
                                      (unsigned long long)(0xFFF - worst);
             atomicMax(reinterpret_cast<unsigned long long*>(&sh.dval[3]), key);
-            (void)worst_c;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
@@ -720,7 +843,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             if (sh.ival[0]) break;
             continue;
         }
-        kkt_on = fmax(dmax / lam, fmax(cmax_s - lam, 0.0) / lam);
+        kkt_on = fmax(dmax / lsc, fmax(cmax_s - lam, 0.0) / lsc);
         ok = kkt_on <= tol;
         break;
     }
@@ -770,6 +893,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             d.finalized[i] = 1;
             d.fails[i] = 0;
             d.finishes[i] += steps + 1;
+            if (d.early && d.early[i]) {  // an early-stopping rule ended this signal
+                d.state[i] = ST_DONE;
+                d.sstatus[i] = MPL_SIG_EARLY_STOP;
+            }
         }
     } else {
         // keep the (monotonically improved) point as the next warm start

@@ -77,6 +77,7 @@ struct mpl_ctx {
     // identity route (eq. batchQ): taken at outer iterations whose bound on |S| is <= qroute
     int qroute = 0;
     int omega = 1;           // subspace search length (Algorithm 2); 1 = Algorithm 1
+    double stop_rinf = -1.0, stop_r2 = -1.0, stop_eps = -1.0;  // early stopping (Sec. 2.5)
     float* Q = nullptr;      // m x m Gram matrix, built on first use, freed with the handle
     float* beta = nullptr;   // beta_cap x m
     int beta_cap = 0;
@@ -193,11 +194,12 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin,
-                    &d.list_apg, &d.explore};
+                    &d.list_apg, &d.explore, &d.early};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
     CK(alloc(h, &d.bnorm, (size_t)P));
     CK(alloc(h, &d.xl1, (size_t)P));
+    CK(alloc(h, &d.f0, (size_t)P));
     CK(alloc(h, &d.eps, (size_t)P));
     double** dbl[] = {&d.obj, &d.kkt_in, &d.kkt_out, &d.ginf, &d.rr, &d.rb};
     for (double** q : dbl) CK(alloc(h, q, (size_t)P));
@@ -446,6 +448,9 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v < 1 || v > 16) return MPL_ERR_ARG;
             h->omega = (int)v;
             return MPL_OK;
+        case MPL_OPT_STOP_RINF: h->stop_rinf = v < 0 ? -1.0 : v; return MPL_OK;
+        case MPL_OPT_STOP_R2: h->stop_r2 = v < 0 ? -1.0 : v; return MPL_OK;
+        case MPL_OPT_STOP_EPS: h->stop_eps = v < 0 ? -1.0 : v; return MPL_OK;
         default:
             return MPL_ERR_ARG;
     }
@@ -469,6 +474,9 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
         case MPL_OPT_OMEGA: *v = h->omega; return MPL_OK;
+        case MPL_OPT_STOP_RINF: *v = h->stop_rinf; return MPL_OK;
+        case MPL_OPT_STOP_R2: *v = h->stop_r2; return MPL_OK;
+        case MPL_OPT_STOP_EPS: *v = h->stop_eps; return MPL_OK;
         default: return MPL_ERR_ARG;
     }
 }
@@ -663,6 +671,9 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     d.p = p;
     d.rho = std::min(h->rho, m);
     d.omega = h->omega;
+    d.stop_rinf = (float)h->stop_rinf;
+    d.stop_r2 = (float)h->stop_r2;
+    d.stop_eps = (float)h->stop_eps;
     d.precision = h->precision;
     d.inner_max = h->inner_max;
     d.eps_in = (float)h->eps_in;
@@ -762,7 +773,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         const double sc = (ginf > lam && ginf > 0) ? lam / ginf : 1.0;
         const double D = -0.5 * sc * sc * rr + sc * rb;
         s.gap = obj > 0 ? (obj - D) / obj : 0.0;
-        if (s.status != MPL_SIG_CERTIFIED) all_ok = false;
+        if (s.status != MPL_SIG_CERTIFIED && s.status != MPL_SIG_EARLY_STOP) all_ok = false;
     }
     return all_ok ? MPL_OK : MPL_ERR_NOT_CONVERGED;
 }

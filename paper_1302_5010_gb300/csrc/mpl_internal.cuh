@@ -36,6 +36,7 @@ struct Dev {
     int n, m, p, smax, rho, mw;  // mw = words of the per-signal membership bitmap
     int precision;               // 0 plain FP32, 1 mixed BF16
     int omega;                   // subspace search length of Algorithm 2 (1 = Algorithm 1)
+    float stop_rinf, stop_r2, stop_eps;  // early-stopping thresholds of Sec. 2.5 (< 0: off)
     int inner_max;
     float eps_in;
     double tol;
@@ -76,6 +77,8 @@ struct Dev {
     int* fails;                  // p consecutive failed finishes
     int* sstatus;                // p mpl_signal_status_t
     int* explore;                // p atoms explored this iteration (Algorithm 2), 0 = keep all
+    int* early;                  // p 1 once an early-stopping rule fired
+    float* f0;                   // p f(x^0) = ||b||^2 / 2
     int* nnz;                    // p
     float* rnorm;                // p ||r|| upper bound
     float* eps;                  // p current eq. (inner) tolerance

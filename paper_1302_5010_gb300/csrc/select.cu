@@ -252,6 +252,11 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     const int i = d.act[cur][kblk];
     const int st0 = d.state[i];
     if (st0 == ST_DONE || st0 == ST_REFINE) return;  // no worst-case analysis this iteration
+    if (d.early && d.early[i] && pa.mode == SEL_NORMAL) {
+        // an early-stopping rule fired after the last master problem: finish on S
+        if (threadIdx.x == 0) { d.snew[i] = 0; d.state[i] = ST_FINALIZE; }
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SelSmem& sh = *reinterpret_cast<SelSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -453,6 +458,16 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
             int q = min(vc, want);
             if (q > d.smax - ss) q = d.smax - ss;
             if (no_grow) q = 0;
+            // early stopping, eq. (stop1): the residual norm, or the certified bound on the
+            // correlations outside S
+            // (only while violators remain: without them the stopping condition of eq. 8 holds)
+            const bool stop1 = d.early && vc > 0 &&
+                               ((d.stop_r2 >= 0.f && rn <= d.stop_r2) ||
+                                (d.stop_rinf >= 0.f && offb <= (double)d.stop_rinf));
+            if (stop1) {
+                d.early[i] = 1;
+                q = 0;
+            }
             if (d.explore) d.explore[i] = q > d.rho ? q : 0;  // prune to rho after the master problem
             if (q > 0) {
                 int* Si = d.S + (size_t)i * d.smax;
@@ -468,8 +483,13 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
                 d.snew[i] = q;
                 d.finalized[i] = 0;
                 d.state[i] = ST_GROW;
+            } else if (fin && stop1) {
+                // the current point is already the exact restricted solution
+                d.ginf[i] = fmax(d.ginf[i], offb);
+                d.state[i] = ST_DONE;
+                d.sstatus[i] = MPL_SIG_EARLY_STOP;
             } else if (fin) {
-                d.kkt_out[i] = fmax(offb - (double)lam, 0.0) / (double)lam;
+                d.kkt_out[i] = lam > 0.f ? fmax(offb - (double)lam, 0.0) / (double)lam : offb;
                 d.ginf[i] = fmax(d.ginf[i], offb);
                 d.state[i] = ST_DONE;
                 if (vc == 0) d.sstatus[i] = MPL_SIG_CERTIFIED;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
     const double bb = block_sum_d(ss, red);
     if (threadIdx.x == 0) {
         const float lam = d.lam[i];
-        const bool bad = nf || !(lam > 0.f) || !isfinite(lam);
+        const bool bad = nf || !(lam >= 0.f) || !isfinite(lam);  // lambda = 0: least squares
         d.state[i] = bad ? ST_DONE : ST_GROW;
         d.sstatus[i] = bad ? MPL_SIG_NONFINITE : MPL_SIG_MAX_OUTER;
         d.ssize[i] = 0;
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
         if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
         if (d.explore) d.explore[i] = 0;
+        if (d.early) { d.early[i] = 0; d.f0[i] = (float)(0.5 * bb); }
         d.eps[i] = d.eps_in;
         d.obj[i] = 0.5 * bb;
         d.rr[i] = bb;
@@ -435,7 +436,14 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
             t = tn;
         }
         for (int r = tid; r < s; r += blockDim.x) xi[r] = sh.u[r];
-        if (tid == 0) d.inner[i] += iters;
+        if (tid == 0) {
+            d.inner[i] += iters;
+            // early stopping, eq. (stop_con): decrease of f over this outer iteration's
+            // master problem (F0 is f at x^{t-1}, new entries at zero)
+            if (d.early && d.stop_eps >= 0.f && d.snew[i] > 0 &&
+                F0 - F <= d.stop_eps * fabsf((float)d.rho * d.f0[i]))
+                d.early[i] = 1;
+        }
         __syncthreads();
     }
 }

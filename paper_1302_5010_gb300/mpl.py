@@ -42,6 +42,9 @@ MPL_OPT_WARM_MAX = 11
 MPL_OPT_WARM_THRESHOLD = 12
 MPL_OPT_QROUTE = 13
 MPL_OPT_OMEGA = 14
+MPL_OPT_STOP_RINF = 15
+MPL_OPT_STOP_R2 = 16
+MPL_OPT_STOP_EPS = 17
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -54,6 +57,7 @@ MPL_SIG_MAX_OUTER = 1
 MPL_SIG_CAPACITY = 2
 MPL_SIG_UNCERTIFIED = 3
 MPL_SIG_NONFINITE = 4
+MPL_SIG_EARLY_STOP = 5
 
 EXPORTED = ("mpl_create", "bmpl_solve", "mpl_correlate", "mpl_destroy", "mpl_set_option", "mpl_get_option",
             "mpl_get_stats", "mpl_get_solution_f64", "mpl_get_phase_times", "mpl_get_launch_count",
@@ -308,7 +312,8 @@ class Solver:
                     inner_max=MPL_OPT_INNER_MAX, warm_start=MPL_OPT_WARM_START, profile=MPL_OPT_PROFILE,
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
                     warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE,
-                    omega=MPL_OPT_OMEGA)
+                    omega=MPL_OPT_OMEGA, stop_rinf=MPL_OPT_STOP_RINF, stop_r2=MPL_OPT_STOP_R2,
+                    stop_eps=MPL_OPT_STOP_EPS)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 
