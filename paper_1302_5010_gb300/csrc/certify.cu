@@ -293,7 +293,6 @@ struct FinShared {
     double red[32];
     int ival[4];
     double dval[4];
-    df part[FIN_THREADS / 32][32];  // per-warp partial dot products (dots_df_block)
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -458,51 +457,61 @@ __device__ void residual_df4(const float* __restrict__ A, int n, const int* Pi, 
     }
 }
 
-// out[a] = a_{idx[a]}^T r for a < cnt, in double-FP32, by the whole CTA
-// (n % 4 == 0): every thread takes its float4 slices of eight atoms at a time,
-// the warps reduce their partial sums, and the per-warp partials of each
-// group of 32 atoms are added in warp order (a fixed summation order).
-__device__ void dots_df_block(const float* __restrict__ A, int n, const int* idx, int cnt, const float* rh,
-                              const float* rl, double* out, df (*part)[32]) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int g0 = 0; g0 < cnt; g0 += 32) {
-        const int gc = min(32, cnt - g0);
-        for (int b0 = 0; b0 < gc; b0 += 8) {
-            const int bc = min(8, gc - b0);
-            df acc[8];
+// out[a] = a_{idx[a]}^T r for a < cnt, in double-FP32, two atoms per warp at a
+// time (n % 4 == 0): lane l takes the float4 slices k = 4l + 128q, up to eight
+// slices of both atoms in flight per round, the residual pair from shared
+// memory; one butterfly per pair (the first level splits the two atoms over the
+// half-warps).  Fixed summation order.
+__device__ void dots_df_warp(const float* __restrict__ A, int n, const int* idx, int cnt, const float* rh,
+                             const float* rl, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int a0 = 2 * warp; a0 < cnt; a0 += 2 * nw) {
+        const bool two = a0 + 1 < cnt;
+        const float* pa = A + (size_t)idx[a0] * n;
+        const float* pb = A + (size_t)idx[two ? a0 + 1 : a0] * n;
+        df sa0{0.f, 0.f}, sa1{0.f, 0.f}, sb0{0.f, 0.f}, sb1{0.f, 0.f};
+        for (int k0 = lane * 4; k0 < n; k0 += 128 * 8) {
+            float4 va[8], vb[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = df{0.f, 0.f};
-            for (int k = tid * 4; k < n; k += nt * 4) {
-                const float4 h4 = *reinterpret_cast<const float4*>(rh + k);
-                const float4 l4 = *reinterpret_cast<const float4*>(rl + k);
-                float4 v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    v[u] = u < bc ? __ldg(reinterpret_cast<const float4*>(A + (size_t)idx[g0 + b0 + u] * n + k))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    acc[u] = df_fma(acc[u], v[u].x, df{h4.x, l4.x});
-                    acc[u] = df_fma(acc[u], v[u].y, df{h4.y, l4.y});
-                    acc[u] = df_fma(acc[u], v[u].z, df{h4.z, l4.z});
-                    acc[u] = df_fma(acc[u], v[u].w, df{h4.w, l4.w});
-                }
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + 128 * q;
+                va[q] = k < n ? __ldg(reinterpret_cast<const float4*>(pa + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                vb[q] = (two && k < n) ? __ldg(reinterpret_cast<const float4*>(pb + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (u < bc) {
-                    const df t = warp_df_sum(acc[u]);
-                    if (lane == 0) part[warp][b0 + u] = t;
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + 128 * q;
+                if (k < n) {
+                    const float4 h4 = *reinterpret_cast<const float4*>(rh + k);
+                    const float4 l4 = *reinterpret_cast<const float4*>(rl + k);
+                    sa0 = df_fma(sa0, va[q].x, df{h4.x, l4.x});
+                    sa1 = df_fma(sa1, va[q].y, df{h4.y, l4.y});
+                    sa0 = df_fma(sa0, va[q].z, df{h4.z, l4.z});
+                    sa1 = df_fma(sa1, va[q].w, df{h4.w, l4.w});
+                    sb0 = df_fma(sb0, vb[q].x, df{h4.x, l4.x});
+                    sb1 = df_fma(sb1, vb[q].y, df{h4.y, l4.y});
+                    sb0 = df_fma(sb0, vb[q].z, df{h4.z, l4.z});
+                    sb1 = df_fma(sb1, vb[q].w, df{h4.w, l4.w});
                 }
             }
         }
-        __syncthreads();
-        if (tid < gc) {
-            df t = part[0][tid];
-            for (int w = 1; w < nw; ++w) t = df_add(t, part[w][tid]);
-            out[g0 + tid] = to_d(t);
+        df sa = df_add(sa0, sa1), sb = df_add(sb0, sb1);
+        // level 16: the lower half-warp keeps atom a, the upper atom b
+        const bool up = lane >= 16;
+        df send = up ? sa : sb, keep = up ? sb : sa;
+        df recv;
+        recv.hi = __shfl_xor_sync(0xffffffffu, send.hi, 16);
+        recv.lo = __shfl_xor_sync(0xffffffffu, send.lo, 16);
+        keep = up ? df_add(recv, keep) : df_add(keep, recv);  // partner order: lower lane first
+#pragma unroll
+        for (int o = 8; o; o >>= 1) {
+            df w;
+            w.hi = __shfl_xor_sync(0xffffffffu, keep.hi, o);
+            w.lo = __shfl_xor_sync(0xffffffffu, keep.lo, o);
+            keep = df_add(keep, w);
         }
-        __syncthreads();
+        if (lane == 0) out[a0] = to_d(keep);
+        if (lane == 16 && two) out[a0 + 1] = to_d(keep);
     }
 }
 
@@ -527,14 +536,29 @@ __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
     // the np x np lower triangle as one flat range of independent loads (row r holds
     // entries r(r+1)/2 .. r(r+1)/2 + r)
     const int tot = np * (np + 1) / 2;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        while (r * (r + 1) / 2 > e) --r;
-        const int c = e - r * (r + 1) / 2;
-        const float v = Gi[(size_t)sh.P[r] * smax + sh.P[c]];
-        if (sh.F.fp64) sh.F.Md[(size_t)r * sh.F.ldd + c] = (double)v;
-        else sh.F.Mf[(size_t)r * sh.F.ldf + c] = v;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * blockDim.x) {
+        // four loads in flight before the stores (the stores could alias them)
+        float v[4];
+        int rr[4], cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            rr[u] = -1;
+            if (e < tot) {
+                int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= e) ++r;
+                while (r * (r + 1) / 2 > e) --r;
+                rr[u] = r;
+                cc[u] = e - r * (r + 1) / 2;
+                v[u] = __ldg(Gi + (size_t)sh.P[r] * smax + sh.P[cc[u]]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (rr[u] < 0) continue;
+            if (sh.F.fp64) sh.F.Md[(size_t)rr[u] * sh.F.ldd + cc[u]] = (double)v[u];
+            else sh.F.Mf[(size_t)rr[u] * sh.F.ldf + cc[u]] = v[u];
+        }
     }
     __syncthreads();
     return factor(sh.F, np, &sh.ival[0]);
@@ -723,7 +747,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             flops += 4ull * n * np;  // residual and on-support correlations
             double lmax = 0.0;
             if (vec4) {
-                dots_df_block(d.A32, n, sh.Pi, np, rh, rl, sh.w, sh.part);
+                dots_df_warp(d.A32, n, sh.Pi, np, rh, rl, sh.w);
+                __syncthreads();
                 for (int a = tid; a < np; a += nt) {
                     const double dv = sh.w[a] - lam * (double)sh.sg[sh.P[a]];
                     sh.w[a] = dv;
@@ -800,7 +825,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             }
             __syncthreads();
             const int nz = sh.ival[2];
-            dots_df_block(d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np, sh.part);
+            dots_df_warp(d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np);
+            __syncthreads();
             for (int k = tid; k < nz; k += nt) {
                 const double ca = sh.w[np + k];
                 if (fabs(ca) > cmax) { cmax = fabs(ca); worst = zpos[k]; }

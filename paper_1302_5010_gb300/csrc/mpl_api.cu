@@ -573,7 +573,8 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     if (pt) pt->end(4, e0, h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     e0 = pt ? pt->begin_if(3, run) : nullptr;
-    if ((e = launch_gram(d, act_ub, run, nl)) != cudaSuccess) return e;
+    const int qmax = (t == 0 && h->warm == 2) ? d.rho + warm_additions(h, d) : d.omega * d.rho;
+    if ((e = launch_gram(d, act_ub, qmax, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(3, e0, run);
     e0 = pt ? pt->begin_if(5, run) : nullptr;
     if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) return e;
@@ -641,8 +642,12 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     const int n = h->n, m = h->m;
     int64_t nl = 0;
     if (!h->side) {
-        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&h->main, cudaStreamNonBlocking));
+        // the outer-iteration chain is the critical path: its blocks go first when an SM
+        // frees up; the exact finishes of converged signals fill in behind it
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
+        CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
         CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -915,8 +920,12 @@ static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const floa
 static mpl_status_t prop_setup(mpl_ctx* h) {
     CK(cudaSetDevice(h->dev));
     if (!h->side) {
-        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&h->main, cudaStreamNonBlocking));
+        // the outer-iteration chain is the critical path: its blocks go first when an SM
+        // frees up; the exact finishes of converged signals fill in behind it
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
+        CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
         CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));

@@ -139,7 +139,8 @@ cudaError_t launch_save_beta(const Dev& d, int cur, int act_n_ub, cudaStream_t s
 cudaError_t build_gram_q(const float* A32, int n, int m, float* Q, int* act, Counters* cnt, cudaStream_t s,
                          int64_t* nl);
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
-cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
+// qmax: most atoms a signal can take this iteration (picks the tile width).
+cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl);
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);

@@ -19,6 +19,19 @@
 
 namespace mpl {
 
+#ifdef MPL_SEL_TRACE
+// Per-signal phase cycle counters of the selection (diagnostic builds only):
+// [row cache, radix passes, collect, re-score, sort + state, calls]
+__device__ long long g_sel_trace[8192][8];
+#define ST_BEGIN long long st0_ = clock64();
+#define ST_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += clock64() - st0_; st0_ = clock64(); } while (0)
+#define ST_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += 1; } while (0)
+#else
+#define ST_BEGIN
+#define ST_ADD(slot) do {} while (0)
+#define ST_CNT(slot) do {} while (0)
+#endif
+
 namespace {
 
 __device__ __forceinline__ bool in_set(const uint32_t* msk, int j) {
@@ -49,6 +62,28 @@ __device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const
     return acc;
 }
 
+// Two fixed-order FP32 dots by one warp, sharing the loads of r (each in the
+// order of warp_dot_f32, so both equal what warp_dot_f32 returns).  n % 4 == 0.
+__device__ __forceinline__ void warp_dot2_f32(const float* __restrict__ a0, const float* __restrict__ a1,
+                                              const float* __restrict__ r, int n, int lane, float* c0, float* c1) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+    for (int k = lane * 4; k < n; k += 128) {
+        const float4 rv = __ldg(reinterpret_cast<const float4*>(r + k));
+        const float4 u = __ldg(reinterpret_cast<const float4*>(a0 + k));
+        const float4 v = __ldg(reinterpret_cast<const float4*>(a1 + k));
+        s0 = fmaf(u.x, rv.x, s0); s0 = fmaf(u.y, rv.y, s0); s0 = fmaf(u.z, rv.z, s0); s0 = fmaf(u.w, rv.w, s0);
+        s1 = fmaf(v.x, rv.x, s1); s1 = fmaf(v.y, rv.y, s1); s1 = fmaf(v.z, rv.z, s1); s1 = fmaf(v.w, rv.w, s1);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    *c0 = s0;
+    *c1 = s1;
+}
+
 __device__ __forceinline__ double warp_dot_f64(const float* __restrict__ a, const double* __restrict__ r,
                                                int n, int lane) {
     double acc = 0.0;
@@ -71,6 +106,7 @@ struct SelSmem {
     unsigned kc;                       // candidates collected
     unsigned vc;                       // violators
     unsigned bin, need;
+    unsigned lcnt;                     // keys in the chosen bin / gathered into the list
     unsigned outmax;                   // largest key outside K
     float offmax;                      // largest certified bound inside K
     int nonfinite;
@@ -111,55 +147,101 @@ __device__ void fill_cache(const float* row, const uint32_t* msk, int m, int mw,
 // over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.  The bin
 // holding the kth key is found by a block-wide suffix sum over the histogram
 // (each thread owns nb / blockDim.x consecutive bins).
-__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+// The histogram scan shared by the passes: the bin that holds the need-th
+// largest key (at most one thread finds it) and what is still needed inside it.
+__device__ void radix_pick(int nb, unsigned need, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int per = nb / nt;  // 4 or 2 consecutive bins per thread
+    unsigned own = 0;
+    for (int b = 0; b < per; ++b) own += sh.hist[tid * per + b];
+    // inclusive suffix sum over the block (higher threads hold larger keys)
+    unsigned suf = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
+        if (lane + o < 32) suf += v;
+    }
+    if (lane == 0) sh.wsum[warp] = suf;  // the warp's total
+    __syncthreads();
+    for (int w = warp + 1; w < nw; ++w) suf += sh.wsum[w];
+    const unsigned above = suf - own;  // keys in bins above this thread's
+    if (tid == 0) { sh.bin = 0; sh.need = need; }
+    __syncthreads();
+    if (above < need && suf >= need) {
+        unsigned cum = above;
+        int b = per - 1;
+        for (; b > 0; --b) {
+            const unsigned c = sh.hist[tid * per + b];
+            if (cum + c >= need) break;
+            cum += c;
+        }
+        sh.bin = (unsigned)(tid * per + b);
+        sh.need = need - cum;
+        sh.lcnt = sh.hist[tid * per + b];  // keys in the chosen bin
+    }
+    __syncthreads();
+}
+
+// Key of the kth largest score (1-based) among the m keys, by 3 radix passes
+// over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.  After the
+// first pass the keys of the chosen top bin (all the later passes look at) are
+// gathered into a list in shared memory when they fit, so the second and third
+// passes scan that list instead of all m keys.
+__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    unsigned* lst = reinterpret_cast<unsigned*>(sh.key);  // free until the violators are sorted
+    constexpr unsigned LCAP = sizeof(sh.key) / sizeof(unsigned);
     unsigned prefix = 0, pmask = 0;
     unsigned need = (unsigned)kth;
+    bool listed = false;
+    unsigned lcount = 0;
     for (int pass = 0; pass < 3; ++pass) {
         const int nb = pass < 2 ? 2048 : 1024;          // 11, 11, 10 bits
         const int sh_ = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
         for (int b = tid; b < nb; b += nt) sh.hist[b] = 0;
+        if (tid == 0) sh.lcnt = 0;
         __syncthreads();
-        int nf = 0;
-#pragma unroll 4
-        for (int j = tid; j < m; j += nt) {
-            const unsigned kj = key_of(row, msk, j, &nf);
-            if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
-        }
-        if (nf) sh.nonfinite = 1;
-        __syncthreads();
-        const int per = nb / nt;  // 4 or 2 consecutive bins per thread
-        unsigned own = 0;
-        for (int b = 0; b < per; ++b) own += sh.hist[tid * per + b];
-        // inclusive suffix sum over the block (higher threads hold larger keys)
-        unsigned suf = own;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned v = __shfl_down_sync(0xffffffffu, suf, o);
-            if (lane + o < 32) suf += v;
-        }
-        if (lane == 0) sh.wsum[warp] = suf;  // the warp's total
-        __syncthreads();
-        for (int w = warp + 1; w < nw; ++w) suf += sh.wsum[w];
-        const unsigned above = suf - own;  // keys in bins above this thread's
-        if (tid == 0) { sh.bin = 0; sh.need = need; }
-        __syncthreads();
-        if (above < need && suf >= need) {  // at most one thread
-            unsigned cum = above;
-            int b = per - 1;
-            for (; b > 0; --b) {
-                const unsigned c = sh.hist[tid * per + b];
-                if (cum + c >= need) break;
-                cum += c;
+        if (listed) {
+            for (unsigned e = tid; e < lcount; e += nt) {
+                const unsigned kj = lst[e];
+                if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
             }
-            sh.bin = (unsigned)(tid * per + b);
-            sh.need = need - cum;
+        } else {
+            int nf = 0;
+#pragma unroll 4
+            for (int j = tid; j < m; j += nt) {
+                const unsigned kj = key_of(row, msk, j, &nf);
+                if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
+            }
+            if (nf) sh.nonfinite = 1;
         }
         __syncthreads();
+        radix_pick(nb, need, sh);
         prefix |= sh.bin << sh_;
         pmask |= (unsigned)(nb - 1) << sh_;
         need = sh.need;
+        const unsigned inbin = sh.lcnt;
         __syncthreads();
+        if (pass == 0 && inbin <= LCAP && inbin > 0) {
+            // gather the keys of the chosen top bin (warp-aggregated slots)
+            if (tid == 0) sh.lcnt = 0;
+            __syncthreads();
+            int nf = 0;
+            for (int jb = tid - lane; jb < m; jb += nt) {
+                const int j = jb + lane;
+                const unsigned kj = j < m ? key_of(row, msk, j, &nf) : 0u;
+                const bool take = j < m && (kj & pmask) == prefix;
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                unsigned base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&sh.lcnt, (unsigned)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (take) lst[base + __popc(bal & ((1u << lane) - 1u))] = kj;
+            }
+            __syncthreads();
+            lcount = sh.lcnt;
+            listed = true;
+            __syncthreads();
+        }
     }
     return prefix;
 }
@@ -172,10 +254,18 @@ __device__ unsigned collect(const float* row, const uint32_t* msk, int m, unsign
     __syncthreads();
     int nf = 0;
     unsigned omax = 0;
-    for (int j = tid; j < m; j += nt) {
-        const unsigned kj = key_of(row, msk, j, &nf);
-        if (kj >= tkey && kj > 0u) {
-            const unsigned pos = atomicAdd(&sh.kc, 1u);
+    const int lane = tid & 31;
+    for (int jb = tid - lane; jb < m; jb += nt) {  // warp-aggregated slots
+        const int j = jb + lane;
+        unsigned kj = 0u;
+        if (j < m) kj = key_of(row, msk, j, &nf);
+        const bool take = j < m && kj >= tkey && kj > 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sh.kc, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+            const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
             if (pos < (unsigned)SEL_KCAP) sh.idx[pos] = j;
         } else if (kj > omax) {
             omax = kj;
@@ -284,18 +374,22 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     const int want = d.rho * d.omega;
     const int kth = prop ? min(pa.W, m) : min(want, m);
     bool exact_scores = false;  // row holds re-scores themselves (overflow fallback)
+    ST_BEGIN
     unsigned kc = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const float D = exact_scores ? 0.f : delta + delta32;
         const bool cache = m <= SEL_ROWCACHE;
         if (cache) fill_cache(row, msk, m, d.mw, sh);
+        ST_ADD(0);
         const uint32_t* mskc = cache ? sh.mk : msk;
         const unsigned kkey = radix_kth(cache ? sh.row : row, mskc, m, kth, sh);
+        ST_ADD(1);
         const float s_rho = __uint_as_float(kkey);
         float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
         kc = collect(cache ? sh.row : row, mskc, m, tkey, sh);
+        ST_ADD(2);
         if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
         // Too many candidates in the band: re-score every atom outside S in place
         // (this row is private to the signal) and select on the re-scores.
@@ -315,10 +409,24 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     if (tid == 0) { sh.vc = 0; sh.offmax = 0.f; }
     __syncthreads();
     float offmax = 0.f;
-    for (unsigned c = warp; c < kc; c += nwarps) {
+    const bool pair = (n & 3) == 0;  // two candidates per warp, sharing the residual loads
+    const unsigned cstep = pair ? 2u * nwarps : (unsigned)nwarps;
+    for (unsigned c0 = pair ? 2u * warp : (unsigned)warp; c0 < kc; c0 += cstep) {
+      float dots[2];
+      if (pair && c0 + 1 < kc) {
+          warp_dot2_f32(d.A32 + (size_t)sh.idx[c0] * n, d.A32 + (size_t)sh.idx[c0 + 1] * n, r32, n, lane,
+                        &dots[0], &dots[1]);
+      } else {
+          dots[0] = warp_dot_f32(d.A32 + (size_t)sh.idx[c0] * n, r32, n, lane);
+          dots[1] = 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const unsigned c = c0 + e;
+        if (c >= kc || (e == 1 && !pair)) break;
         const int j = sh.idx[c];
         const float* aj = d.A32 + (size_t)j * n;
-        const float c32 = fabsf(warp_dot_f32(aj, r32, n, lane));
+        const float c32 = fabsf(dots[e]);
         float score = c32;
         int viol = c32 > lam_sel;
         float certb = c32 + delta32;
@@ -330,9 +438,11 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
         }
         if (lane == 0) sh.sc[c] = viol ? score : -score;
         offmax = fmaxf(offmax, certb);
+      }
     }
     if (lane == 0 && offmax > 0.f) atomicMax(reinterpret_cast<unsigned*>(&sh.offmax), __float_as_uint(offmax));
     __syncthreads();
+    ST_ADD(3);
     if (prop) {
         // --- warm-start proposal / training examples: the top-W candidates by re-score
         float* wsm = reinterpret_cast<float*>(smem_raw + sizeof(SelSmem));
@@ -446,6 +556,8 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     if (vc > 1) sort_desc(sh, len);
 
     // State transition (one thread).
+    ST_ADD(4);
+    ST_CNT(5);
     if (tid == 0) {
         d.outer[i] += 1;
         if (sh.nonfinite) {
@@ -564,6 +676,19 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
 }
 
 }  // namespace
+
+#ifdef MPL_SEL_TRACE
+extern "C" int mpl_debug_sel_trace(long long* out, int count, int reset) {
+    if (count > 8192) count = 8192;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, g_sel_trace, sizeof(long long) * 8 * (size_t)count) != cudaSuccess) return -1;
+    if (reset) {
+        static long long zero[8192][8];
+        if (cudaMemcpyToSymbol(g_sel_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
+    }
+    return count;
+}
+#endif
 
 cudaError_t prepare_select() {
     static bool attr = false;

@@ -193,12 +193,13 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
     }
 }
 
-// Same tile and per-output summation order (k ascending, one FMA chain) as
-// k_gram, with the K slices staged by cp.async in a GS-deep ring so that
-// GS - 1 slices are in flight while one is consumed (the kernel is bound by the
-// latency of its L2 reads, not by its FLOPs).  Needs n % 4 == 0 (16-byte rows).
+// Same per-output summation order (k ascending, one FMA chain) as k_gram, with
+// the K slices staged by cp.async in a GS-deep ring so that GS - 1 slices are in
+// flight while one is consumed.  Tile BM rows (atoms of S) x BN columns (new
+// atoms, then b); each thread computes TR rows x TC columns.  The host takes the
+// narrow 32 x 16 tile when at most 15 atoms arrive per signal (the columns of a
+// wider tile would mostly be empty).  Needs n % 4 == 0 (16-byte rows).
 constexpr int GS = 4, GPAD = GBK + 4;
-constexpr size_t GRAM_SMEM = (size_t)GS * (GBM + GBN) * GPAD * sizeof(float);
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
@@ -208,76 +209,105 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+template <int BM, int BN, int TR, int TC>
 __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
+    static_assert((BM / TR) * (BN / TC) == 256, "one output block per thread");
+    constexpr int NX = BN / TC;                  // threads along the columns
+    constexpr int CHUNKS = (BM + BN) * (GBK / 4);  // 16-byte chunks per slice
     const int g = blockIdx.x;
     if (g >= d.cnt->grow_n) return;
     const int i = d.list_grow[g];
     const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
-    const int a0 = blockIdx.y * GBM;
+    const int a0 = blockIdx.y * BM;
     if (a0 >= s || q == 0) return;
     const int n = d.n, smax = d.smax;
     const int* Si = d.S + (size_t)i * smax;
     float* Gi = d.G + (size_t)i * smax * smax;
     extern __shared__ __align__(16) float gsm[];
-    float* As = gsm;                          // [GS][GBM][GPAD]
-    float* Bs = gsm + (size_t)GS * GBM * GPAD;  // [GS][GBN][GPAD]
+    float* As = gsm;                            // [GS][BM][GPAD]
+    float* Bs = gsm + (size_t)GS * BM * GPAD;   // [GS][BN][GPAD]
     const int tid = threadIdx.x;
-    const int ty = tid >> 3, tx = tid & 7;
-    // the three 16-byte chunks this thread stages per slice: A rows lr and lr + 32, B row lr
-    const int lr = tid >> 3, kc = (tid & 7) * 4;
+    const int ty = tid / NX, tx = tid % NX;
     const int nsl = (n + GBK - 1) / GBK;
-    for (int b0 = 0; b0 <= q; b0 += GBN) {
-        const int ra0 = a0 + lr, ra1 = a0 + lr + 32, rb = b0 + lr;
-        const float* pa0 = ra0 < s ? d.A32 + (size_t)Si[ra0] * n : nullptr;
-        const float* pa1 = ra1 < s ? d.A32 + (size_t)Si[ra1] * n : nullptr;
-        const float* pb = rb < q ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+    for (int b0 = 0; b0 <= q; b0 += BN) {
+        // source rows of this thread's chunks (c = tid + 256 e), fixed for the column chunk
+        constexpr int PER = (CHUNKS + 255) / 256;
+        const float* src[PER];
+        float* dst0[PER];
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int c = tid + 256 * e;
+            const int rr = c / (GBK / 4), kc = (c % (GBK / 4)) * 4;
+            const float* p = nullptr;
+            if (c < CHUNKS) {
+                if (rr < BM) {
+                    const int ra = a0 + rr;
+                    p = ra < s ? d.A32 + (size_t)Si[ra] * n : nullptr;
+                } else {
+                    const int rb = b0 + rr - BM;
+                    p = rb < q ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+                }
+            }
+            src[e] = p;
+            dst0[e] = c >= CHUNKS ? nullptr : (rr < BM ? As + (size_t)rr * GPAD + kc : Bs + (size_t)(rr - BM) * GPAD + kc);
+        }
         auto issue = [&](int sl) {
-            const int st = sl % GS, k = sl * GBK + kc;
-            const bool kin = k < n;
-            float* da = As + ((size_t)st * GBM + lr) * GPAD + kc;
-            float* db = Bs + ((size_t)st * GBN + lr) * GPAD + kc;
-            cp_async16(da, (pa0 && kin) ? pa0 + k : d.A32, (pa0 && kin) ? 16 : 0);
-            cp_async16(da + 32 * GPAD, (pa1 && kin) ? pa1 + k : d.A32, (pa1 && kin) ? 16 : 0);
-            cp_async16(db, (pb && kin) ? pb + k : d.A32, (pb && kin) ? 16 : 0);
+            const int st = sl % GS;
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                if (dst0[e] == nullptr) continue;
+                const int c = tid + 256 * e;
+                const int rr = c / (GBK / 4), kc = (c % (GBK / 4)) * 4, k = sl * GBK + kc;
+                float* dst = dst0[e] + (size_t)st * (rr < BM ? BM : BN) * GPAD;
+                const bool ok = src[e] != nullptr && k < n;
+                cp_async16(dst, ok ? src[e] + k : d.A32, ok ? 16 : 0);
+            }
         };
 #pragma unroll
         for (int sl = 0; sl < GS - 1; ++sl) {
             if (sl < nsl) issue(sl);
             cp_async_commit();
         }
-        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        float acc[TR][TC];
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+            for (int v = 0; v < TC; ++v) acc[u][v] = 0.f;
         for (int sl = 0; sl < nsl; ++sl) {
             cp_async_wait<GS - 2>();
             __syncthreads();
             if (sl + GS - 1 < nsl) issue(sl + GS - 1);
             cp_async_commit();
             const int st = sl % GS;
-            const float* Ar0 = As + ((size_t)st * GBM + ty * 2) * GPAD;
-            const float* Ar1 = Ar0 + GPAD;
-            const float* Bt = Bs + ((size_t)st * GBN + tx) * GPAD;
+            const float* Ar = As + ((size_t)st * BM + ty * TR) * GPAD;
+            const float* Bt = Bs + ((size_t)st * BN + tx) * GPAD;
 #pragma unroll
             for (int k = 0; k < GBK; k += 4) {
-                const float4 x0 = *reinterpret_cast<const float4*>(Ar0 + k);
-                const float4 x1 = *reinterpret_cast<const float4*>(Ar1 + k);
+                float4 x[TR];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const float4 y = *reinterpret_cast<const float4*>(Bt + (size_t)v * 8 * GPAD + k);
-                    acc[0][v] = fmaf(x0.x, y.x, acc[0][v]); acc[0][v] = fmaf(x0.y, y.y, acc[0][v]);
-                    acc[0][v] = fmaf(x0.z, y.z, acc[0][v]); acc[0][v] = fmaf(x0.w, y.w, acc[0][v]);
-                    acc[1][v] = fmaf(x1.x, y.x, acc[1][v]); acc[1][v] = fmaf(x1.y, y.y, acc[1][v]);
-                    acc[1][v] = fmaf(x1.z, y.z, acc[1][v]); acc[1][v] = fmaf(x1.w, y.w, acc[1][v]);
+                for (int u = 0; u < TR; ++u) x[u] = *reinterpret_cast<const float4*>(Ar + (size_t)u * GPAD + k);
+#pragma unroll
+                for (int v = 0; v < TC; ++v) {
+                    const float4 y = *reinterpret_cast<const float4*>(Bt + (size_t)v * NX * GPAD + k);
+#pragma unroll
+                    for (int u = 0; u < TR; ++u) {
+                        acc[u][v] = fmaf(x[u].x, y.x, acc[u][v]);
+                        acc[u][v] = fmaf(x[u].y, y.y, acc[u][v]);
+                        acc[u][v] = fmaf(x[u].z, y.z, acc[u][v]);
+                        acc[u][v] = fmaf(x[u].w, y.w, acc[u][v]);
+                    }
                 }
             }
         }
         cp_async_wait<0>();
         __syncthreads();  // the ring is reused by the next column chunk
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int a = a0 + ty * 2 + u;
+        for (int u = 0; u < TR; ++u) {
+            const int a = a0 + ty * TR + u;
             if (a >= s) continue;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int bb = b0 + tx + 8 * v;
+            for (int v = 0; v < TC; ++v) {
+                const int bb = b0 + tx + NX * v;
                 if (bb > q) continue;
                 if (bb == q) {
                     if (a >= s0) d.h[(size_t)i * smax + a] = acc[u][v];
@@ -291,9 +321,43 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
     }
 }
 
+template <int BM, int BN>
+constexpr size_t gram_smem() { return (size_t)GS * (BM + BN) * GPAD * sizeof(float); }
+
 // ------------------------------------------------------------------ APG
 // Gram block in shared memory when s <= gcap (<= APG_SMEM_S), else read from
 // global memory (L2).  Dynamic shared memory: [G gcap^2 | 6 vectors of vcap].
+// y = G x with TPR threads per row (s <= 256 / TPR): lane = row slot + (256 / TPR / 8)
+// ... the TPR threads of a row sit 32 / TPR lanes apart and take every TPR-th
+// column; their partial sums meet in a fixed butterfly.  With the packed leading
+// dimension ld = 32 / TPR (mod 32) the TPR column phases fall in disjoint banks.
+template <int TPR>
+__device__ __forceinline__ void gram_mv_split(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                              float* __restrict__ y) {
+    constexpr int RW = 32 / TPR;  // rows per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = lane / RW, r = warp * RW + (lane % RW);
+    float a = 0.f;
+    if (r < s)
+        for (int c = p; c < s; c += TPR) a = fmaf(G[(size_t)c * ld + r], x[c], a);
+#pragma unroll
+    for (int o = RW; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (p == 0 && r < s) y[r] = a;
+}
+
+// Packed leading dimension of an s x s block for gram_mv_split (see above).
+__host__ __device__ __forceinline__ int apg_ld(int s) {
+    if (s <= 64) return s + ((8 - s) & 31);    // = 8 (mod 32), TPR 4
+    if (s <= 128) return s + ((16 - s) & 31);  // = 16 (mod 32), TPR 2
+    return s;
+}
+
+// Floats reserved for a packed block of up to gcap atoms (padded rows included).
+__host__ __device__ __forceinline__ size_t apg_area(int gcap) {
+    const size_t g = (size_t)gcap, h = (size_t)(gcap < 128 ? gcap : 128);
+    return g * g > h * (h + 32) ? g * g : h * (h + 32);
+}
+
 __device__ __forceinline__ void gram_mv(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
                                         float* __restrict__ y) {
     // y = G x, one row per thread; G symmetric so column r is read with unit
@@ -324,7 +388,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
     const int tid = threadIdx.x;
     const int smax = d.smax;
     if (tid == 0) {
-        float* base = gsm + (size_t)gcap * gcap;
+        float* base = gsm + apg_area(gcap);
         sh.u = base; sh.up = base + vcap; sh.Gu = base + 2 * vcap;
         sh.Gup = base + 3 * vcap; sh.h = base + 4 * vcap; sh.v = base + 5 * vcap;
     }
@@ -345,13 +409,19 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         }
         const bool insm = s <= gcap;
         const float* G = insm ? gsm : Gg;
-        const int ld = insm ? s : smax;
+        const int ld = insm ? apg_ld(s) : smax;
         if (insm) {
             for (int e = tid; e < s * s; e += blockDim.x) {
                 const int r = e / s, c = e - r * s;
-                gsm[e] = Gg[(size_t)r * smax + c];
+                gsm[(size_t)r * ld + c] = Gg[(size_t)r * smax + c];
             }
         }
+        // the block's matrix-vector product: split rows while the block is small
+        auto mv = [&](const float* x, float* y) {
+            if (insm && s <= 64) gram_mv_split<4>(G, ld, s, x, y);
+            else if (insm && s <= 128) gram_mv_split<2>(G, ld, s, x, y);
+            else gram_mv(G, ld, s, x, y);
+        };
         float* xi = d.xS + (size_t)i * smax;
         float* ritz = d.ritz + (size_t)i * smax;
         const int prev = s - d.snew[i];  // ritz vector valid for the first `prev` entries
@@ -365,7 +435,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         float theta = 1.f;
         const int npow = (prev > 0 && d.outer[i] > 1) ? 6 : 14;
         for (int pi = 0; pi < npow; ++pi) {
-            gram_mv(G, ld, s, sh.v, sh.Gu);
+            mv(sh.v, sh.Gu);
             __syncthreads();
             float vv = 0.f, vg = 0.f;
             for (int r = tid; r < s; r += blockDim.x) { vv += sh.v[r] * sh.v[r]; vg += sh.v[r] * sh.Gu[r]; }
@@ -383,7 +453,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         float L = fmaxf(1.05f * theta, 1e-30f);
 
         // F(u) and G u at the warm start
-        gram_mv(G, ld, s, sh.u, sh.Gu);
+        mv(sh.u, sh.Gu);
         __syncthreads();
         float part = 0.f;
         for (int r = tid; r < s; r += blockDim.x) {
@@ -407,7 +477,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
                 sh.u[r] = z;
             }
             __syncthreads();
-            gram_mv(G, ld, s, sh.u, sh.Gu);
+            mv(sh.u, sh.Gu);
             __syncthreads();
             part = 0.f;
             for (int r = tid; r < s; r += blockDim.x)
@@ -725,19 +795,26 @@ cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl) {
 cudaError_t prepare_gram() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_gram_async, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAM_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gram_async<64, 32, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_smem<64, 32>());
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
-cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
+cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
-    dim3 grid(ub, (d.smax + GBM - 1) / GBM);
     if ((d.n & 3) == 0) {
         cudaError_t ep = prepare_gram();
         if (ep != cudaSuccess) return ep;
-        k_gram_async<<<grid, 256, GRAM_SMEM, s>>>(d);
+        if (qmax + 1 <= 16) {  // the new atoms and b fit one 16-column tile
+            dim3 grid(ub, (d.smax + 31) / 32);
+            k_gram_async<32, 16, 1, 2><<<grid, 256, gram_smem<32, 16>(), s>>>(d);
+        } else {
+            dim3 grid(ub, (d.smax + 63) / 64);
+            k_gram_async<64, 32, 2, 4><<<grid, 256, gram_smem<64, 32>(), s>>>(d);
+        }
     } else {
+        dim3 grid(ub, (d.smax + GBM - 1) / GBM);
         k_gram<false><<<grid, 256, 0, s>>>(d);
     }
     ++*nl;
@@ -747,7 +824,7 @@ cudaError_t launch_gram(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
 cudaError_t prepare_apg() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    const int mx = (int)(((size_t)APG_SMEM_S * APG_SMEM_S + 6 * 1024) * sizeof(float));
+    const int mx = (int)((apg_area(APG_SMEM_S) + 6 * 1024) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(k_apg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) attr = true;
     return e;
@@ -758,7 +835,7 @@ cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, 
     vcap = ((vcap + 31) / 32) * 32;
     if (vcap > d.smax) vcap = d.smax;
     const int gcap = vcap < APG_SMEM_S ? vcap : APG_SMEM_S;
-    const size_t dyn = ((size_t)gcap * gcap + 6 * (size_t)vcap) * sizeof(float);
+    const size_t dyn = (apg_area(gcap) + 6 * (size_t)vcap) * sizeof(float);
     cudaError_t ep = prepare_apg();
     if (ep != cudaSuccess) return ep;
     int per_sm = 0;
