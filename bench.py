@@ -31,6 +31,17 @@ UNIT = "signals/s"
 TOL = 1e-6
 FP32_LANES_PER_SM = 128
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
+# roofline block reports, from the ncu captures summarised under profiles/ (set to None when
+# the kernel changes after its capture).
+TRAFFIC = {
+    "k_finish": {"bytes_per_launch": (15.214080e6 + 3.920128e6) / 2,
+                 "capture": "profiles/k_finish_c2.md (launches 5 and 6 of the 1024 x 8192, p = 256 solve)"},
+    "k_corr_bf16": {"bytes_per_launch": 17.319424e6,
+                    "capture": "profiles/k_corr_bf16_c2.md (first outer iteration, 256 signals)"},
+    "k_corr_f32": None,
+}
+
 
 def workload_desc(cfg: str, P, path: str) -> dict:
     meta = P.meta
@@ -234,7 +245,14 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     stream = torch.cuda.current_stream()
     # one-time tuning on the batch (identity route, handshake cadence), like the layout
     # work of mpl_create it is outside the timed region
-    tune = None if args.no_autotune else solver.autotune(B, lam, TOL, stream)
+    tune = None
+    if args.tune:
+        qr, se = (int(v) for v in args.tune.split(","))
+        solver.set(mpl.MPL_OPT_QROUTE, qr)
+        solver.set(mpl.MPL_OPT_SYNC_EVERY, se)
+        tune = {"qroute": qr, "sync_every": se, "fixed": True}
+    elif not args.no_autotune:
+        tune = solver.autotune(B, lam, TOL, stream)
     # phase timing events ride inside the captured iteration graphs; warm up with
     # the same setting so that the timed steps only replay graphs
     solver.set(mpl.MPL_OPT_PROFILE, 1)
@@ -247,7 +265,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, phase_tot, launches, certified = [], np.zeros(10), 0, True
+    step_ms, phase_tot, launches, certified = [], np.zeros(11), 0, True
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -305,16 +323,22 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         gemm = {"kernel": "k_corr_bf16", "bound": "tensor", "achieved": gemm_ach, "peak": pk["bf16_tflops"],
                 "unit": "TFLOP/s", "frac": gemm_ach / pk["bf16_tflops"],
                 "peak_note": f"dense bf16, of {pk['source']}"}
-    gemm.update({"ms_per_step": corr_ms, "flop_per_step": flops})
+    gemm.update({"ms_per_step": corr_ms, "flop_per_step": flops,
+                 "identity_route_ms_per_step": phase_tot[10] / args.steps,
+                 "identity_route_columns_per_step": phase_tot[9] / args.steps})
     if fin_ms > corr_ms:
         ach = fin_flops / (fin_ms / 1e3) / 1e12 if fin_ms > 0 else 0.0
+        tr = TRAFFIC.get("k_finish")
         roof = {"kernel": "k_finish", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None,
+                "frac": ach / fp32_peak, "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_unit": "bytes per launch", "traffic_source": tr["capture"] if tr else None,
                 "peak_note": "FP32 FMA peak from unit counts and max SM clock; the kernel is latency-bound "
                              "(dependent factor/solve sweeps)",
                 "ms_per_step": fin_ms, "flop_per_step": fin_flops}
     else:
-        roof = dict(gemm, traffic=None)
+        tr = TRAFFIC.get(gemm["kernel"])
+        roof = dict(gemm, traffic=tr["bytes_per_launch"] if tr else None, traffic_unit="bytes per launch",
+                    traffic_source=tr["capture"] if tr else None)
     # summed event times per phase (the finish runs on a second stream, so phases overlap)
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if v > 0}
 
@@ -338,6 +362,8 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default route and handshake cadence")
+    ap.add_argument("--tune", default=None, metavar="QROUTE,SYNC",
+                    help="fix the tuned settings instead of running the autotuner (profiling runs)")
     ap.add_argument("--ref-signals", type=int, default=64)
     ap.add_argument("--cpu-signals", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")

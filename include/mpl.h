@@ -250,7 +250,9 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
  * entry 8 the algorithmic FLOPs of the exact finish (factorisations, solves,
  * residual and correlation sums); entry 9 how many of the entry-7 columns the
  * identity route (MPL_OPT_QROUTE) scored instead of the GEMM; 7..9 always
- * filled.  Returns the number of values written (<= cap, <= 10). */
+ * filled.  Entry 10: device milliseconds of the identity-route scoring (entry
+ * 1 then holds the GEMM alone).  Returns the number of values written (<= cap,
+ * <= 11). */
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
 
 /* Autotuner of the batched solve (no counterpart in the paper, which has no

@@ -37,9 +37,11 @@ __device__ __forceinline__ float4 load4(const float* row, int k, int n) {
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
     const int act_n = d.cnt->act_n_of(cur);
-    const int k0 = blockIdx.y * BN;
+    // signal tiles vary fastest, so the blocks in flight share their atom tile in L2
+    // (the dictionary streams from HBM once per launch)
+    const int k0 = blockIdx.x * BN;
     if (k0 >= act_n) return;
-    const int j0 = blockIdx.x * BM;
+    const int j0 = blockIdx.y * BM;
     const int n = d.n, m = d.m;
     const int* act = d.act_of(cur);
 
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
 
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
-    dim3 grid((d.m + BM - 1) / BM, (act_n_ub + BN - 1) / BN);
+    dim3 grid((act_n_ub + BN - 1) / BN, (d.m + BM - 1) / BM);
     const bool vec = (d.n % 4) == 0;
     if (vec) k_corr_f32<true><<<grid, 256, 0, s>>>(d, cur);
     else k_corr_f32<false><<<grid, 256, 0, s>>>(d, cur);

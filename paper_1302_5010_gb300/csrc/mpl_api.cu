@@ -99,7 +99,7 @@ struct mpl_ctx {
     int last_p = 0;
     std::vector<mpl_signal_stats_t> stats;
     int64_t launches = 0;
-    double phase_ms[10] = {0};
+    double phase_ms[11] = {0};
     std::vector<cudaEvent_t> evpool;
 };
 
@@ -204,6 +204,9 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     double** dbl[] = {&d.obj, &d.kkt_in, &d.kkt_out, &d.ginf, &d.rr, &d.rb};
     for (double** q : dbl) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.cnt, 1));
+    CK(alloc(h, &d.ovf_cnt, 1));
+    CK(alloc(h, &d.ovf_list, (size_t)P));
+    CK(cudaMemset(d.ovf_cnt, 0, sizeof(Counters)));
     CK(alloc(h, &h->Bint, pn));
     CK(alloc(h, &h->lamint, (size_t)P));
     CK(cudaMemset(d.xS, 0, ps * sizeof(float)));
@@ -259,6 +262,9 @@ void set_bounds(mpl_ctx* h, Dev& d) {
     }
 }
 
+// Phase index of the identity-route correlation (timed apart from the GEMM).
+constexpr int PH_QROUTE = 10;
+
 struct PhaseTimer {
     mpl_ctx* h;
     cudaStream_t s;
@@ -297,11 +303,12 @@ struct PhaseTimer {
         marks.push_back({phase, {b, e}});
     }
     cudaEvent_t begin_if(int phase, cudaStream_t on = nullptr) {
-        if (only_a >= 0 && phase != only_a && phase != only_b) return nullptr;
+        if (only_a >= 0 && phase != only_a && phase != only_b && phase != PH_QROUTE) return nullptr;
         return begin(on);
     }
     void collect() {
         for (int k = 0; k < 7; ++k) h->phase_ms[k] = 0.0;
+        h->phase_ms[PH_QROUTE] = 0.0;
         add(marks);
     }
     void add(const std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>& mks) {
@@ -532,7 +539,8 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     const int no_grow = t >= h->max_outer;
     const int route = iteration_route(h, d, t);
     cudaError_t e;
-    cudaEvent_t e0 = pt ? pt->begin_if(1, run) : nullptr;
+    const int ph_corr = route == ROUTE_Q ? PH_QROUTE : 1;
+    cudaEvent_t e0 = pt ? pt->begin_if(ph_corr, run) : nullptr;
     if (route == ROUTE_Q) {
         if ((e = launch_corr_q(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     } else if (h->precision == 1 && route == ROUTE_GEMM) {
@@ -542,7 +550,7 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
         if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     }
     if (t == 0 && h->qroute > 0 && (e = launch_save_beta(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-    if (pt) pt->end(1, e0, run);
+    if (pt) pt->end(ph_corr, e0, run);
     e0 = pt ? pt->begin_if(2, run) : nullptr;
     if (t == 0 && h->warm == 2) {
         // learned warm start: the first worst-case analysis also admits the atoms the
@@ -557,6 +565,27 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
         if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa, route)) != cudaSuccess) return e;
     } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, nullptr, route)) != cudaSuccess) {
         return e;
+    }
+    if (d.ovf_list) {
+        // second pass for the signals whose band overflowed: FP32 correlations of just
+        // those residuals, then their selection with the FP32 band
+        Dev d2 = d;
+        d2.act[cur] = d.ovf_list;
+        d2.cnt = d.ovf_cnt;
+        d2.ovf_list = nullptr;
+        if ((e = launch_corr_f32(d2, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        if (t == 0 && h->warm == 2) {
+            PropArgs pa{};
+            pa.mode = SEL_PROPOSE;
+            pa.W = std::min(h->warm_w, d.m);
+            pa.cap = h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax);
+            pa.thr = (float)h->warm_thr;
+            pa.w = h->pwb;
+            pa.rn = h->rn;
+            if ((e = launch_select(d2, cur, no_grow, act_ub, run, nl, &pa, ROUTE_GEMM_F32)) != cudaSuccess) return e;
+        } else if ((e = launch_select(d2, cur, no_grow, act_ub, run, nl, nullptr, ROUTE_GEMM_F32)) != cudaSuccess) {
+            return e;
+        }
     }
     if ((e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(2, e0, run);
@@ -689,6 +718,9 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     d.B = h->Bint;
     d.lam = h->lamint;
     set_bounds(h, d);
+    // a second, FP32 selection pass for bands that overflow the candidate buffer: only
+    // for the wide bands (BF16 GEMM, identity route) of dictionaries above the row cache
+    if (!((h->precision == 1 || h->qroute > 0) && m > SEL_ROWCACHE_ATOMS)) d.ovf_list = nullptr;
     if (h->precision == 1 && h->tmap_p != h->cap_p) {
         CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
         h->tmap_p = h->cap_p;
@@ -708,7 +740,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     int act_ub = p;
     const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
-    double graph_phase[8] = {0};
+    double graph_phase[11] = {0};
     for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
         if (graph) {
             size_t gi = 0;
@@ -757,6 +789,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     CK(cudaStreamSynchronize(st));
     pt.collect();
     for (int k = 1; k < 7; ++k) h->phase_ms[k] += graph_phase[k];
+    h->phase_ms[PH_QROUTE] += graph_phase[PH_QROUTE];
     h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
     h->phase_ms[8] = (double)h->cnt_h->fin_flops;  // algorithmic FLOPs of the exact finish
     h->phase_ms[9] = (double)h->cnt_h->qcols;      // of those columns, scored by the identity route
@@ -888,6 +921,7 @@ static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const floa
         d.A16 = h->A16;
         d.B = h->Bint;
         d.lam = h->lamint;
+        d.ovf_list = nullptr;  // example mode keeps the in-kernel fallback
         set_bounds(h, d);
         CK(launch_init(d, st, &nl));
         if (h->precision == 1) {
@@ -1091,7 +1125,7 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
 
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
     if (!h || !ms_out) return 0;
-    const int k = std::min(cap, 10);
+    const int k = std::min(cap, 11);
     for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
     return k;
 }

@@ -89,6 +89,8 @@ struct Dev {
     double* rr;                  // p ||r||^2
     double* rb;                  // p r^T b
     int* act[2];                 // active lists (signal ids), by outer-iteration parity
+    int* ovf_list;               // signals whose candidate band overflowed (second pass), or null
+    Counters* ovf_cnt;           // its length in act_n[parity]
     int* list_grow;              // signals with new atoms
     int* list_fin;               // signals sent to the exact finish
     int* list_apg;               // master-problem work list
@@ -174,6 +176,7 @@ enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SH
 // Candidate capacity of the selection kernel (per signal, in shared memory).
 constexpr int SEL_KCAP = 4096;
 constexpr int SEL_THREADS = 512;
+constexpr int SEL_ROWCACHE_ATOMS = 8192;  // score rows up to this length are cached in shared memory
 // Master problem: Gram block kept in shared memory up to this size.
 constexpr int APG_SMEM_S = 200;
 constexpr int APG_THREADS = 256;

@@ -93,15 +93,15 @@ __device__ __forceinline__ double warp_dot_f64(const float* __restrict__ a, cons
     return acc;
 }
 
-constexpr int SEL_ROWCACHE = 8192;  // score rows up to this length stay in shared memory
+constexpr int SEL_ROWCACHE = SEL_ROWCACHE_ATOMS;
 
 struct SelSmem {
     unsigned hist[2048];
     unsigned long long key[SEL_KCAP];  // sort keys of the violators
     int idx[SEL_KCAP];                 // candidate atoms
     float sc[SEL_KCAP];                // their re-scores, negated for non-violators
-    float row[SEL_ROWCACHE];           // the signal's score row (when m fits)
-    uint32_t mk[SEL_ROWCACHE / 32];    // and its membership bitmap
+    float row[SEL_ROWCACHE];           // selection keys of the signal's scores (when m fits): the
+                                       // bits of |c_j|, 0 for members of S and non-finite scores
     unsigned wsum[32];                 // per-warp partial sums of the histogram scan
     unsigned kc;                       // candidates collected
     unsigned vc;                       // violators
@@ -114,6 +114,13 @@ struct SelSmem {
 
 // Key of atom j: the IEEE bits of |score| (monotone for non-negative floats);
 // members of S and non-finite scores key to 0 (non-finite is flagged).
+__device__ __forceinline__ unsigned key_of(const float* v, const uint32_t* msk, int j, int u, int* nf) {
+    if (in_set(msk, j)) return 0u;
+    const unsigned b = __float_as_uint(fabsf(v[u]));
+    if (b >= 0x7f800000u) { *nf = 1; return 0u; }
+    return b;
+}
+
 __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk, int j, int* nf) {
     if (in_set(msk, j)) return 0u;
     const float v = fabsf(row[j]);
@@ -124,8 +131,10 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
 
 // Copy the score row and the membership bitmap into shared memory (loads
 // batched eight deep so that they are in flight together).
-__device__ void fill_cache(const float* row, const uint32_t* msk, int m, int mw, SelSmem& sh) {
+__device__ void fill_cache(const float* row, const uint32_t* msk, int m, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    unsigned* keys = reinterpret_cast<unsigned*>(sh.row);
+    int nf = 0;
     for (int j0 = tid; j0 < m; j0 += 8 * nt) {
         float v[8];
 #pragma unroll
@@ -136,12 +145,24 @@ __device__ void fill_cache(const float* row, const uint32_t* msk, int m, int mw,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int j = j0 + u * nt;
-            if (j < m) sh.row[j] = v[u];
+            if (j < m) keys[j] = key_of(v, msk, j, u, &nf);
         }
     }
-    for (int w = tid; w < mw; w += nt) sh.mk[w] = msk[w];
+    if (nf) sh.nonfinite = 1;
     __syncthreads();
 }
+
+// Keys read from the cache (S members and non-finite scores already 0) or
+// computed from the score row in global memory.
+struct CachedKeys {
+    const unsigned* k;
+    __device__ __forceinline__ unsigned operator()(int j, int*) const { return k[j]; }
+};
+struct RowKeys {
+    const float* row;
+    const uint32_t* msk;
+    __device__ __forceinline__ unsigned operator()(int j, int* nf) const { return key_of(row, msk, j, nf); }
+};
 
 // Key of the kth largest score (1-based) among the m keys, by 3 radix passes
 // over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.  The bin
@@ -187,7 +208,8 @@ __device__ void radix_pick(int nb, unsigned need, SelSmem& sh) {
 // first pass the keys of the chosen top bin (all the later passes look at) are
 // gathered into a list in shared memory when they fit, so the second and third
 // passes scan that list instead of all m keys.
-__device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh) {
+template <typename K>
+__device__ unsigned radix_kth(K key, int m, int kth, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     unsigned* lst = reinterpret_cast<unsigned*>(sh.key);  // free until the violators are sorted
     constexpr unsigned LCAP = sizeof(sh.key) / sizeof(unsigned);
@@ -210,7 +232,7 @@ __device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int 
             int nf = 0;
 #pragma unroll 4
             for (int j = tid; j < m; j += nt) {
-                const unsigned kj = key_of(row, msk, j, &nf);
+                const unsigned kj = key(j, &nf);
                 if ((kj & pmask) == prefix) atomicAdd(&sh.hist[(kj >> sh_) & (nb - 1)], 1u);
             }
             if (nf) sh.nonfinite = 1;
@@ -229,7 +251,7 @@ __device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int 
             int nf = 0;
             for (int jb = tid - lane; jb < m; jb += nt) {
                 const int j = jb + lane;
-                const unsigned kj = j < m ? key_of(row, msk, j, &nf) : 0u;
+                const unsigned kj = j < m ? key(j, &nf) : 0u;
                 const bool take = j < m && (kj & pmask) == prefix;
                 const unsigned bal = __ballot_sync(0xffffffffu, take);
                 unsigned base = 0;
@@ -248,7 +270,8 @@ __device__ unsigned radix_kth(const float* row, const uint32_t* msk, int m, int 
 
 // Collect { j not in S : key >= tkey } into sh.idx (capacity SEL_KCAP) and the
 // largest key left outside.  Returns the number found (may exceed the capacity).
-__device__ unsigned collect(const float* row, const uint32_t* msk, int m, unsigned tkey, SelSmem& sh) {
+template <typename K>
+__device__ unsigned collect(K key, int m, unsigned tkey, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) { sh.kc = 0; sh.outmax = 0; }
     __syncthreads();
@@ -258,7 +281,7 @@ __device__ unsigned collect(const float* row, const uint32_t* msk, int m, unsign
     for (int jb = tid - lane; jb < m; jb += nt) {  // warp-aggregated slots
         const int j = jb + lane;
         unsigned kj = 0u;
-        if (j < m) kj = key_of(row, msk, j, &nf);
+        if (j < m) kj = key(j, &nf);
         const bool take = j < m && kj >= tkey && kj > 0u;
         const unsigned bal = __ballot_sync(0xffffffffu, take);
         unsigned base = 0;
@@ -379,18 +402,25 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     for (int attempt = 0; attempt < 2; ++attempt) {
         const float D = exact_scores ? 0.f : delta + delta32;
         const bool cache = m <= SEL_ROWCACHE;
-        if (cache) fill_cache(row, msk, m, d.mw, sh);
+        if (cache) fill_cache(row, msk, m, sh);
         ST_ADD(0);
-        const uint32_t* mskc = cache ? sh.mk : msk;
-        const unsigned kkey = radix_kth(cache ? sh.row : row, mskc, m, kth, sh);
+        const CachedKeys ck{reinterpret_cast<const unsigned*>(sh.row)};
+        const RowKeys rk{row, msk};
+        const unsigned kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_ADD(1);
         const float s_rho = __uint_as_float(kkey);
         float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
-        kc = collect(cache ? sh.row : row, mskc, m, tkey, sh);
+        kc = cache ? collect(ck, m, tkey, sh) : collect(rk, m, tkey, sh);
         ST_ADD(2);
         if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
+        if (d.ovf_list) {
+            // the band of this route is too wide: this signal is selected again from FP32
+            // correlations (second pass of the iteration, narrower band)
+            if (tid == 0) d.ovf_list[atomicAdd(&d.ovf_cnt->act_n[cur], 1)] = i;
+            return;
+        }
         // Too many candidates in the band: re-score every atom outside S in place
         // (this row is private to the signal) and select on the re-scores.
         for (int j = warp; j < m; j += nwarps) {
@@ -666,6 +696,7 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
         __syncthreads();
     }
     if (tid == 0) {
+        if (d.ovf_cnt) d.ovf_cnt->act_n[cur ^ 1] = 0;  // next iteration's second-pass list
         d.cnt->cols += (unsigned long long)nact;
         d.cnt->grow_n = base[0];
         d.cnt->apg_n = base[0];

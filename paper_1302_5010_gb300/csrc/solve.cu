@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
         if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
         if (d.explore) d.explore[i] = 0;
+        if (i == 0 && d.ovf_cnt) { d.ovf_cnt->act_n[0] = 0; d.ovf_cnt->act_n[1] = 0; }
         if (d.early) { d.early[i] = 0; d.f0[i] = (float)(0.5 * bb); }
         d.eps[i] = d.eps_in;
         d.obj[i] = 0.5 * bb;

@@ -270,8 +270,8 @@ def mpl_get_solution_f64(h, p: int, X64) -> None:
 
 
 def mpl_get_phase_times(h) -> list:
-    buf = (ctypes.c_double * 10)()
-    k = load().mpl_get_phase_times(h, buf, 10)
+    buf = (ctypes.c_double * 11)()
+    k = load().mpl_get_phase_times(h, buf, 11)
     return [buf[i] for i in range(k)]
 
 
@@ -289,7 +289,7 @@ def mpl_get_launch_count(h) -> int:
 
 
 PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "corr_columns",
-          "finish_flops", "qroute_columns")
+          "finish_flops", "qroute_columns", "qroute")
 
 
 @dataclass

@@ -33,3 +33,17 @@ def test_c3_shape_mixed_subset():
     X, X64, res = solve_gpu(P, precision=1, smax=1024)
     assert_certified(res)
     check_against_oracle(P, X64, oracle_solve(P))
+
+
+@pytest.mark.parametrize("cfg,p,smax", [("c3", 16, 1024), ("c5", 24, 512)])
+def test_large_dictionary_mixed_equals_plain(cfg, p, smax):
+    """Above the row cache the BF16 band can overflow the candidate buffer; those
+    signals are selected again from FP32 correlations in the same iteration, so
+    the mixed path still picks exactly the plain path's atoms."""
+    P = synth.make_config(cfg, p=p)
+    Xp, _, rp = solve_gpu(P, precision=0, smax=smax)
+    Xm, _, rm = solve_gpu(P, precision=1, smax=smax)
+    assert_certified(rp)
+    assert_certified(rm)
+    np.testing.assert_array_equal(rp.stats["outer_iters"], rm.stats["outer_iters"])
+    np.testing.assert_array_equal(Xp, Xm)
