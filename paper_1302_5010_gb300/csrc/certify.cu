@@ -30,15 +30,18 @@ namespace mpl {
 
 #ifdef MPL_FIN_TRACE
 // Per-signal phase cycle counters of the exact finish (diagnostic builds only):
-// [factor, solve, crossing, gram-zero-check, verify, exact-zero-check, steps, refinements]
-__device__ long long g_fin_trace[8192][8];
+// [factor, solve, crossing, gram-zero-check, verify, exact-zero-check, steps, refinements,
+//  of the factor: support + right-hand side, Gram gather]
+__device__ long long g_fin_trace[8192][10];
 #define FT_BEGIN long long ft0_ = clock64();
+#define FT_SPLIT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; } while (0)
 #define FT_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
 #define FT_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
 #else
 #define FT_BEGIN
 #define FT_ADD(slot) do {} while (0)
 #define FT_CNT(slot) do {} while (0)
+#define FT_SPLIT(slot) do {} while (0)
 #endif
 
 namespace {
@@ -532,7 +535,7 @@ __device__ int exact_factor(FinShared& sh, const float* A, int n, int np) {
 }
 
 // Copy the lower triangle of G_PP into the current factor storage and factor it.
-__device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
+__device__ void gather_gram(FinShared& sh, const float* Gi, int smax, int np) {
     // the np x np lower triangle as one flat range of independent loads (row r holds
     // entries r(r+1)/2 .. r(r+1)/2 + r)
     const int tot = np * (np + 1) / 2;
@@ -561,6 +564,10 @@ __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
         }
     }
     __syncthreads();
+}
+
+__device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
+    gather_gram(sh, Gi, smax, np);
     return factor(sh.F, np, &sh.ival[0]);
 }
 
@@ -640,7 +647,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             for (int a = tid; a < np; a += nt) sh.z[a] = (double)hi[sh.P[a]] - lam * (double)sh.sg[sh.P[a]];
             FT_CNT(6);
             flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
-            const int fres = load_factor(sh, Gi, smax, np);
+            FT_SPLIT(8);
+            gather_gram(sh, Gi, smax, np);
+            FT_SPLIT(9);
+            const int fres = factor(sh.F, np, &sh.ival[0]);
             FT_ADD(0);
             if (fres != 0) {
                 if (sh.F.fp64) break;
@@ -975,9 +985,9 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
 extern "C" int mpl_debug_fin_trace(long long* out, int count, int reset) {
     if (count > 8192) count = 8192;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 8 * (size_t)count) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 10 * (size_t)count) != cudaSuccess) return -1;
     if (reset) {
-        static long long zero[8192][8];
+        static long long zero[8192][10];
         if (cudaMemcpyToSymbol(mpl::g_fin_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
     }
     return count;

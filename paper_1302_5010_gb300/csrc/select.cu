@@ -131,9 +131,13 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
 
 // Copy the score row and the membership bitmap into shared memory (loads
 // batched eight deep so that they are in flight together).
-__device__ void fill_cache(const float* row, const uint32_t* msk, int m, SelSmem& sh) {
+__device__ void fill_cache(const float* row, const uint32_t* msk_g, int m, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned* keys = reinterpret_cast<unsigned*>(sh.row);
+    // the membership bitmap (m / 32 <= 256 words) staged in the histogram, free until the radix passes
+    uint32_t* msk = sh.hist;
+    for (int w = tid; w < (m + 31) / 32; w += nt) msk[w] = msk_g[w];
+    __syncthreads();
     int nf = 0;
     for (int j0 = tid; j0 < m; j0 += 8 * nt) {
         float v[8];
