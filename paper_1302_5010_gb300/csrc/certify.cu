@@ -109,75 +109,74 @@ __device__ __forceinline__ double bsum(double v, double* red) {
 }
 
 
-// Supports up to this size are factored right-looking (chol_block_rl) and solved by one warp.
-constexpr int WARP_FACTOR_MAX = 64;
 
-// Left-looking (dot-product form) Cholesky, in place on the lower triangle of
-// M, one row per thread across the CTA: column j is
-// L_rj = (G_rj - sum_{q<j} L_rq L_jq) / L_jj; rdiag receives 1/L_jj.
+// Blocked right-looking Cholesky by the whole CTA, panels of four columns: one
+// thread factors the 4 x 4 diagonal block, the threads take the panel's rows
+// below it, then the trailing lower triangle gets the rank-4 update with its
+// elements spread evenly over the CTA.  Three CTA barriers per four columns.
+// Returns 0 or -1 (non-positive pivot); flag likewise.
 template <typename T>
-__device__ int chol_block(T* M, int ld, int np, T* rdiag, int* flag) {
+__device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* flag) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int j = 0; j < np; ++j) {
-        const T* Lj = M + (size_t)j * ld;
-        for (int r = j + tid; r < np; r += nt) {
-            const T* Lr = M + (size_t)r * ld;
-            T a0 = Lr[j], a1 = T(0);
-            int q = 0;
-            for (; q + 1 < j; q += 2) {
-                a0 -= Lr[q] * Lj[q];
-                a1 -= Lr[q + 1] * Lj[q + 1];
-            }
-            if (q < j) a0 -= Lr[q] * Lj[q];
-            M[(size_t)r * ld + j] = a0 + a1;
-        }
-        __syncthreads();
-        const T sj = M[(size_t)j * ld + j];
-        if (!(sj > T(0))) {
-            if (tid == 0) *flag = 1;
-            return -1;
-        }
-        const T dg = sqrt(sj), inv = T(1) / dg;
-        __syncthreads();
-        for (int r = j + tid; r < np; r += nt) M[(size_t)r * ld + j] = (r == j) ? dg : M[(size_t)r * ld + j] * inv;
-        if (tid == 0) rdiag[j] = inv;
-        __syncthreads();
-    }
-    if (tid == 0) *flag = 0;
-    return 0;
-}
-
-// Right-looking Cholesky by the whole CTA for np <= 64 (lower triangle of M in
-// shared memory): per column, one thread takes the pivot, the column is scaled,
-// and the trailing triangle gets the rank-1 update with four threads per row
-// (every fourth column each).  Two CTA barriers per column instead of a serial
-// chain of dot products.  Returns 0 or -1 (non-positive pivot); flag likewise.
-template <typename T>
-__device__ int chol_block_rl(T* M, int ld, int np, T* rdiag, int* flag) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int rq = tid & 63, cq = tid >> 6, cstep = nt >> 6;  // 64 row slots x (nt / 64) column phases
-    for (int j = 0; j < np; ++j) {
+    for (int j = 0; j < np; j += 4) {
+        const int w = min(4, np - j);
         if (tid == 0) {
-            const T sj = M[(size_t)j * ld + j];
-            *flag = (sj > T(0)) ? 0 : 1;
-            if (sj > T(0)) {
-                const T dg = sqrt(sj);
-                M[(size_t)j * ld + j] = dg;
-                rdiag[j] = T(1) / dg;
+            int bad = 0;
+            for (int k = 0; k < w && !bad; ++k) {
+                T* Rk = M + (size_t)(j + k) * ld + j;
+                T dkk = Rk[k];
+                for (int q = 0; q < k; ++q) dkk -= Rk[q] * Rk[q];
+                if (!(dkk > T(0))) { bad = 1; break; }
+                const T dg = sqrt(dkk), inv = T(1) / dg;
+                Rk[k] = dg;
+                rdiag[j + k] = inv;
+                for (int r = k + 1; r < w; ++r) {
+                    T* Rr = M + (size_t)(j + r) * ld + j;
+                    T v = Rr[k];
+                    for (int q = 0; q < k; ++q) v -= Rr[q] * Rk[q];
+                    Rr[k] = v * inv;
+                }
             }
+            *flag = bad;
         }
         __syncthreads();
         if (*flag) return -1;
-        const T inv = rdiag[j];
-        for (int r = j + 1 + tid; r < np; r += nt) M[(size_t)r * ld + j] *= inv;
-        __syncthreads();
-        const int r = j + 1 + rq;
-        if (r < np) {
-            const T lr = M[(size_t)r * ld + j];
-            for (int c = j + 1 + cq; c <= r; c += cstep) M[(size_t)r * ld + c] -= lr * M[(size_t)c * ld + j];
+        // panel rows below the diagonal block
+        for (int r = j + w + tid; r < np; r += nt) {
+            T* Rr = M + (size_t)r * ld + j;
+            T l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < w) {
+                    const T* Rk = M + (size_t)(j + k) * ld + j;
+                    T v = Rr[k];
+#pragma unroll
+                    for (int q = 0; q < k; ++q) v -= l[q] * Rk[q];
+                    l[k] = v * rdiag[j + k];
+                    Rr[k] = l[k];
+                }
+            }
         }
+        __syncthreads();
+        // trailing triangle: rows r >= c >= j + w, element e <-> (r', c') in row-major order
+        const int b0 = j + w, nr = np - b0;
+        const int tot = nr * (nr + 1) / 2;
+        for (int e = tid; e < tot; e += nt) {
+            int rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+            while (rr * (rr + 1) / 2 > e) --rr;
+            const int r = b0 + rr, c = b0 + (e - rr * (rr + 1) / 2);
+            const T* Lr = M + (size_t)r * ld + j;
+            const T* Lc = M + (size_t)c * ld + j;
+            T acc = M[(size_t)r * ld + c];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < w) acc -= Lr[k] * Lc[k];
+            M[(size_t)r * ld + c] = acc;
+        }
+        __syncthreads();
     }
-    __syncthreads();
+    if (tid == 0) *flag = 0;
     return 0;
 }
 
@@ -257,12 +256,8 @@ struct Factor {
 };
 
 __device__ int factor(Factor& F, int np, int* flag) {
-    if (!F.fp64) {
-        if (np > WARP_FACTOR_MAX) return chol_block(F.Mf, F.ldf, np, F.rdf, flag);
-        return chol_block_rl(F.Mf, F.ldf, np, F.rdf, flag);
-    }
-    if (np > WARP_FACTOR_MAX) return chol_block(F.Md, F.ldd, np, F.rdd, flag);
-    return chol_block_rl(F.Md, F.ldd, np, F.rdd, flag);
+    if (!F.fp64) return chol_panel4(F.Mf, F.ldf, np, F.rdf, flag);
+    return chol_panel4(F.Md, F.ldd, np, F.rdd, flag);
 }
 
 // v <- G_PP^{-1} v with the current factor (FP32 factor: solved in FP32).

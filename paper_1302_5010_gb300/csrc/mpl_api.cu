@@ -60,6 +60,9 @@ struct mpl_ctx {
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;  // phase timing nodes
     };
     std::vector<GraphEntry> graphs;  // captured outer iterations, valid for the current workspace
+    mpl_signal_stats_t* stats_d = nullptr;    // packed per-signal statistics (device, cap_p)
+    mpl_signal_stats_t* stats_pin = nullptr;  // and their pinned host copy
+    int stats_pin_cap = 0;
     float* Bint = nullptr;           // fixed internal copies of B and lambda (graph parameters)
     float* lamint = nullptr;
     // proposal network (learned warm start)
@@ -208,6 +211,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.ovf_list, (size_t)P));
     CK(cudaMemset(d.ovf_cnt, 0, sizeof(Counters)));
     CK(alloc(h, &h->Bint, pn));
+    CK(alloc(h, &h->stats_d, (size_t)P));
     CK(alloc(h, &h->lamint, (size_t)P));
     CK(cudaMemset(d.xS, 0, ps * sizeof(float)));
     CK(cudaMemset(d.G, 0, pss * sizeof(float)));
@@ -370,6 +374,7 @@ mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
 void mpl_destroy(mpl_handle_t h) {
     if (!h) return;
     free_ws(h);
+    if (h->stats_pin) cudaFreeHost(h->stats_pin);
     cudaFree(h->Q);
     cudaFree(h->beta);
     cudaFree(h->A32);
@@ -773,17 +778,17 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     pt.end(0, t_all);
     if (X_host) CK(cudaMemcpyAsync(X, Xd, (size_t)m * p * sizeof(float), cudaMemcpyDeviceToHost, st));
 
-    // per-signal statistics
-    std::vector<int> iv(10 * (size_t)p);
-    std::vector<double> dvv(6 * (size_t)p);
-    const int* isrc[] = {d.outer, d.inner, d.ssize, d.nnz, d.sstatus, d.finishes};
-    for (int k = 0; k < 6; ++k)
-        CK(cudaMemcpyAsync(iv.data() + (size_t)k * p, isrc[k], (size_t)p * sizeof(int), cudaMemcpyDeviceToHost, st));
-    const double* dsrc[] = {d.obj, d.kkt_in, d.kkt_out, d.ginf, d.rr, d.rb};
-    for (int k = 0; k < 6; ++k)
-        CK(cudaMemcpyAsync(dvv.data() + (size_t)k * p, dsrc[k], (size_t)p * sizeof(double), cudaMemcpyDeviceToHost, st));
-    std::vector<float> lamh((size_t)p);
-    CK(cudaMemcpyAsync(lamh.data(), lamd, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
+    // per-signal statistics: packed on the device, one copy into pinned memory
+    if (h->stats_pin_cap < p) {
+        if (h->stats_pin) cudaFreeHost(h->stats_pin);
+        h->stats_pin = nullptr;
+        h->stats_pin_cap = 0;
+        CK(cudaMallocHost(&h->stats_pin, (size_t)p * sizeof(mpl_signal_stats_t)));
+        h->stats_pin_cap = p;
+    }
+    CK(launch_pack_stats(d, h->stats_d, st, &nl));
+    CK(cudaMemcpyAsync(h->stats_pin, h->stats_d, (size_t)p * sizeof(mpl_signal_stats_t), cudaMemcpyDeviceToHost, st));
+    (void)lamd;
     CK(cudaEventRecord(h->ev_out, st));
     CK(cudaStreamWaitEvent(caller, h->ev_out, 0));
     CK(cudaStreamSynchronize(st));
@@ -795,23 +800,10 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     h->phase_ms[9] = (double)h->cnt_h->qcols;      // of those columns, scored by the identity route
     h->launches = nl;
     bool all_ok = true;
+    std::memcpy(h->stats.data(), h->stats_pin, (size_t)p * sizeof(mpl_signal_stats_t));
     for (int i = 0; i < p; ++i) {
-        mpl_signal_stats_t& s = h->stats[(size_t)i];
-        s.outer_iters = iv[(size_t)0 * p + i];
-        s.inner_iters = iv[(size_t)1 * p + i];
-        s.active_size = iv[(size_t)2 * p + i];
-        s.nnz = iv[(size_t)3 * p + i];
-        s.status = iv[(size_t)4 * p + i];
-        s.finishes = iv[(size_t)5 * p + i];
-        const double obj = dvv[(size_t)0 * p + i];
-        s.objective = obj;
-        s.kkt = std::max(dvv[(size_t)1 * p + i], dvv[(size_t)2 * p + i]);
-        const double ginf = dvv[(size_t)3 * p + i], rr = dvv[(size_t)4 * p + i], rb = dvv[(size_t)5 * p + i];
-        const double lam = (double)lamh[(size_t)i];
-        const double sc = (ginf > lam && ginf > 0) ? lam / ginf : 1.0;
-        const double D = -0.5 * sc * sc * rr + sc * rb;
-        s.gap = obj > 0 ? (obj - D) / obj : 0.0;
-        if (s.status != MPL_SIG_CERTIFIED && s.status != MPL_SIG_EARLY_STOP) all_ok = false;
+        const int status = h->stats[(size_t)i].status;
+        if (status != MPL_SIG_CERTIFIED && status != MPL_SIG_EARLY_STOP) all_ok = false;
     }
     return all_ok ? MPL_OK : MPL_ERR_NOT_CONVERGED;
 }

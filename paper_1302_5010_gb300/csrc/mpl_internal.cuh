@@ -151,6 +151,7 @@ cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl)
 cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl);
 cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, int64_t* nl);
 cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl);
+cudaError_t launch_pack_stats(const Dev& d, mpl_signal_stats_t* out, cudaStream_t s, int64_t* nl);
 cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
                            cudaStream_t s, int64_t* nl);
 cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl);

@@ -856,6 +856,35 @@ cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     return cudaGetLastError();
 }
 
+// Per-signal statistics packed on the device into the host struct layout (one copy back).
+__global__ void k_pack_stats(Dev d, mpl_signal_stats_t* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.p) return;
+    mpl_signal_stats_t s;
+    s.outer_iters = d.outer[i];
+    s.inner_iters = d.inner[i];
+    s.active_size = d.ssize[i];
+    s.nnz = d.nnz[i];
+    s.status = d.sstatus[i];
+    s.finishes = d.finishes[i];
+    const double obj = d.obj[i];
+    s.objective = obj;
+    s.kkt = fmax(d.kkt_in[i], d.kkt_out[i]);
+    // relative duality gap with the dual point xi * min(1, lambda / ||A^T xi||_inf) of eq. 5
+    const double ginf = d.ginf[i], rr = d.rr[i], rb = d.rb[i], lam = (double)d.lam[i];
+    const double sc = (ginf > lam && ginf > 0.0) ? lam / ginf : 1.0;
+    const double D = -0.5 * sc * sc * rr + sc * rb;
+    s.gap = obj > 0.0 ? (obj - D) / obj : 0.0;
+    out[i] = s;
+}
+
+cudaError_t launch_pack_stats(const Dev& d, mpl_signal_stats_t* out, cudaStream_t s, int64_t* nl) {
+    if (d.p <= 0) return cudaSuccess;
+    k_pack_stats<<<(d.p + 127) / 128, 128, 0, s>>>(d, out);
+    ++*nl;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     k_smpl_prune<<<ub, 256, 0, s>>>(d);
