@@ -175,7 +175,7 @@ cudaError_t prepare_corr_bf16();
 enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SHAPE = 3 };
 
 // Candidate capacity of the selection kernel (per signal, in shared memory).
-constexpr int SEL_KCAP = 4096;
+constexpr int SEL_KCAP = 2048;
 constexpr int SEL_THREADS = 512;
 constexpr int SEL_ROWCACHE_ATOMS = 8192;  // score rows up to this length are cached in shared memory
 // Master problem: Gram block kept in shared memory up to this size.

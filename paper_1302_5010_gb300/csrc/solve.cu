@@ -798,6 +798,9 @@ cudaError_t prepare_gram() {
     if (attr) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_gram_async<64, 32, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gram_smem<64, 32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_async<64, 64, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gram_smem<64, 64>());
     if (e == cudaSuccess) attr = true;
     return e;
 }
@@ -810,6 +813,9 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
         if (qmax + 1 <= 16) {  // the new atoms and b fit one 16-column tile
             dim3 grid(ub, (d.smax + 31) / 32);
             k_gram_async<32, 16, 1, 2><<<grid, 256, gram_smem<32, 16>(), s>>>(d);
+        } else if (qmax + 1 <= 64) {  // one 64-column pass (e.g. a warm start's first iteration)
+            dim3 grid(ub, (d.smax + 63) / 64);
+            k_gram_async<64, 64, 4, 4><<<grid, 256, gram_smem<64, 64>(), s>>>(d);
         } else {
             dim3 grid(ub, (d.smax + 63) / 64);
             k_gram_async<64, 32, 2, 4><<<grid, 256, gram_smem<64, 32>(), s>>>(d);
