@@ -21,8 +21,8 @@
  *   3. master problem (eq. "primal_MPL"): the LASSO restricted to I, warm
  *      started from x_I (Alg. 1, step 4), solved by accelerated proximal
  *      gradient (Nesterov/FISTA, the paper's PG rule for lambda > 0) with a
- *      backtracking line search for the step 1/L (the "proper line search" of
- *      Lemma 1) and a function-value momentum restart that keeps f monotone,
+ *      backtracking line search for the step 1/L (the line search Lemma 1
+ *      takes for granted) and a function-value momentum restart that keeps f monotone,
  *      stopped by the relative-decrease rule (eq. "inner") with eps_in.
  *      The gradient A_I^T (A_I u - b) is evaluated as G u - h with
  *      G = A_I^T A_I and h = A_I^T b, which is the same quantity.
