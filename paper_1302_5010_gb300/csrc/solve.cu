@@ -15,6 +15,19 @@
 
 namespace mpl {
 
+#ifdef MPL_APG_TRACE
+// Per-signal phase cycle counters of the master problem (diagnostic builds only):
+// [Gram block + vectors, power iteration, FISTA, write-back, master problems, FISTA iterations]
+__device__ long long g_apg_trace[8192][8];
+#define AT_BEGIN long long at0_ = clock64();
+#define AT_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_apg_trace[i][slot] += clock64() - at0_; at0_ = clock64(); } while (0)
+#define AT_CNT(slot, v) do { if (threadIdx.x == 0 && i < 8192) g_apg_trace[i][slot] += (v); } while (0)
+#else
+#define AT_BEGIN
+#define AT_ADD(slot) do {} while (0)
+#define AT_CNT(slot, v) do {} while (0)
+#endif
+
 namespace {
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
@@ -332,9 +345,11 @@ constexpr size_t gram_smem() { return (size_t)GS * (BM + BN) * GPAD * sizeof(flo
 // ... the TPR threads of a row sit 32 / TPR lanes apart and take every TPR-th
 // column; their partial sums meet in a fixed butterfly.  With the packed leading
 // dimension ld = 32 / TPR (mod 32) the TPR column phases fall in disjoint banks.
+// With h != nullptr the thread that writes y_r also returns its share of the
+// restricted objective, lambda |x_r| + x_r (y_r / 2 - h_r) (summed over its rows).
 template <int TPR>
-__device__ __forceinline__ void gram_mv_split(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
-                                              float* __restrict__ y) {
+__device__ __forceinline__ float gram_mv_split(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                               float* __restrict__ y, const float* h = nullptr, float lam = 0.f) {
     constexpr int RW = 32 / TPR;  // rows per warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = lane / RW, r = warp * RW + (lane % RW);
@@ -343,7 +358,12 @@ __device__ __forceinline__ void gram_mv_split(const float* __restrict__ G, int l
         for (int c = p; c < s; c += TPR) a = fmaf(G[(size_t)c * ld + r], x[c], a);
 #pragma unroll
     for (int o = RW; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (p == 0 && r < s) y[r] = a;
+    float part = 0.f;
+    if (p == 0 && r < s) {
+        y[r] = a;
+        if (h) part = lam * fabsf(x[r]) + x[r] * (0.5f * a - h[r]);
+    }
+    return part;
 }
 
 // Packed leading dimension of an s x s block for gram_mv_split (see above).
@@ -359,8 +379,9 @@ __host__ __device__ __forceinline__ size_t apg_area(int gcap) {
     return g * g > h * (h + 32) ? g * g : h * (h + 32);
 }
 
-__device__ __forceinline__ void gram_mv(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
-                                        float* __restrict__ y) {
+__device__ __forceinline__ float gram_mv(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                         float* __restrict__ y, const float* h = nullptr, float lam = 0.f) {
+    float part = 0.f;
     // y = G x, one row per thread; G symmetric so column r is read with unit
     // stride across threads (conflict-free in shared memory, coalesced in global)
     for (int r = threadIdx.x; r < s; r += blockDim.x) {
@@ -373,15 +394,34 @@ __device__ __forceinline__ void gram_mv(const float* __restrict__ G, int ld, int
             a3 = fmaf(G[(size_t)(c + 3) * ld + r], x[c + 3], a3);
         }
         for (; c < s; ++c) a0 = fmaf(G[(size_t)c * ld + r], x[c], a0);
-        y[r] = (a0 + a1) + (a2 + a3);
+        const float yr = (a0 + a1) + (a2 + a3);
+        y[r] = yr;
+        if (h) part += lam * fabsf(x[r]) + x[r] * (0.5f * yr - h[r]);
     }
+    return part;
 }
 
 struct ApgVec {
     float *u, *up, *Gu, *Gup, *h, *v;
-    float red[32];
+    float red[96];
     int item;
 };
+
+// Three block sums in one pass (two barriers); every thread gets the totals.
+__device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    __syncthreads();
+    if (lane == 0) { red[warp] = a; red[32 + warp] = b; red[64 + warp] = c; }
+    __syncthreads();
+    a = b = c = 0.f;
+    for (int w = 0; w < nw; ++w) { a += red[w]; b += red[32 + w]; c += red[64 + w]; }
+}
 
 __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) {
     extern __shared__ __align__(16) float gsm[];
@@ -399,6 +439,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         const int it = sh.item;
         if (it >= d.cnt->apg_n) break;
         const int i = d.list_apg[it];
+        AT_BEGIN
         const int s = d.ssize[i];
         const float lam = d.lam[i];
         const float eps = d.eps[i];
@@ -412,9 +453,25 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         const float* G = insm ? gsm : Gg;
         const int ld = insm ? apg_ld(s) : smax;
         if (insm) {
-            for (int e = tid; e < s * s; e += blockDim.x) {
-                const int r = e / s, c = e - r * s;
-                gsm[(size_t)r * ld + c] = Gg[(size_t)r * smax + c];
+            // eight loads in flight per thread before their stores
+            for (int e0 = tid; e0 < s * s; e0 += 8 * blockDim.x) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < s * s) {
+                        const int r = e / s, c = e - r * s;
+                        v[u] = __ldg(Gg + (size_t)r * smax + c);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < s * s) {
+                        const int r = e / s, c = e - r * s;
+                        gsm[(size_t)r * ld + c] = v[u];
+                    }
+                }
             }
         }
         // the block's matrix-vector product: split rows while the block is small
@@ -422,6 +479,12 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
             if (insm && s <= 64) gram_mv_split<4>(G, ld, s, x, y);
             else if (insm && s <= 128) gram_mv_split<2>(G, ld, s, x, y);
             else gram_mv(G, ld, s, x, y);
+        };
+        // y = G x and this thread's share of the restricted objective at x
+        auto mvF = [&](const float* x, float* y) -> float {
+            if (insm && s <= 64) return gram_mv_split<4>(G, ld, s, x, y, sh.h, lam);
+            if (insm && s <= 128) return gram_mv_split<2>(G, ld, s, x, y, sh.h, lam);
+            return gram_mv(G, ld, s, x, y, sh.h, lam);
         };
         float* xi = d.xS + (size_t)i * smax;
         float* ritz = d.ritz + (size_t)i * smax;
@@ -432,25 +495,39 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
             sh.v[r] = (r < prev && d.outer[i] > 1) ? ritz[r] : 1.f;
         }
         __syncthreads();
-        // Step size: power iteration for lambda_max(G) (warm started), L = 1.05 theta.
+        AT_ADD(0);
+        // Step size: power iteration for lambda_max(G) (warm started), L = 1.05 theta.  The
+        // iterate ping-pongs between two vectors and is normalised every fourth step (and
+        // at the last, where the Rayleigh quotient is taken): growth over four steps stays
+        // far inside FP32 range for |S| <= 1024.
         float theta = 1.f;
         const int npow = (prev > 0 && d.outer[i] > 1) ? 6 : 14;
+        float* pv = sh.v;
+        float* pw = sh.Gu;
         for (int pi = 0; pi < npow; ++pi) {
-            mv(sh.v, sh.Gu);
+            mv(pv, pw);
             __syncthreads();
-            float vv = 0.f, vg = 0.f;
-            for (int r = tid; r < s; r += blockDim.x) { vv += sh.v[r] * sh.v[r]; vg += sh.v[r] * sh.Gu[r]; }
-            const float tv = block_sum(vv, sh.red);
-            const float tg = block_sum(vg, sh.red);
-            float gg = 0.f;
-            for (int r = tid; r < s; r += blockDim.x) gg += sh.Gu[r] * sh.Gu[r];
-            const float tgg = block_sum(gg, sh.red);
-            theta = tv > 0.f ? tg / tv : 1.f;
-            const float inv = tgg > 0.f ? rsqrtf(tgg) : 0.f;
-            for (int r = tid; r < s; r += blockDim.x) sh.v[r] = sh.Gu[r] * inv;
-            __syncthreads();
+            if ((pi & 3) == 3 || pi == npow - 1) {
+                float vv = 0.f, vg = 0.f, gg = 0.f;
+                for (int r = tid; r < s; r += blockDim.x) {
+                    vv += pv[r] * pv[r];
+                    vg += pv[r] * pw[r];
+                    gg += pw[r] * pw[r];
+                }
+                block_sum3(vv, vg, gg, sh.red);
+                theta = vv > 0.f ? vg / vv : 1.f;
+                const float inv = gg > 0.f ? rsqrtf(gg) : 0.f;
+                for (int r = tid; r < s; r += blockDim.x) pv[r] = pw[r] * inv;
+                __syncthreads();
+            } else {
+                float* t = pv;
+                pv = pw;
+                pw = t;
+            }
         }
-        for (int r = tid; r < s; r += blockDim.x) ritz[r] = sh.v[r];
+        for (int r = tid; r < s; r += blockDim.x) ritz[r] = pv[r];
+        __syncthreads();  // pv may be the Gu buffer, which the next product overwrites
+        AT_ADD(1);
         float L = fmaxf(1.05f * theta, 1e-30f);
 
         // F(u) and G u at the warm start
@@ -478,11 +555,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
                 sh.u[r] = z;
             }
             __syncthreads();
-            mv(sh.u, sh.Gu);
-            __syncthreads();
-            part = 0.f;
-            for (int r = tid; r < s; r += blockDim.x)
-                part += lam * fabsf(sh.u[r]) + sh.u[r] * (0.5f * sh.Gu[r] - sh.h[r]);
+            part = mvF(sh.u, sh.Gu);  // the block sum's barriers also publish Gu
             const float Fn = block_sum(part, sh.red);
             ++iters;
             if (Fn > F) {
@@ -506,7 +579,11 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
             beta = (t - 1.f) / tn;
             t = tn;
         }
+        AT_ADD(2);
         for (int r = tid; r < s; r += blockDim.x) xi[r] = sh.u[r];
+        AT_ADD(3);
+        AT_CNT(4, 1);
+        AT_CNT(5, iters);
         if (tid == 0) {
             d.inner[i] += iters;
             // early stopping, eq. (stop_con): decrease of f over this outer iteration's
@@ -827,6 +904,19 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
     ++*nl;
     return cudaGetLastError();
 }
+
+#ifdef MPL_APG_TRACE
+extern "C" int mpl_debug_apg_trace(long long* out, int count, int reset) {
+    if (count > 8192) count = 8192;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, g_apg_trace, sizeof(long long) * 8 * (size_t)count) != cudaSuccess) return -1;
+    if (reset) {
+        static long long zero[8192][8];
+        if (cudaMemcpyToSymbol(g_apg_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
+    }
+    return count;
+}
+#endif
 
 cudaError_t prepare_apg() {
     static bool attr = false;
