@@ -897,6 +897,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             r64[k] = v;
             if (rsm) { d.R32[(size_t)i * n + k] = rh[k]; d.R32lo[(size_t)i * n + k] = rl[k]; }
             if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(rh[k]);
+            if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = __float2bfloat16_rn(rh[k]);
             rr += v * v;
             rb += v * (double)b[k];
             rs += (double)rh[k] * (double)rh[k];

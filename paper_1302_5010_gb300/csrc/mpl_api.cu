@@ -185,6 +185,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     if (need_r16) {
         CK(alloc(h, &d.R16, pn + 64));
         CK(alloc(h, &d.R16c, pn + 64 * (size_t)n));
+        CK(alloc(h, &d.pos, (size_t)P));
     }
     CK(alloc(h, &d.Cs, (size_t)P * m));
     CK(alloc(h, &d.mask, (size_t)P * mw));
@@ -549,7 +550,9 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     if (route == ROUTE_Q) {
         if ((e = launch_corr_q(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     } else if (h->precision == 1 && route == ROUTE_GEMM) {
-        if ((e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        // the residual writers keep the compacted BF16 rows current (d.pos); only a path
+        // without them needs the gather
+        if (!d.pos && (e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
         if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
     } else {
         if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
@@ -557,6 +560,8 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     if (t == 0 && h->qroute > 0 && (e = launch_save_beta(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(ph_corr, e0, run);
     e0 = pt ? pt->begin_if(2, run) : nullptr;
+    // without a second selection pass the selection's last CTA builds the work lists
+    const int fuse = d.ovf_list == nullptr ? 1 : 0;
     if (t == 0 && h->warm == 2) {
         // learned warm start: the first worst-case analysis also admits the atoms the
         // proposal network accepts among the W largest correlations
@@ -567,8 +572,8 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
         pa.thr = (float)h->warm_thr;
         pa.w = h->pwb;
         pa.rn = h->rn;
-        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa, route)) != cudaSuccess) return e;
-    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, nullptr, route)) != cudaSuccess) {
+        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa, route, fuse)) != cudaSuccess) return e;
+    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, nullptr, route, fuse)) != cudaSuccess) {
         return e;
     }
     if (d.ovf_list) {
@@ -592,7 +597,7 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
             return e;
         }
     }
-    if ((e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
+    if (!fuse && (e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(2, e0, run);
     // the exact finish touches only signals without violators: overlap it
     // with the Gram growth / master problem / residual of the others

@@ -28,6 +28,7 @@ struct Counters {
     unsigned long long cols;  // signal columns processed by the correlation (all iterations)
     unsigned long long fin_flops;  // algorithmic FLOPs of the exact finish (factor, solves, residual sums)
     unsigned long long qcols;  // signal columns scored by the identity route beta - Q_S x_S
+    int sel_done;    // selection CTAs finished (the last one compacts the lists)
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 
@@ -58,6 +59,7 @@ struct Dev {
     double* R64;                 // p x n residual of the exact finish (FP64)
     __nv_bfloat16* R16;          // p x n residual (BF16, mixed)
     __nv_bfloat16* R16c;         // act_n x n compacted BF16 residual for the GEMM
+    int* pos;                    // p row of each signal in R16c (its place in the next active list)
     float* Cs;                   // act_n x m correlation scores (row k <-> act[k])
     uint32_t* mask;              // p x mw membership bitmap of S_i
     int* S;                      // p x smax active-set atom indices (append order)
@@ -132,8 +134,9 @@ cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_
 cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
 // Correlation routes of one outer iteration (selects the selection kernel's error band).
 enum CorrRoute : int { ROUTE_GEMM = 0, ROUTE_GEMM_F32 = 1, ROUTE_Q = 2 };
+// fuse_compact: the selection's last CTA also builds the work lists (k_compact not needed).
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa = nullptr, int route = ROUTE_GEMM);
+                          const PropArgs* pa = nullptr, int route = ROUTE_GEMM, int fuse_compact = 0);
 // Identity route (eq. batchQ): scores beta_i - Q_S x_S into the compacted score rows.
 cudaError_t launch_corr_q(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
 // beta_i = score row of signal i (after an FP32 correlation of the residual b_i).

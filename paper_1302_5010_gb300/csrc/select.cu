@@ -363,7 +363,7 @@ __device__ __forceinline__ unsigned ordered_bits(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa, int route) {
+__device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, const PropArgs& pa, int route) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -650,19 +650,22 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
 
 // Stable compaction of the active list into the work lists of this outer
 // iteration (one CTA): grow, finish, master problem, and the next active list.
-__global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
+// The states were written by other CTAs of the same launch when the compaction
+// runs at the end of the selection, so they are read past L1.
+__device__ void compact_body(const Dev& d, int cur) {
     const int nact = d.cnt->act_n[cur];
     const int* act = d.act[cur];
     int* nxt = d.act[cur ^ 1];
     __shared__ int wsum[3][32];
     __shared__ int base[3];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nw = nt >> 5;
     if (tid < 3) base[tid] = 0;
+    if (tid < 96) wsum[tid / 32][tid % 32] = 0;
     __syncthreads();
-    for (int c0 = 0; c0 < nact; c0 += 1024) {
+    for (int c0 = 0; c0 < nact; c0 += nt) {
         const int k = c0 + tid;
         int sig = -1, st = ST_DONE;
-        if (k < nact) { sig = act[k]; st = d.state[sig]; }
+        if (k < nact) { sig = __ldcg(act + k); st = __ldcg(d.state + sig); }
         const int f[3] = {st == ST_GROW || st == ST_REFINE, st == ST_FINALIZE, st != ST_DONE};
         if (st == ST_REFINE) d.state[sig] = ST_GROW;  // master problem again, no new atoms
         int pre[3];
@@ -677,7 +680,7 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
         if (warp == 0) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                int v = wsum[q][lane];
+                int v = lane < nw ? wsum[q][lane] : 0;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int u = __shfl_up_sync(0xffffffffu, v, o);
                     if (lane >= o) v += u;
@@ -692,7 +695,10 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
             if (f[q]) {
                 if (q == 0) { d.list_grow[off] = sig; d.list_apg[off] = sig; }
                 else if (q == 1) d.list_fin[off] = sig;
-                else nxt[off] = sig;
+                else {
+                    nxt[off] = sig;
+                    if (d.pos) d.pos[sig] = off;  // its GEMM row next iteration
+                }
             }
         }
         __syncthreads();
@@ -708,6 +714,27 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
         d.cnt->act_n[cur ^ 1] = base[2];
         d.cnt->apg_head = 0;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) { compact_body(d, cur); }
+
+// The selection of one outer iteration; with fuse set, the last CTA to finish
+// (counted with a fenced atomic) also runs the compaction, saving a launch.
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa, int route,
+                                                           int fuse) {
+    select_body(d, cur, no_grow, pa, route);
+    if (!fuse) return;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&d.cnt->sel_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    compact_body(d, cur);
+    if (threadIdx.x == 0) d.cnt->sel_done = 0;
 }
 
 }  // namespace
@@ -735,14 +762,14 @@ cudaError_t prepare_select() {
 }
 
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa, int route) {
+                          const PropArgs* pa, int route, int fuse_compact) {
     if (act_n_ub <= 0) return cudaSuccess;
     PropArgs a{};
     if (pa) a = *pa;
     const size_t sm = sizeof(SelSmem) + (a.mode != SEL_NORMAL ? PROP_NPARAM * sizeof(float) : 0);
     cudaError_t e = prepare_select();
     if (e != cudaSuccess) return e;
-    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a, route);
+    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a, route, fuse_compact);
     ++*nl;
     return cudaGetLastError();
 }

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.R32lo[(size_t)i * n + k] = 0.f;
         r64[k] = (double)v;
         if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(v);
+        if (d.pos) d.R16c[(size_t)i * n + k] = __float2bfloat16_rn(v);  // active list = identity
         ss += (double)v * (double)v;
     }
     uint32_t* mw = d.mask + (size_t)i * d.mw;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.fails[i] = 0;
         d.nnz[i] = 0;
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
+        if (d.pos) d.pos[i] = i;
         if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
         if (d.explore) d.explore[i] = 0;
         if (i == 0 && d.ovf_cnt) { d.ovf_cnt->act_n[0] = 0; d.ovf_cnt->act_n[1] = 0; }
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->cols = 0ull;
             d.cnt->fin_flops = 0ull;
             d.cnt->qcols = 0ull;
+            d.cnt->sel_done = 0;
         }
     }
 }
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         // at the last, where the Rayleigh quotient is taken): growth over four steps stays
         // far inside FP32 range for |S| <= 1024.
         float theta = 1.f;
-        const int npow = (prev > 0 && d.outer[i] > 1) ? 6 : 14;
+        const int npow = !(lam > 0.f) ? 0 : ((prev > 0 && d.outer[i] > 1) ? 3 : 8);  // CG needs no step size
         float* pv = sh.v;
         float* pw = sh.Gu;
         for (int pi = 0; pi < npow; ++pi) {
@@ -543,7 +546,50 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         const float F0 = F;
         float t = 1.f, beta = 0.f;
         int iters = 0, restarts_in_row = 0;
-        for (int k = 0; k < d.inner_max; ++k) {
+        if (!(lam > 0.f)) {
+            // lambda = 0: the restricted problem is least squares G u = h, solved by
+            // conjugate gradients (the paper's CGD rule for lambda = 0) from the warm start;
+            // r in up, the direction in Gup, G times the direction in v
+            float rr = 0.f, hh = 0.f;
+            for (int r = tid; r < s; r += blockDim.x) {
+                const float res = sh.h[r] - sh.Gu[r];
+                sh.up[r] = res;
+                sh.Gup[r] = res;
+                rr += res * res;
+                hh += sh.h[r] * sh.h[r];
+            }
+            float z0 = 0.f;
+            block_sum3(rr, hh, z0, sh.red);
+            const float stop2 = eps * eps * hh;
+            const int cg_max = min(d.inner_max, 4 * s + 20);
+            for (int k = 0; k < cg_max && rr > stop2; ++k) {
+                mv(sh.Gup, sh.v);
+                __syncthreads();
+                float pgp = 0.f;
+                for (int r = tid; r < s; r += blockDim.x) pgp += sh.Gup[r] * sh.v[r];
+                pgp = block_sum(pgp, sh.red);
+                if (!(pgp > 0.f)) break;
+                const float alpha = rr / pgp;
+                float rn = 0.f;
+                for (int r = tid; r < s; r += blockDim.x) {
+                    sh.u[r] += alpha * sh.Gup[r];
+                    sh.Gu[r] += alpha * sh.v[r];
+                    const float res = sh.up[r] - alpha * sh.v[r];
+                    sh.up[r] = res;
+                    rn += res * res;
+                }
+                rn = block_sum(rn, sh.red);
+                const float bcg = rn / rr;
+                rr = rn;
+                for (int r = tid; r < s; r += blockDim.x) sh.Gup[r] = sh.up[r] + bcg * sh.Gup[r];
+                __syncthreads();
+                ++iters;
+            }
+            part = 0.f;
+            for (int r = tid; r < s; r += blockDim.x) part += sh.u[r] * (0.5f * sh.Gu[r] - sh.h[r]);
+            F = block_sum(part, sh.red);
+        }
+        for (int k = 0; lam > 0.f && k < d.inner_max; ++k) {
             // extrapolate, prox-gradient step (the one matvec is G u of the new point)
             const float invL = 1.f / L, thr = lam * invL;
             for (int r = tid; r < s; r += blockDim.x) {
@@ -667,6 +713,11 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
                 o[0] = __float2bfloat16_rn(acc.x); o[1] = __float2bfloat16_rn(acc.y);
                 o[2] = __float2bfloat16_rn(acc.z); o[3] = __float2bfloat16_rn(acc.w);
             }
+            if (d.pos) {  // straight into the GEMM's compacted rows for the next iteration
+                __nv_bfloat16* o = d.R16c + (size_t)d.pos[i] * n + k;
+                o[0] = __float2bfloat16_rn(acc.x); o[1] = __float2bfloat16_rn(acc.y);
+                o[2] = __float2bfloat16_rn(acc.z); o[3] = __float2bfloat16_rn(acc.w);
+            }
             ss = fmaf(acc.x, acc.x, ss); ss = fmaf(acc.y, acc.y, ss);
             ss = fmaf(acc.z, acc.z, ss); ss = fmaf(acc.w, acc.w, ss);
         }
@@ -676,6 +727,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
             for (int a = 0; a < nz; ++a) acc = fmaf(-nzv[a], __ldg(d.A32 + (size_t)nzi[a] * n + k), acc);
             r32[k] = acc;
             if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(acc);
+            if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = __float2bfloat16_rn(acc);
             ss = fmaf(acc, acc, ss);
         }
     }
