@@ -58,7 +58,7 @@ typedef enum {
     MPL_OPT_EPS_IN = 4,     /* relative-decrease tolerance of eq. (inner) for the FP32
                                master problem.  default 1e-4 */
     MPL_OPT_INNER_MAX = 5,  /* s_max, PG iterations per master problem.  default 400 */
-    MPL_OPT_WARM_START = 6, /* 0: x^0 = 0 (Alg. 1, step 1);
+    MPL_OPT_WARM_START = 6, /* 0: x^0 = 0 (Alg. 1);
                                2: proposal network seeds the active sets.  default 0 */
     MPL_OPT_SYNC_EVERY = 7, /* outer iterations launched per host/device handshake. default 2 */
     MPL_OPT_PROFILE = 8,    /* 1: record per-phase device times (mpl_get_phase_times) with
@@ -157,7 +157,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                         double tol, void* stream);
 
 /*
- * mpl_correlate -- the worst-case analysis product of Algorithm 1, step 3,
+ * mpl_correlate -- the worst-case analysis product of Algorithm 1,
  * g_i = A^T r_i for p given vectors (a full matrix-vector product, FMVP,
  * Sec. 2.4), computed by the handle's current correlation path
  * (MPL_OPT_PRECISION).
@@ -203,8 +203,8 @@ mpl_status_t mpl_correlate_noalloc(const float* A, int n, int m, const float* R,
  * W candidates of each signal from the first correlation c = A^T b:
  *   features (|c_j|/lambda, log(||b||/lambda), ||A^T a_j|| / sqrt(1 + m/n)),
  *   standardised, then 64 ReLU -> 64 ReLU -> 1 logit; BF16 weights, FP32 arithmetic.
- * The first outer iteration then adds MPL's own rho largest violators (Alg. 1,
- * step 3) plus every candidate whose logit exceeds MPL_OPT_WARM_THRESHOLD; the
+ * The first outer iteration then adds MPL's own rho largest violators (the
+ * worst-case analysis of Alg. 1) plus every candidate whose logit exceeds MPL_OPT_WARM_THRESHOLD; the
  * loop continues unchanged to the KKT tolerance, so solutions do not depend on
  * the proposal (atoms are never deleted, Sec. 2.2).
  * Parameter vector (MPL_PROPOSAL_NPARAM floats): mean[3], std[3], W1[64][3],

@@ -12,14 +12,14 @@
  *     x* = argmin_x  lambda*||x||_1 + 0.5*||b - A x||^2          (eq. 2)
  *
  * by running Algorithm 1 literally, in double precision:
- *   1. x = 0, residual xi = b, active set I = {} (Alg. 1, step 1).
- *   2. worst-case analysis: g = A^T xi (Alg. 1, step 3).  The atoms j not in
+ *   1. x = 0, residual xi = b, active set I = {} (the initialisation of Alg. 1).
+ *   2. worst-case analysis: g = A^T xi (Alg. 1).  The atoms j not in
  *      I with |g_j| > lambda are ranked by |g_j| (larger first, lower index on
  *      ties) and the first rho of them form J_t; I <- I u J_t.
  *      If J_t is empty the stopping condition ||xi^T A||_inf <= lambda of
  *      Sec. 2.3 holds and the loop ends.
  *   3. master problem (eq. "primal_MPL"): the LASSO restricted to I, warm
- *      started from x_I (Alg. 1, step 4), solved by accelerated proximal
+ *      started from x_I (Alg. 1), solved by accelerated proximal
  *      gradient (Nesterov/FISTA, the paper's PG rule for lambda > 0) with a
  *      backtracking line search for the step 1/L (the line search Lemma 1
  *      takes for granted) and a function-value momentum restart that keeps f monotone,
@@ -33,7 +33,7 @@
  *      satisfy |h_i - G_iP z| <= lambda, z is the exact restricted minimiser
  *      (the optimality conditions of eq. 5 on I) and replaces u.  Otherwise
  *      PG continues with a 100x tighter eps_in and the finish is retried.
- *   5. x_I = u, xi = b - A_I x_I (Alg. 1, step 8); back to 2.
+ *   5. x_I = u, xi = b - A_I x_I (the residual update of Alg. 1); back to 2.
  *
  * The worst-case analysis can alternatively use the BMPL identity
  * (eq. "batchQ"): A^T xi = beta - Q_I x_I with Q = A^T A and beta = A^T b
@@ -43,7 +43,7 @@
  * (Sec. 2.3, last paragraph): the restricted problem is least squares and the
  * finish solves G z = h directly.
  *
- * Subspace exploratory matching (SMPL, Algorithm 2; omega > 1): step 2 takes
+ * Subspace exploratory matching (SMPL, Algorithm 2; omega > 1): item 2 above takes
  * the omega*rho largest violators J_omega instead, the master problem is
  * solved on I u J_omega (warm started, new entries at zero), and only the rho
  * atoms of J_omega with the largest |u_i| stay (ties to the earlier-selected
@@ -537,7 +537,7 @@ static int solve_one(const double* At, int n, int m, const double* Q, const doub
             int j = rk[a].idx;
             w->inI[j] = 1;
             w->I[s + a] = j;
-            w->u[s + a] = 0.0; /* warm start: new entries start at zero (Alg. 1, step 4) */
+            w->u[s + a] = 0.0; /* warm start: new entries start at zero (Alg. 1) */
         }
         free(rk);
         /* new rows/columns of G = A_I^T A_I and new entries of h = A_I^T b */

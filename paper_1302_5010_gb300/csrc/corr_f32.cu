@@ -1,4 +1,4 @@
-// Worst-case analysis of Algorithm 1 (step 3) for all active signals at once:
+// Worst-case analysis of Algorithm 1 for all active signals at once:
 // the correlation scores C = A^T R, computed in plain FP32 on the SIMT cores.
 //
 // C row k holds the m scores of signal act[k]: C[k*m + j] = a_j^T r_{act[k]}.

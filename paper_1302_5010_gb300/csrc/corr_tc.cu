@@ -1,4 +1,4 @@
-// Worst-case analysis of Algorithm 1 (step 3) on the 5th-generation tensor
+// Worst-case analysis of Algorithm 1 on the 5th-generation tensor
 // cores: C = A^T R with BF16 operands and FP32 accumulation.
 //
 // Both operands are K-major rows in HBM: atoms A16 (m x n) and the compacted

@@ -1,4 +1,4 @@
-// Worst-case analysis, second half (Algorithm 1, step 3): per signal, the rho
+// Worst-case analysis of Algorithm 1, second half: per signal, the rho
 // atoms outside the active set with the largest |a_j^T r| above lambda, and
 // the stopping test ||r^T A||_inf <= lambda of Sec. 2.3.
 //
@@ -622,7 +622,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
                 for (int a = 0; a < q; ++a) {
                     const int j = (int)(0xffffffffu - (unsigned)(sh.key[a] & 0xffffffffull));
                     Si[ss + a] = j;
-                    xi[ss + a] = 0.f;  // warm start: new entries at zero (Alg. 1, step 4)
+                    xi[ss + a] = 0.f;  // warm start: new entries at zero (Alg. 1)
                     mw[j >> 5] |= 1u << (j & 31);
                 }
                 d.ssize[i] = ss + q;

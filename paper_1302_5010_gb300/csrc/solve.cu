@@ -1,15 +1,15 @@
-// Master problem (eq. "primal_MPL") and residual (Algorithm 1, steps 4-8),
+// Master problem (eq. "primal_MPL") and residual update of Algorithm 1,
 // batched over signals, plus solve set-up and output.
 //
-//   k_init      x^0 = 0, xi^0 = b, I_0 = {} (Alg. 1, step 1)
+//   k_init      x^0 = 0, xi^0 = b, I_0 = {} (the initialisation of Alg. 1)
 //   k_gram      new rows of the Gram block G_S = A_S^T A_S and h_S = A_S^T b
 //               for the atoms appended this iteration (the explicit copies of
 //               A_I that Sec. 2.4 recommends become Gram rows here)
 //   k_apg       accelerated proximal gradient on
 //                   min_u lambda*||u||_1 + 0.5 u^T G u - h^T u
-//               warm started from x_S (Alg. 1, step 4), stopped by eq. (inner)
+//               warm started from x_S (Alg. 1), stopped by eq. (inner)
 //               or s_max; persistent CTAs pull signals from a device queue
-//   k_residual  xi = b - A_S x_S (Alg. 1, step 8), FP32 (+ BF16 copy)
+//   k_residual  xi = b - A_S x_S (the residual update of Alg. 1), FP32 (+ BF16 copy)
 //   k_scatter   dense X from the active sets
 #include "mpl_internal.cuh"
 

@@ -1,4 +1,4 @@
-"""The worst-case analysis product g = A^T r (Algorithm 1, step 3) from both
+"""The worst-case analysis product g = A^T r (Algorithm 1) from both
 correlation paths, against FP64 on the same data, within the rigorous error
 bounds that the selection's candidate band relies on:
 
