@@ -118,6 +118,19 @@ __device__ __forceinline__ double bsum(double v, double* red) {
 template <typename T>
 __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* flag) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    // (r', c') of this thread's first TPOS elements of any trailing triangle (the
+    // row-major enumeration does not depend on the triangle's size)
+    constexpr int TPOS = 6;
+    int rpos[TPOS], cpos[TPOS];
+#pragma unroll
+    for (int k = 0; k < TPOS; ++k) {
+        const int e = tid + k * nt;
+        int rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        while (rr * (rr + 1) / 2 > e) --rr;
+        rpos[k] = rr;
+        cpos[k] = e - rr * (rr + 1) / 2;
+    }
     for (int j = 0; j < np; j += 4) {
         const int w = min(4, np - j);
         if (tid == 0) {
@@ -158,14 +171,22 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
             }
         }
         __syncthreads();
-        // trailing triangle: rows r >= c >= j + w, element e <-> (r', c') in row-major order
+        // trailing triangle: rows r >= c >= j + w, element e <-> (r', c') in row-major order;
+        // the first elements of a thread reuse the positions worked out before the loop
         const int b0 = j + w, nr = np - b0;
         const int tot = nr * (nr + 1) / 2;
-        for (int e = tid; e < tot; e += nt) {
-            int rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-            while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-            while (rr * (rr + 1) / 2 > e) --rr;
-            const int r = b0 + rr, c = b0 + (e - rr * (rr + 1) / 2);
+        for (int e = tid, k8 = 0; e < tot; e += nt, ++k8) {
+            int rr, cc;
+            if (k8 < TPOS) {
+                rr = rpos[k8];
+                cc = cpos[k8];
+            } else {
+                rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+                while (rr * (rr + 1) / 2 > e) --rr;
+                cc = e - rr * (rr + 1) / 2;
+            }
+            const int r = b0 + rr, c = b0 + cc;
             const T* Lr = M + (size_t)r * ld + j;
             const T* Lc = M + (size_t)c * ld + j;
             T acc = M[(size_t)r * ld + c];
