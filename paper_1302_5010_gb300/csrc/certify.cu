@@ -312,6 +312,8 @@ struct FinShared {
     double red[32];
     int ival[4];
     double dval[4];
+    int fac_np;  // rows of the FP32 factor that match P in its order (-1: rebuild next step)
+    float cs[2]; // rotation of the factor update
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -329,6 +331,134 @@ __device__ int build_support(int s, FinShared& sh) {
     }
     __syncthreads();
     return sh.ival[1];
+}
+
+// Incremental changes of the FP32 factor of G_PP when the support loses or
+// gains one atom, instead of refactoring (up to FAC_INC_MAX atoms).
+constexpr int FAC_INC_MAX = 64;
+
+// Drop factor row/column k: the trailing factor absorbs the dropped column by a
+// rank-one update (L33' L33'^T = L33 L33^T + l l^T, rotations by warp 0), then
+// rows and columns after k move up by one; P and the reciprocal diagonal follow.
+__device__ __noinline__ void fac_remove(FinShared& sh, int k, int np) {
+    float* M = sh.F.Mf;
+    const int ld = sh.F.ldf;
+    const int m = np - k - 1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        // lane owns entries lane and lane + 32 of the dropped column below the diagonal
+        float x0 = lane < m ? M[(size_t)(k + 1 + lane) * ld + k] : 0.f;
+        float x1 = lane + 32 < m ? M[(size_t)(k + 33 + lane) * ld + k] : 0.f;
+        for (int j = 0; j < m; ++j) {
+            const int J = k + 1 + j;
+            const float xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+            const float ljj = M[(size_t)J * ld + J];
+            const float r = sqrtf(ljj * ljj + xj * xj);
+            const float c = r / ljj, sn = xj / ljj;
+            __syncwarp();
+            if (lane == 0) { M[(size_t)J * ld + J] = r; sh.F.rdf[J] = 1.f / r; }
+            if (lane > j && lane < m) {
+                float* L = M + (size_t)(k + 1 + lane) * ld + J;
+                const float ln = (*L + sn * x0) / c;
+                *L = ln;
+                x0 = c * x0 - sn * ln;
+            }
+            if (lane + 32 > j && lane + 32 < m) {
+                float* L = M + (size_t)(k + 33 + lane) * ld + J;
+                const float ln = (*L + sn * x1) / c;
+                *L = ln;
+                x1 = c * x1 - sn * ln;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // move rows/columns after k by one (each thread stages up to 16 entries of one row)
+    const int r = tid >> 2, cq = tid & 3;
+    float v[16];
+    const bool live = r < np - 1;
+    const int rs = r < k ? r : r + 1;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int c = cq + 4 * u;
+        v[u] = (live && c <= r) ? M[(size_t)rs * ld + (c < k ? c : c + 1)] : 0.f;
+    }
+    float rd = 0.f;
+    int pr = 0;
+    if (tid < np - 1) { rd = sh.F.rdf[tid < k ? tid : tid + 1]; pr = sh.P[tid < k ? tid : tid + 1]; }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int c = cq + 4 * u;
+        if (live && c <= r) M[(size_t)r * ld + c] = v[u];
+    }
+    if (tid < np - 1) { sh.F.rdf[tid] = rd; sh.P[tid] = pr; }
+    __syncthreads();
+}
+
+// Append the support atom at position a as the factor's last row: forward
+// substitution L l = G_Pa by warp 0, l_nn = sqrt(G_aa - l^T l).  Returns 0, or
+// -1 when the new pivot is not positive (the caller refactors).
+__device__ __noinline__ int fac_append(FinShared& sh, const float* Gi, int smax, int a, int np) {
+    float* M = sh.F.Mf;
+    const int ld = sh.F.ldf;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        const int r0 = lane, r1 = lane + 32;
+        float y0 = r0 < np ? Gi[(size_t)sh.P[r0] * smax + a] : 0.f;
+        float y1 = r1 < np ? Gi[(size_t)sh.P[r1] * smax + a] : 0.f;
+        for (int j = 0; j < np; ++j) {
+            const float yj = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31) * sh.F.rdf[j];
+            if (lane == (j & 31)) { if (j < 32) y0 = yj; else y1 = yj; }
+            if (r0 > j && r0 < np) y0 -= M[(size_t)r0 * ld + j] * yj;
+            if (r1 > j && r1 < np) y1 -= M[(size_t)r1 * ld + j] * yj;
+        }
+        float ss = (r0 < np ? y0 * y0 : 0.f) + (r1 < np ? y1 * y1 : 0.f);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float dnn = Gi[(size_t)a * smax + a] - ss;
+        if (r0 < np) M[(size_t)np * ld + r0] = y0;
+        if (r1 < np) M[(size_t)np * ld + r1] = y1;
+        if (lane == 0) {
+            const bool ok = dnn > 0.f;
+            sh.ival[0] = ok ? 0 : 1;
+            if (ok) {
+                const float dg = sqrtf(dnn);
+                M[(size_t)np * ld + np] = dg;
+                sh.F.rdf[np] = 1.f / dg;
+                sh.P[np] = a;
+            }
+        }
+    }
+    __syncthreads();
+    return sh.ival[0] ? -1 : 0;
+}
+
+// After atoms of P were zeroed (sign 0): drop them from the FP32 factor, last
+// first, or leave the factor to be rebuilt.
+__device__ void drop_zeroed(FinShared& sh, int np) {
+    if (sh.fac_np < 0 || sh.F.fp64) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh.fac_np = -1;
+        __syncthreads();
+        return;
+    }
+    int cur = np;
+    for (int a = np - 1; a >= 0; --a)
+        if (sh.sg[sh.P[a]] == 0) fac_remove(sh, a, cur--);
+    __syncthreads();
+    if (threadIdx.x == 0) sh.fac_np = cur;
+    __syncthreads();
+}
+
+// The atom at position a joins P: append it to the FP32 factor, or leave the
+// factor to be rebuilt.
+__device__ void join_support(FinShared& sh, const float* Gi, int smax, int a, int np) {
+    const bool ok = sh.fac_np >= 0 && !sh.F.fp64 && np < FAC_INC_MAX;
+    __syncthreads();
+    const int res = ok ? fac_append(sh, Gi, smax, a, np) : -1;
+    if (threadIdx.x == 0) sh.fac_np = res == 0 ? np + 1 : -1;
+    __syncthreads();
 }
 
 // r = b - A_P x in double-FP32.  Each thread keeps 8 independent chains (8
@@ -651,34 +781,43 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
     double kkt_on = 0.0, cmax_s = 0.0;
     int np = 0;
     const int max_steps = s + 32;
-    if (tid == 0) sh.ival[3] = 0;  // 1: the last step added an atom from the exact check
+    if (tid == 0) { sh.ival[3] = 0; sh.fac_np = -1; }  // ival[3] = 1: the last step added an atom from the exact check
     for (int a = tid; a < s; a += nt) sh.adds[a] = 0;
     __syncthreads();
     int steps = 0;
     unsigned long long flops = 0;  // algorithmic work (thread 0 keeps the tally)
     for (int step = 0; step < max_steps; ++step, ++steps) {
-        np = build_support(s, sh);
+        // the FP32 factor of the previous step, updated for the atoms that left or joined P,
+        // or a new support list and factor
+        const bool inc = sh.fac_np >= 0 && !sh.F.fp64;
+        np = inc ? sh.fac_np : build_support(s, sh);
         // ---- solve on P
         if (np > 0) {
             for (int a = tid; a < np; a += nt) sh.z[a] = (double)hi[sh.P[a]] - lam * (double)sh.sg[sh.P[a]];
             FT_CNT(6);
-            flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
-            FT_SPLIT(8);
-            gather_gram(sh, Gi, smax, np);
-            FT_SPLIT(9);
-            const int fres = factor(sh.F, np, &sh.ival[0]);
-            FT_ADD(0);
-            if (fres != 0) {
-                if (sh.F.fp64) break;
-                __syncthreads();
-                if (tid == 0) sh.F.fp64 = 1;  // FP32 pivot breakdown: retry this step in FP64
-                __syncthreads();
-                --step;
-                continue;
+            if (!inc) {
+                flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
+                FT_SPLIT(8);
+                gather_gram(sh, Gi, smax, np);
+                FT_SPLIT(9);
+                const int fres = factor(sh.F, np, &sh.ival[0]);
+                FT_ADD(0);
+                if (fres != 0) {
+                    if (sh.F.fp64) break;
+                    __syncthreads();
+                    if (tid == 0) sh.F.fp64 = 1;  // FP32 pivot breakdown: retry this step in FP64
+                    __syncthreads();
+                    --step;
+                    continue;
+                }
+            } else {
+                flops += 2ull * np * np;
             }
             fsolve(sh.F, np, sh.z);
             FT_ADD(1);
         }
+        if (tid == 0) sh.fac_np = (!sh.F.fp64 && np <= FAC_INC_MAX) ? np : -1;
+        __syncthreads();
         // ---- first sign crossing on the segment x -> z.  Skipped right after the
         // exact check admitted an atom: its coefficient may be below the FP32
         // Gram block's resolution, so it goes straight to exact refinement.
@@ -719,6 +858,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
                 if (sh.x[pa] == 0.0) sh.sg[pa] = 0;
             }
             __syncthreads();
+            drop_zeroed(sh, np);
             continue;
         }
         // consistent: x <- z on P (zero elsewhere)
@@ -757,6 +897,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             }
             __syncthreads();
             if (sh.ival[0]) break;
+            join_support(sh, Gi, smax, a, np);
             continue;
         }
         // ---- exact verification: r = b - A_P x, c = A^T r (double-FP32), Newton refinement on P
@@ -826,7 +967,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             if (!lam0 && !(sh.x[pa] * (double)sh.sg[pa] > 0.0)) { sh.sg[pa] = 0; sh.x[pa] = 0.0; sh.ival[0] = 1; }
         }
         __syncthreads();
-        if (sh.ival[0]) continue;
+        if (sh.ival[0]) {
+            drop_zeroed(sh, np);
+            continue;
+        }
         flops += 2ull * n * (unsigned long long)(s - np);
         // exact check of the zero entries of S
         double cmax = 0.0;
@@ -893,6 +1037,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             }
             __syncthreads();
             if (sh.ival[0]) break;
+            join_support(sh, Gi, smax, a, np);
             continue;
         }
         kkt_on = fmax(dmax / lsc, fmax(cmax_s - lam, 0.0) / lsc);
