@@ -401,6 +401,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     const int want = d.rho * d.omega;
     const int kth = prop ? min(pa.W, m) : min(want, m);
     bool exact_scores = false;  // row holds re-scores themselves (overflow fallback)
+    float kth_floor = 0.f;      // lower bound on the kth largest re-score (s_(kth) - D)
     ST_BEGIN
     unsigned kc = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -413,6 +414,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         const unsigned kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_ADD(1);
         const float s_rho = __uint_as_float(kkey);
+        kth_floor = (s_rho - D) * (1.f - 1e-6f);
         float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
@@ -488,15 +490,26 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             }
             wsm[dst] = pa.w ? pa.w[t] : 0.f;
         }
-        for (unsigned c = tid; c < kc; c += blockDim.x)
-            sh.key[c] = ((unsigned long long)__float_as_uint(fabsf(sh.sc[c])) << 32) |
-                        (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
-        int len2 = 1;
-        while (len2 < (int)kc) len2 <<= 1;
-        for (int t = kc + tid; t < len2; t += blockDim.x) sh.key[t] = 0ull;
+        // only candidates that can be among the W largest re-scores are sorted: the W-th
+        // largest re-score is at least s_(W) - D
+        if (tid == 0) sh.vc = 0;
         __syncthreads();
-        if (kc > 1) sort_desc(sh, len2);
-        const int W = min((int)kc, pa.W);
+        for (unsigned c = tid; c < kc; c += blockDim.x) {
+            const float a = fabsf(sh.sc[c]);
+            if (a >= kth_floor) {
+                const unsigned pos = atomicAdd(&sh.vc, 1u);
+                sh.key[pos] = ((unsigned long long)__float_as_uint(a) << 32) |
+                              (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
+            }
+        }
+        __syncthreads();
+        const unsigned kw = sh.vc;
+        int len2 = 1;
+        while (len2 < (int)kw) len2 <<= 1;
+        for (int t = kw + tid; t < len2; t += blockDim.x) sh.key[t] = 0ull;
+        __syncthreads();
+        if (kw > 1) sort_desc(sh, len2);
+        const int W = min((int)kw, pa.W);
         const float f1 = logf(fmaxf(rn, 1e-30f) / lam);
         const float gscale = rsqrtf(1.f + (float)m / (float)n);
         // logits (or examples) for the W candidates, in score order
