@@ -22,8 +22,9 @@
 // worst-case analysis certifies the atoms outside S (eq. 8).
 //
 // One CTA per signal.  Shared memory is sized by the host from its bound on
-// |S|; the FP64 factor lives in shared memory up to FIN_SMEM_P atoms and in a
-// global FP64 workspace beyond.
+// |S|; the FP32 factor lives in shared memory when the bound fits there at two
+// CTAs per SM; larger FP32 factors and the FP64 factor use the signal's global
+// workspace.
 #include "mpl_internal.cuh"
 
 namespace mpl {
@@ -252,13 +253,61 @@ __device__ void solve_warp_reg(const T* M, int ld, int np, const T* rdiag, T* v)
     __syncwarp();
 }
 
+// (L L^T) v = v by the CTA in blocks of 32 unknowns: warp 0 solves each diagonal
+// block with the right-hand side in registers, then all threads apply the block to
+// the remaining unknowns (rows of L below it going forward, its columns going back).
+template <typename T>
+__device__ void solve_cta(const T* M, int ld, int np, const T* rdiag, T* v) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    for (int b0 = 0; b0 < np; b0 += 32) {  // forward: L y = v
+        const int bw = min(32, np - b0);
+        if (tid < 32) {
+            T y = lane < bw ? v[b0 + lane] : T(0);
+            for (int j = 0; j < bw; ++j) {
+                const T yj = __shfl_sync(0xffffffffu, y, j) * rdiag[b0 + j];
+                if (lane == j) y = yj;
+                if (lane > j && lane < bw) y -= M[(size_t)(b0 + lane) * ld + b0 + j] * yj;
+            }
+            if (lane < bw) v[b0 + lane] = y;
+        }
+        __syncthreads();
+        for (int r = b0 + bw + tid; r < np; r += nt) {
+            const T* Lr = M + (size_t)r * ld + b0;
+            T acc = T(0);
+            for (int c = 0; c < bw; ++c) acc += Lr[c] * v[b0 + c];
+            v[r] -= acc;
+        }
+        __syncthreads();
+    }
+    for (int b1 = np; b1 > 0; b1 -= 32) {  // backward: L^T x = y
+        const int b0 = max(0, b1 - 32), bw = b1 - b0;
+        if (tid < 32) {
+            T y = lane < bw ? v[b0 + lane] : T(0);
+            for (int j = bw - 1; j >= 0; --j) {
+                const T xj = __shfl_sync(0xffffffffu, y, j) * rdiag[b0 + j];
+                if (lane == j) y = xj;
+                if (lane < j) y -= M[(size_t)(b0 + j) * ld + b0 + lane] * xj;
+            }
+            if (lane < bw) v[b0 + lane] = y;
+        }
+        __syncthreads();
+        for (int r = tid; r < b0; r += nt) {
+            T acc = T(0);
+            for (int c = 0; c < bw; ++c) acc += M[(size_t)(b0 + c) * ld + r] * v[b0 + c];
+            v[r] -= acc;
+        }
+        __syncthreads();
+    }
+}
+
 // Block version: warp 0 runs the sweeps (each sum is split over its lanes).
 template <typename T>
 __device__ void solve_block(const T* M, int ld, int np, const T* rdiag, T* v) {
-    if (threadIdx.x < 32) {
-        if (np <= 64) solve_warp_reg(M, ld, np, rdiag, v);
-        else solve_warp(M, ld, np, rdiag, v);
+    if (np > 64) {
+        solve_cta(M, ld, np, rdiag, v);
+        return;
     }
+    if (threadIdx.x < 32) solve_warp_reg(M, ld, np, rdiag, v);
     __syncthreads();
 }
 
@@ -286,11 +335,12 @@ __device__ void fsolve(const Factor& F, int np, double* v) {
     if (!F.fp64) {
         for (int a = threadIdx.x; a < np; a += blockDim.x) F.vf[a] = (float)v[a];
         __syncthreads();
-        if (threadIdx.x < 32) {
-            if (np <= 64) solve_warp_reg(F.Mf, F.ldf, np, F.rdf, F.vf);
-            else solve_warp(F.Mf, F.ldf, np, F.rdf, F.vf);
+        if (np > 64) {
+            solve_cta(F.Mf, F.ldf, np, F.rdf, F.vf);
+        } else {
+            if (threadIdx.x < 32) solve_warp_reg(F.Mf, F.ldf, np, F.rdf, F.vf);
+            __syncthreads();
         }
-        __syncthreads();
         for (int a = threadIdx.x; a < np; a += blockDim.x) v[a] = (double)F.vf[a];
         __syncthreads();
         return;
@@ -738,9 +788,13 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         float* q = reinterpret_cast<float*>(p);
         sh.F.rdf = q; q += scap;
         sh.F.vf = q; q += scap;
-        sh.F.ldf = (scap + 1) | 1;  // odd stride spreads a column over the banks
-        sh.F.Mf = msm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
-        if (msm) q += (size_t)scap * sh.F.ldf;
+        // the FP32 factor sits in shared memory when the signal's whole active set fits
+        // the msm x msm area the launch reserved, else in the signal's global workspace;
+        // an odd stride spreads a column over the banks
+        const bool fsm = s <= msm;
+        sh.F.ldf = fsm ? ((msm + 1) | 1) : ((scap + 1) | 1);
+        sh.F.Mf = fsm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
+        if (msm) q += (size_t)msm * ((msm + 1) | 1);
         sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
         sh.Pi = sh.sg + scap;
@@ -1120,7 +1174,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
 cudaError_t prepare_finish() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIN_SMEM_MAX);
     if (e == cudaSuccess) attr = true;
     return e;
 }
@@ -1129,11 +1183,16 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     if (ub <= 0) return cudaSuccess;
     scap = ((scap + 31) / 32) * 32;
     if (scap > d.smax) scap = d.smax;
-    const int msm = scap <= FIN_SMEM_P ? 1 : 0;
-    const size_t ldf = (size_t)((scap + 1) | 1);
+    // shared-memory factor area: the whole bound while two CTAs still fit on an SM
+    auto dyn_of = [&](int mf, int rs) {
+        return 4 * (size_t)scap * sizeof(double) + (2 * (size_t)scap + (size_t)mf * ((mf + 1) | 1)) * sizeof(float) +
+               4 * (size_t)scap * sizeof(int) + (rs ? 2 * (size_t)d.n * sizeof(float) : 0);
+    };
     const int rsm = d.n <= 4096 ? 1 : 0;
-    const size_t dyn = 4 * (size_t)scap * sizeof(double) + (2 * scap + (msm ? scap * ldf : 0)) * sizeof(float) +
-                       4 * (size_t)scap * sizeof(int) + (rsm ? 2 * (size_t)d.n * sizeof(float) : 0);
+    // (one CTA per SM with a larger area loses more to the halved concurrency than the
+    // shared-memory factor gains, so the area is the bound or nothing)
+    const int msm = dyn_of(scap, rsm) <= FIN_SMEM_TWO_CTAS ? scap : 0;
+    const size_t dyn = dyn_of(msm, rsm);
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
     k_finish<<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);

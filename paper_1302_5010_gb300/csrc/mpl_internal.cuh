@@ -185,7 +185,8 @@ constexpr int SEL_ROWCACHE_ATOMS = 8192;  // score rows up to this length are ca
 constexpr int APG_SMEM_S = 200;
 constexpr int APG_THREADS = 256;
 // Exact finish: FP32 factor in shared memory up to this support size (global beyond).
-constexpr int FIN_SMEM_P = 128;
+constexpr size_t FIN_SMEM_TWO_CTAS = 110 * 1024;  // dynamic shared memory that keeps 2 finish CTAs per SM
+constexpr size_t FIN_SMEM_MAX = 225 * 1024;       // the most one finish CTA takes
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_MAX_PIVOTS = 16;
 constexpr int FIN_MAX_FAILS = 6;
