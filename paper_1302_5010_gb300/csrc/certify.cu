@@ -111,13 +111,15 @@ __device__ __forceinline__ double bsum(double v, double* red) {
 
 
 
-// Blocked right-looking Cholesky by the whole CTA, panels of four columns: one
-// thread factors the 4 x 4 diagonal block, the threads take the panel's rows
-// below it, then the trailing lower triangle gets the rank-4 update with its
-// elements spread evenly over the CTA.  Three CTA barriers per four columns.
+// Blocked right-looking Cholesky by the whole CTA, panels of W columns: one
+// thread factors the W x W diagonal block, the threads take the panel's rows
+// below it, then the trailing lower triangle gets the rank-W update with its
+// elements spread evenly over the CTA.  Three CTA barriers per panel.  With the
+// factor in global memory (stage != null) the panel is kept in shared memory
+// and wide panels (fewer passes over the trailing triangle) pay off.
 // Returns 0 or -1 (non-positive pivot); flag likewise.
-template <typename T>
-__device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* flag) {
+template <typename T, int W>
+__device__ __noinline__ int chol_panel(T* M, int ld, int np, T* rdiag, int* flag, T* stage = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     // (r', c') of this thread's first TPOS elements of any trailing triangle (the
     // row-major enumeration does not depend on the triangle's size)
@@ -132,8 +134,8 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
         rpos[k] = rr;
         cpos[k] = e - rr * (rr + 1) / 2;
     }
-    for (int j = 0; j < np; j += 4) {
-        const int w = min(4, np - j);
+    for (int j = 0; j < np; j += W) {
+        const int w = min(W, np - j);
         if (tid == 0) {
             int bad = 0;
             for (int k = 0; k < w && !bad; ++k) {
@@ -158,9 +160,9 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
         // panel rows below the diagonal block
         for (int r = j + w + tid; r < np; r += nt) {
             T* Rr = M + (size_t)r * ld + j;
-            T l[4];
+            T l[W];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < W; ++k) {
                 if (k < w) {
                     const T* Rk = M + (size_t)(j + k) * ld + j;
                     T v = Rr[k];
@@ -168,6 +170,7 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
                     for (int q = 0; q < k; ++q) v -= l[q] * Rk[q];
                     l[k] = v * rdiag[j + k];
                     Rr[k] = l[k];
+                    if (stage) stage[(size_t)r * W + k] = l[k];
                 }
             }
         }
@@ -176,6 +179,40 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
         // the first elements of a thread reuse the positions worked out before the loop
         const int b0 = j + w, nr = np - b0;
         const int tot = nr * (nr + 1) / 2;
+        if (stage) {
+            // factor in global memory: the panel comes from shared memory and each
+            // thread keeps four element loads in flight before its stores
+            for (int e0 = tid; e0 < tot; e0 += 4 * nt) {
+                int rr4[4], cc4[4];
+                T a4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * nt;
+                    rr4[u] = -1;
+                    if (e < tot) {
+                        int rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+                        while (rr * (rr + 1) / 2 > e) --rr;
+                        rr4[u] = b0 + rr;
+                        cc4[u] = b0 + (e - rr * (rr + 1) / 2);
+                        a4[u] = M[(size_t)rr4[u] * ld + cc4[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (rr4[u] < 0) continue;
+                    const T* Lr = stage + (size_t)rr4[u] * W;
+                    const T* Lc = stage + (size_t)cc4[u] * W;
+                    T acc = a4[u];
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        if (k < w) acc -= Lr[k] * Lc[k];
+                    M[(size_t)rr4[u] * ld + cc4[u]] = acc;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         for (int e = tid, k8 = 0; e < tot; e += nt, ++k8) {
             int rr, cc;
             if (k8 < TPOS) {
@@ -192,7 +229,7 @@ __device__ __noinline__ int chol_panel4(T* M, int ld, int np, T* rdiag, int* fla
             const T* Lc = M + (size_t)c * ld + j;
             T acc = M[(size_t)r * ld + c];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < W; ++k)
                 if (k < w) acc -= Lr[k] * Lc[k];
             M[(size_t)r * ld + c] = acc;
         }
@@ -315,19 +352,25 @@ __device__ void solve_block(const T* M, int ld, int np, const T* rdiag, T* v) {
 // FP32-accurate; refinement with exact residuals recovers full accuracy), or
 // FP64 in the global workspace when FP32 refinement stagnates.  Every thread
 // of the CTA returns the same result.
+constexpr int FAC_PANEL_GLOBAL = 4;   // panel width of a factor in global memory
+
 struct Factor {
     float* Mf;       // FP32 factor, leading dimension ldf
     float* rdf;
     double* Md;      // FP64 factor (global workspace), leading dimension ldd
     double* rdd;     // reciprocal diagonal for the FP64 factor
     float* vf;       // FP32 right-hand side scratch
+    float* stage;    // panel staging (np x FAC_PANEL_GLOBAL) for an FP32 factor in global memory, else null
     int ldf, ldd;
     int fp64;        // which factor is current
 };
 
 __device__ int factor(Factor& F, int np, int* flag) {
-    if (!F.fp64) return chol_panel4(F.Mf, F.ldf, np, F.rdf, flag);
-    return chol_panel4(F.Md, F.ldd, np, F.rdd, flag);
+    if (!F.fp64) {
+        if (F.stage) return chol_panel<float, FAC_PANEL_GLOBAL>(F.Mf, F.ldf, np, F.rdf, flag, F.stage);
+        return chol_panel<float, 4>(F.Mf, F.ldf, np, F.rdf, flag);
+    }
+    return chol_panel<double, 4>(F.Md, F.ldd, np, F.rdd, flag);
 }
 
 // v <- G_PP^{-1} v with the current factor (FP32 factor: solved in FP32).
@@ -795,6 +838,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         sh.F.ldf = fsm ? ((msm + 1) | 1) : ((scap + 1) | 1);
         sh.F.Mf = fsm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
         if (msm) q += (size_t)msm * ((msm + 1) | 1);
+        sh.F.stage = msm ? nullptr : q;  // panel staging for a factor in global memory
+        if (!msm) q += (size_t)FAC_PANEL_GLOBAL * scap;
         sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
         sh.Pi = sh.sg + scap;
@@ -1185,7 +1230,8 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     if (scap > d.smax) scap = d.smax;
     // shared-memory factor area: the whole bound while two CTAs still fit on an SM
     auto dyn_of = [&](int mf, int rs) {
-        return 4 * (size_t)scap * sizeof(double) + (2 * (size_t)scap + (size_t)mf * ((mf + 1) | 1)) * sizeof(float) +
+        return 4 * (size_t)scap * sizeof(double) +
+               (2 * (size_t)scap + (mf ? (size_t)mf * ((mf + 1) | 1) : (size_t)FAC_PANEL_GLOBAL * scap)) * sizeof(float) +
                4 * (size_t)scap * sizeof(int) + (rs ? 2 * (size_t)d.n * sizeof(float) : 0);
     };
     const int rsm = d.n <= 4096 ? 1 : 0;
