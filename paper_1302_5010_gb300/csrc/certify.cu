@@ -352,7 +352,7 @@ __device__ void solve_block(const T* M, int ld, int np, const T* rdiag, T* v) {
 // FP32-accurate; refinement with exact residuals recovers full accuracy), or
 // FP64 in the global workspace when FP32 refinement stagnates.  Every thread
 // of the CTA returns the same result.
-constexpr int FAC_PANEL_GLOBAL = 4;   // panel width of a factor in global memory
+constexpr int FAC_PANEL_GLOBAL = 8;   // panel width of a factor in global memory
 
 struct Factor {
     float* Mf;       // FP32 factor, leading dimension ldf
