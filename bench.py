@@ -249,14 +249,16 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         solver.set(mpl.MPL_OPT_WARM_START, 2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    # one-time tuning on the batch (identity route, handshake cadence), like the layout
+    # one-time tuning on the batch (identity route, handshake cadence, Gram from Q), like the layout
     # work of mpl_create it is outside the timed region
     tune = None
     if args.tune:
-        qr, se = (int(v) for v in args.tune.split(","))
+        vals = [int(v) for v in args.tune.split(",")]
+        qr, se, qg = (vals + [0])[:3]
         solver.set(mpl.MPL_OPT_QROUTE, qr)
         solver.set(mpl.MPL_OPT_SYNC_EVERY, se)
-        tune = {"qroute": qr, "sync_every": se, "fixed": True}
+        solver.set(mpl.MPL_OPT_QGRAM, qg)
+        tune = {"qroute": qr, "sync_every": se, "qgram": qg, "fixed": True}
     elif not args.no_autotune:
         tune = solver.autotune(B, lam, TOL, stream)
     def timed_steps(profile: bool, clocks=None):
@@ -379,7 +381,7 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default route and handshake cadence")
-    ap.add_argument("--tune", default=None, metavar="QROUTE,SYNC",
+    ap.add_argument("--tune", default=None, metavar="QROUTE,SYNC[,QGRAM]",
                     help="fix the tuned settings instead of running the autotuner (profiling runs)")
     ap.add_argument("--ref-signals", type=int, default=64)
     ap.add_argument("--cpu-signals", type=int, default=256)

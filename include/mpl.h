@@ -90,13 +90,22 @@ typedef enum {
                                      Negative = off (default) */
     MPL_OPT_STOP_R2 = 16,         /* eq. (stop1): stop once ||xi|| <= this value.  Negative =
                                      off (default) */
-    MPL_OPT_STOP_EPS = 17         /* eq. (stop_con): stop after a master problem whose decrease
+    MPL_OPT_STOP_EPS = 17,        /* eq. (stop_con): stop after a master problem whose decrease
                                      of the objective, f(x^{t-1}) - f(x^t), is <= this value
                                      times |rho f(x^0)|, f(x^0) = ||b||^2 / 2.  Negative = off
                                      (default).  A stopped signal gets the exact restricted
                                      solution on its S and status MPL_SIG_EARLY_STOP; lambda = 0
                                      (least squares, the OMP reduction of Sec. 2.5 with rho = 1)
                                      needs one of these rules or MPL_OPT_MAX_OUTER to end. */
+    MPL_OPT_QGRAM = 18            /* 1: the Gram growth reads the new entries of A_S^T A_S from
+                                     Q = A^T A (Sec. 3: Q is precomputed off-line for the batch,
+                                     and the master problem's Gram block Q_SS is a sub-block of
+                                     it) instead of multiplying the atoms' columns; the entries
+                                     of A_S^T b for the new atoms are one FP32 FMA chain each.
+                                     Q (4 m^2 bytes) is built on first use, as for
+                                     MPL_OPT_QROUTE, by one FMA chain per entry in the order
+                                     the computed Gram block uses, so the solution is
+                                     bit-identical either way.  0 = compute (default). */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -261,8 +270,9 @@ int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
  * candidate setting -- the identity route for the first k = 0, 1, 2, 4 outer
  * iterations after the first (MPL_OPT_QROUTE = k rho plus the warm-start
  * additions; k > 0 only when Q = A^T A fits in a quarter of the free device
- * memory) and MPL_OPT_SYNC_EVERY in {1, 2, 4} -- and keeps the fastest on the
- * handle.  Every candidate computes the same solution, so only time is
+ * memory) and MPL_OPT_SYNC_EVERY in {1, 2, 4}; then, where Q fits, the best
+ * of those with MPL_OPT_QGRAM = 1 at each MPL_OPT_SYNC_EVERY -- and keeps the
+ * fastest on the handle.  Every candidate computes the same solution, so only time is
  * compared.  Each candidate runs once untimed (graph capture, Q build) and
  * three times timed with events on `stream`; the median counts.  The solutions
  * go to a scratch buffer the call allocates and frees; the handle's last-solve
@@ -273,8 +283,9 @@ typedef struct {
     int qroute;          /* chosen MPL_OPT_QROUTE */
     int sync_every;      /* chosen MPL_OPT_SYNC_EVERY */
     double ms;           /* median solve time of the choice */
-    double ms_default;   /* median solve time with qroute 0 and sync_every 2 */
+    double ms_default;   /* median solve time with qroute 0, sync_every 2, qgram 0 */
     int candidates;      /* settings timed */
+    int qgram;           /* chosen MPL_OPT_QGRAM */
 } mpl_tune_result_t;
 mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* lambda, double tol,
                           void* stream, mpl_tune_result_t* out);

@@ -108,7 +108,95 @@ __global__ void k_gram_q_prep(Counters* cnt, int* act, int m) {
     }
 }
 
+// Gram growth from Q (Sec. 3: Q = A^T A is precomputed off-line, and the master
+// problem's Gram block G_SS is its S x S sub-block).  For each growing signal
+// the new columns of G_SS are copied out of Q, and h = A_S^T b gets its new
+// entries.  Q was built by the FP32 GEMM with one FMA chain per entry over k
+// ascending, the order of the computed Gram block, and h here is the same kind
+// of chain (a_k b_k, k ascending, from 0), so G and h are the same bits as
+// launch_gram's.
+constexpr int GQ_BUF = 10240;  // floats of the staging buffer for the h chains
+
+__global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
+    const int g = blockIdx.x;
+    if (g >= d.cnt->grow_n) return;
+    const int i = d.list_grow[g];
+    const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
+    if (q == 0) return;  // a refine pass: the block is complete
+    const int n = d.n, m = d.m, smax = d.smax;
+    const int* Si = d.S + (size_t)i * smax;
+    float* Gi = d.G + (size_t)i * smax * smax;
+    __shared__ int sidx[1024];  // smax <= 1024
+    __shared__ __align__(16) float hbuf[GQ_BUF];
+    for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
+    __syncthreads();
+    // new columns (and, by symmetry, rows) of G_SS: independent loads, all in flight
+    const int total = s * q;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int a = e / q, c = e - a * q;
+        const float v = __ldg(d.Q + (size_t)sidx[a] * m + sidx[s0 + c]);
+        Gi[(size_t)a * smax + s0 + c] = v;
+        Gi[(size_t)(s0 + c) * smax + a] = v;
+    }
+    // h of the new atoms, one FMA chain per atom (thread), over k ascending.  The
+    // atoms' columns and b pass through shared memory kc entries at a time (coalesced
+    // loads by the whole block), so the chains wait on shared memory, not on L2.
+    const float* b = d.B + (size_t)i * n;
+    const bool vec = (n & 3) == 0;
+    for (int c0 = 0; c0 < q; c0 += 256) {
+        const int qg = min(256, q - c0);
+        const int kc = (GQ_BUF / (qg + 1) - 4) & ~31;  // >= 32
+        const int ks = kc + 4;  // = 4 (mod 32): a row per thread, float4 reads conflict-free
+        const int c = threadIdx.x;
+        float acc = 0.f;
+        for (int k0 = 0; k0 < n; k0 += kc) {
+            const int kw = min(kc, n - k0);
+            __syncthreads();  // the previous chunk is consumed
+            if (vec) {
+                const int v4 = kw >> 2;
+                for (int e = threadIdx.x; e < (qg + 1) * v4; e += blockDim.x) {
+                    const int r = e / v4, k4 = e - r * v4;
+                    const float* src = (r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b) + k0 + 4 * k4;
+                    *reinterpret_cast<float4*>(hbuf + r * ks + 4 * k4) = __ldg(reinterpret_cast<const float4*>(src));
+                }
+            } else {
+                for (int e = threadIdx.x; e < (qg + 1) * kw; e += blockDim.x) {
+                    const int r = e / kw, k = e - r * kw;
+                    const float* src = r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b;
+                    hbuf[r * ks + k] = __ldg(src + k0 + k);
+                }
+            }
+            __syncthreads();
+            if (c < qg) {
+                const float* ar = hbuf + c * ks;
+                const float* br = hbuf + qg * ks;
+                if (vec) {
+#pragma unroll 4
+                    for (int k = 0; k < kw; k += 4) {
+                        const float4 a4 = *reinterpret_cast<const float4*>(ar + k);
+                        const float4 b4 = *reinterpret_cast<const float4*>(br + k);
+                        acc = fmaf(a4.x, b4.x, acc);
+                        acc = fmaf(a4.y, b4.y, acc);
+                        acc = fmaf(a4.z, b4.z, acc);
+                        acc = fmaf(a4.w, b4.w, acc);
+                    }
+                } else {
+                    for (int k = 0; k < kw; ++k) acc = fmaf(ar[k], br[k], acc);
+                }
+            }
+        }
+        if (c < qg) d.h[(size_t)i * smax + s0 + c0 + c] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    k_gram_gather<<<ub, 256, 0, s>>>(d);
+    ++*nl;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_corr_q(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;

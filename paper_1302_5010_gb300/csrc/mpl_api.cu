@@ -79,6 +79,8 @@ struct mpl_ctx {
     double eps_in = 1e-4;
     // identity route (eq. batchQ): taken at outer iterations whose bound on |S| is <= qroute
     int qroute = 0;
+    // Gram growth gathered from Q instead of computed (MPL_OPT_QGRAM)
+    int qgram = 0;
     int omega = 1;           // subspace search length (Algorithm 2); 1 = Algorithm 1
     double stop_rinf = -1.0, stop_r2 = -1.0, stop_eps = -1.0;  // early stopping (Sec. 2.5)
     float* Q = nullptr;      // m x m Gram matrix, built on first use, freed with the handle
@@ -457,6 +459,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v < 0 || v > 1024) return MPL_ERR_ARG;
             h->qroute = (int)v;
             return MPL_OK;
+        case MPL_OPT_QGRAM:
+            if (v != 0 && v != 1) return MPL_ERR_ARG;
+            h->qgram = (int)v;
+            return MPL_OK;
         case MPL_OPT_OMEGA:
             if (v < 1 || v > 16) return MPL_ERR_ARG;
             h->omega = (int)v;
@@ -486,6 +492,7 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_MAX: *v = h->warm_max; return MPL_OK;
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
+        case MPL_OPT_QGRAM: *v = h->qgram; return MPL_OK;
         case MPL_OPT_OMEGA: *v = h->omega; return MPL_OK;
         case MPL_OPT_STOP_RINF: *v = h->stop_rinf; return MPL_OK;
         case MPL_OPT_STOP_R2: *v = h->stop_r2; return MPL_OK;
@@ -494,8 +501,8 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
     }
 }
 
-// Q = A^T A (once per handle) and the beta rows for p signals, for the identity route.
-static mpl_status_t ensure_identity_route(mpl_ctx* h, int p, cudaStream_t st, int64_t* nl) {
+// Q = A^T A, once per handle (identity route, Gram gather).
+static mpl_status_t ensure_q(mpl_ctx* h, cudaStream_t st, int64_t* nl) {
     const int n = h->n, m = h->m;
     if (!h->Q) {
         CK(cudaMalloc(&h->Q, (size_t)m * m * sizeof(float)));
@@ -511,6 +518,14 @@ static mpl_status_t ensure_identity_route(mpl_ctx* h, int p, cudaStream_t st, in
         CK(es);
         clear_graphs(h);
     }
+    return MPL_OK;
+}
+
+// Q and the beta rows for p signals, for the identity route.
+static mpl_status_t ensure_identity_route(mpl_ctx* h, int p, cudaStream_t st, int64_t* nl) {
+    const mpl_status_t qs = ensure_q(h, st, nl);
+    if (qs != MPL_OK) return qs;
+    const int m = h->m;
     if (h->beta_cap < p) {
         cudaFree(h->beta);
         h->beta = nullptr;
@@ -613,7 +628,11 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     e0 = pt ? pt->begin_if(3, run) : nullptr;
     const int qmax = (t == 0 && h->warm == 2) ? d.rho + warm_additions(h, d) : d.omega * d.rho;
-    if ((e = launch_gram(d, act_ub, qmax, run, nl)) != cudaSuccess) return e;
+    if (h->qgram) {
+        if ((e = launch_gram_gather(d, act_ub, run, nl)) != cudaSuccess) return e;
+    } else if ((e = launch_gram(d, act_ub, qmax, run, nl)) != cudaSuccess) {
+        return e;
+    }
     if (pt) pt->end(3, e0, run);
     e0 = pt ? pt->begin_if(5, run) : nullptr;
     if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) return e;
@@ -741,6 +760,10 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         if (qs != MPL_OK) return qs;
         d.Q = h->Q;
         d.beta = h->beta;
+    } else if (h->qgram) {
+        mpl_status_t qs = ensure_q(h, st, &nl);
+        if (qs != MPL_OK) return qs;
+        d.Q = h->Q;
     }
 
     if (h->warm == 2 && !h->prop_ready) return MPL_ERR_ARG;  // no proposal weights loaded
@@ -1153,14 +1176,19 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int keep_q = h->qroute, keep_se = h->sync_every, keep_prof = h->profile;
+    const int keep_q = h->qroute, keep_se = h->sync_every, keep_prof = h->profile, keep_g = h->qgram;
     h->profile = 0;
-    mpl_tune_result_t best{keep_q, keep_se, 1e300, 0.0, 0};
+    mpl_tune_result_t best{keep_q, keep_se, 1e300, 0.0, 0, keep_g};
     mpl_status_t first_err = MPL_OK;
-    for (int qr : qcands) {
+    // stage 0: identity route x handshake interval with the computed Gram; stage 1: the
+    // Gram gathered from Q with the stage-0 route at each handshake interval
+    for (int stage = 0; stage < 2; ++stage)
+    for (int qr : (stage == 0 ? qcands : std::vector<int>{best.qroute})) {
+        if (stage == 1 && (!q_fits || best.candidates == 0)) break;
         for (int se : se_cands) {
             h->qroute = qr;
             h->sync_every = se;
+            h->qgram = stage;
             clear_graphs(h);
             mpl_status_t rc = bmpl_solve(h, B, p, lambda, X, tol, stream);  // capture + warm-up
             std::vector<float> t;
@@ -1180,8 +1208,8 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
             std::sort(t.begin(), t.end());
             const double med = t[t.size() / 2];
             ++best.candidates;
-            if (qr == 0 && se == 2) best.ms_default = med;
-            if (med < best.ms) { best.ms = med; best.qroute = qr; best.sync_every = se; }
+            if (qr == 0 && se == 2 && stage == 0) best.ms_default = med;
+            if (med < best.ms) { best.ms = med; best.qroute = qr; best.sync_every = se; best.qgram = stage; }
         }
     }
     cudaEventDestroy(e0);
@@ -1192,10 +1220,12 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
     if (best.candidates == 0) {
         h->qroute = keep_q;
         h->sync_every = keep_se;
+        h->qgram = keep_g;
         return first_err != MPL_OK ? first_err : MPL_ERR_CUDA;
     }
     h->qroute = best.qroute;
     h->sync_every = best.sync_every;
+    h->qgram = best.qgram;
     if (out) *out = best;
     return MPL_OK;
 }

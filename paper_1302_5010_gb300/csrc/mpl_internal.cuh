@@ -146,6 +146,8 @@ cudaError_t build_gram_q(const float* A32, int n, int m, float* Q, int* act, Cou
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 // qmax: most atoms a signal can take this iteration (picks the tile width).
 cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl);
+// Gram growth gathered from Q (MPL_OPT_QGRAM): same outputs, bit for bit, as launch_gram.
+cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);

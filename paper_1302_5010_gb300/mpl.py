@@ -45,6 +45,7 @@ MPL_OPT_OMEGA = 14
 MPL_OPT_STOP_RINF = 15
 MPL_OPT_STOP_R2 = 16
 MPL_OPT_STOP_EPS = 17
+MPL_OPT_QGRAM = 18
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -74,7 +75,7 @@ class SignalStats(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("qroute", ctypes.c_int32), ("sync_every", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32)]
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32), ("qgram", ctypes.c_int32)]
 
 
 class MplError(RuntimeError):
@@ -313,7 +314,7 @@ class Solver:
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
                     warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE,
                     omega=MPL_OPT_OMEGA, stop_rinf=MPL_OPT_STOP_RINF, stop_r2=MPL_OPT_STOP_R2,
-                    stop_eps=MPL_OPT_STOP_EPS)
+                    stop_eps=MPL_OPT_STOP_EPS, qgram=MPL_OPT_QGRAM)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 

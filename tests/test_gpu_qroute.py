@@ -7,7 +7,11 @@ ranks by the same fixed-order FP32 re-score as the GEMM route, so a solve that
 takes the identity route at some or all iterations must pick the same atoms at
 every outer iteration and return bit-identical solutions.  The oracle's own
 identity route (corr_route = 1) is pinned against its direct route on CPU; here
-the GPU route is checked against the GPU GEMM route and the FP64 oracle."""
+the GPU route is checked against the GPU GEMM route and the FP64 oracle.
+
+The Gram growth read out of Q (MPL_OPT_QGRAM) gives the same G and h bits as
+the computed Gram block (one FMA chain per entry, k ascending, on both
+sides), so every solve with it must equal the one without it bit for bit."""
 import numpy as np
 import pytest
 
@@ -88,6 +92,52 @@ def test_identity_route_warm_start():
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gram_from_q_is_bit_identical_c2(precision):
+    P = synth.make_config("c2", p=64)
+    Xg, X64g, rg = solve_gpu(P, precision=precision)
+    Xq, X64q, rq = solve_gpu(P, precision=precision, qgram=1)
+    assert_certified(rq)
+    for k in ("outer_iters", "inner_iters", "active_size", "finishes"):
+        np.testing.assert_array_equal(rg.stats[k], rq.stats[k])
+    np.testing.assert_array_equal(Xg, Xq)
+    np.testing.assert_array_equal(X64g, X64q)
+
+
+@pytest.mark.parametrize("n,m,p,rho,omega", [(198, 777, 9, 3, 1), (260, 1000, 13, 5, 1), (256, 1000, 11, 4, 3)])
+def test_gram_from_q_ragged(n, m, p, rho, omega):
+    """n % 4 != 0: the scalar Gram kernel and the scalar h chain; n % 16 != 0:
+    the vector chain's ragged tail; omega > 1: Algorithm 2's explored atoms."""
+    P = synth.small_problem(n, m, p, 4, min(30, n // 6), rho=rho, seed=3 * n + m + p, lam_frac=0.03)
+    Xg, _, _ = solve_gpu(P, precision=0, omega=omega)
+    X, X64, res = solve_gpu(P, precision=0, omega=omega, qgram=1)
+    assert_certified(res)
+    np.testing.assert_array_equal(X, Xg)
+    check_against_oracle(P, X64, oracle_solve(P))
+
+
+def test_gram_from_q_with_identity_route_and_warm_start():
+    import torch
+    P = synth.make_config("c2", p=32)
+    Pt = synth.make_config("c2", p=1024, seed_shift=9000)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1)
+    Xt = torch.empty((Pt.p, Pt.m), device="cuda")
+    s.solve(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt)
+    s.train_proposal(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt, epochs=2)
+    s.set(mpl.MPL_OPT_WARM_START, 2)
+    B, lam = torch.from_numpy(P.B).cuda(), torch.from_numpy(P.lam).cuda()
+    X0 = torch.empty((P.p, P.m), device="cuda")
+    s.solve(B, lam, X0)
+    s.set(mpl.MPL_OPT_QGRAM, 1)
+    s.set(mpl.MPL_OPT_QROUTE, 2 * P.rho)
+    X1 = torch.empty((P.p, P.m), device="cuda")
+    r1 = s.solve(B, lam, X1)
+    torch.cuda.synchronize()
+    assert np.all(r1.stats["status"] == mpl.MPL_SIG_CERTIFIED)
+    assert torch.equal(X0, X1)
+    s.close()
+
+
 def test_autotune_keeps_the_solution():
     import torch
     P = synth.make_config("c2", p=64)
@@ -99,9 +149,11 @@ def test_autotune_keeps_the_solution():
     assert t["candidates"] >= 3
     assert t["sync_every"] in (1, 2, 4)
     assert t["qroute"] in [0] + [min(256, k * P.rho) for k in (1, 2, 4)]
+    assert t["qgram"] in (0, 1) and t["candidates"] >= 12  # Q fits: both stages ran
     assert 0 < t["ms"] <= t["ms_default"] + 1e-9
     assert s.h is not None and mpl.mpl_get_option(s.h, mpl.MPL_OPT_QROUTE) == t["qroute"]
     assert mpl.mpl_get_option(s.h, mpl.MPL_OPT_SYNC_EVERY) == t["sync_every"]
+    assert mpl.mpl_get_option(s.h, mpl.MPL_OPT_QGRAM) == t["qgram"]
     X1 = torch.empty((P.p, P.m), device="cuda")
     r = s.solve(B, lam, X1)
     torch.cuda.synchronize()
