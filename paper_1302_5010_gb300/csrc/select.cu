@@ -130,8 +130,9 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
 }
 
 // Copy the score row and the membership bitmap into shared memory (loads
-// batched eight deep so that they are in flight together).
-__device__ void fill_cache(const float* row, const uint32_t* msk_g, int m, SelSmem& sh) {
+// batched eight deep so that they are in flight together).  Returns the largest
+// key this thread wrote.
+__device__ unsigned fill_cache(const float* row, const uint32_t* msk_g, int m, SelSmem& sh) {
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned* keys = reinterpret_cast<unsigned*>(sh.row);
     // the membership bitmap (m / 32 <= 256 words) staged in the histogram, free until the radix passes
@@ -139,6 +140,7 @@ __device__ void fill_cache(const float* row, const uint32_t* msk_g, int m, SelSm
     for (int w = tid; w < (m + 31) / 32; w += nt) msk[w] = msk_g[w];
     __syncthreads();
     int nf = 0;
+    unsigned tmax = 0;
     for (int j0 = tid; j0 < m; j0 += 8 * nt) {
         float v[8];
 #pragma unroll
@@ -149,11 +151,16 @@ __device__ void fill_cache(const float* row, const uint32_t* msk_g, int m, SelSm
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int j = j0 + u * nt;
-            if (j < m) keys[j] = key_of(v, msk, j, u, &nf);
+            if (j < m) {
+                const unsigned kj = key_of(v, msk, j, u, &nf);
+                keys[j] = kj;
+                tmax = max(tmax, kj);
+            }
         }
     }
     if (nf) sh.nonfinite = 1;
     __syncthreads();
+    return tmax;
 }
 
 // Keys read from the cache (S members and non-finite scores already 0) or
@@ -270,6 +277,106 @@ __device__ unsigned radix_kth(K key, int m, int kth, SelSmem& sh) {
         }
     }
     return prefix;
+}
+
+// Key of the kth largest cached key without a histogram, for kth <= 512 (one
+// thread per key of the short list below).  Each thread's largest key is known
+// from fill_cache.  Let jw = ceil(kth / warps); every warp has jw threads whose
+// largest key is at least the warp's jw-th largest thread maximum, so at least
+// kth distinct keys are >= T = the minimum of those over the warps: T is a lower
+// bound on the kth largest key.  The keys >= T (with their atoms) go to a list
+// in sh.key as (key << 32 | j); the kth largest is the entry with exactly
+// kth - 1 entries above it.  Returns false (the caller takes the radix passes)
+// when T is 0 or the list has more than blockDim.x entries.  On success *tlo = T
+// and *below = the largest key < T (for the bound on the atoms left out).
+__device__ bool fast_kth(const unsigned* keys, int m, int kth, unsigned tmax, SelSmem& sh, unsigned* kkey,
+                         unsigned* tlo, unsigned* below) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int jw = (kth + nw - 1) / nw;
+    if (jw > 32) return false;
+    unsigned v = tmax;
+    if (jw == 1) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    } else {
+        // bitonic sort of the warp's 32 thread maxima, descending from lane 0
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const unsigned o = __shfl_xor_sync(0xffffffffu, v, j);
+                const bool desc = (lane & k) == 0, lower = (lane & j) == 0;
+                v = (desc == lower) ? max(v, o) : min(v, o);
+            }
+        }
+        v = __shfl_sync(0xffffffffu, v, jw - 1);
+    }
+    if (tid == 0) sh.lcnt = 0;
+    if (lane == 0) sh.wsum[warp] = v;
+    __syncthreads();
+    unsigned T = 0xffffffffu;
+    for (int w = 0; w < nw; ++w) T = min(T, sh.wsum[w]);
+    if (T == 0u) return false;  // uniform: every thread read the same values
+    // the list: keys >= T (warp-aggregated slots); the largest key below T
+    unsigned omax = 0;
+    for (int jb = tid - lane; jb < m; jb += nt) {
+        const int j = jb + lane;
+        const unsigned kj = j < m ? keys[j] : 0u;
+        const bool take = j < m && kj >= T;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sh.lcnt, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+            const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (pos < (unsigned)nt) sh.key[pos] = ((unsigned long long)kj << 32) | (unsigned)j;
+        } else {
+            omax = max(omax, kj);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    if (tid == 0) sh.outmax = 0;
+    __syncthreads();
+    if (lane == 0 && omax) atomicMax(&sh.outmax, omax);
+    const unsigned c = sh.lcnt;
+    if (c > (unsigned)nt) return false;  // uniform
+    if (tid < (int)c) {
+        const unsigned long long e = sh.key[tid];
+        unsigned above = 0;
+        for (unsigned u = 0; u < c; ++u) above += sh.key[u] > e ? 1u : 0u;
+        if (above == (unsigned)kth - 1u) sh.bin = (unsigned)(e >> 32);
+    }
+    __syncthreads();
+    *kkey = sh.bin;
+    *tlo = T;
+    *below = sh.outmax;
+    return true;
+}
+
+// The band { j : key >= tkey } from the list of fast_kth (tkey >= its T): into
+// sh.idx, with the largest key left outside (list keys below tkey, or below T).
+__device__ unsigned collect_list(unsigned tkey, unsigned below, SelSmem& sh) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned c = sh.lcnt;
+    if (tid == 0) { sh.kc = 0; sh.outmax = below; }
+    __syncthreads();
+    unsigned omax = 0;
+    for (unsigned t0 = tid - lane; t0 < c; t0 += blockDim.x) {
+        const unsigned t = t0 + lane;
+        const unsigned long long e = t < c ? sh.key[t] : 0ull;
+        const unsigned kj = (unsigned)(e >> 32);
+        const bool take = t < c && kj >= tkey;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sh.kc, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) sh.idx[base + __popc(bal & ((1u << lane) - 1u))] = (int)(unsigned)(e & 0xffffffffull);
+        else if (t < c) omax = max(omax, kj);
+    }
+    if (omax) atomicMax(&sh.outmax, omax);
+    __syncthreads();
+    return sh.kc;
 }
 
 // Collect { j not in S : key >= tkey } into sh.idx (capacity SEL_KCAP) and the
@@ -407,18 +514,21 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     for (int attempt = 0; attempt < 2; ++attempt) {
         const float D = exact_scores ? 0.f : delta + delta32;
         const bool cache = m <= SEL_ROWCACHE;
-        if (cache) fill_cache(row, msk, m, sh);
+        const unsigned tmax = cache ? fill_cache(row, msk, m, sh) : 0u;
         ST_ADD(0);
         const CachedKeys ck{reinterpret_cast<const unsigned*>(sh.row)};
         const RowKeys rk{row, msk};
-        const unsigned kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
+        unsigned kkey = 0, tlo = 0, below = 0;
+        const bool listed = cache && fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);
+        if (!listed) kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_ADD(1);
         const float s_rho = __uint_as_float(kkey);
         kth_floor = (s_rho - D) * (1.f - 1e-6f);
         float tau = prop ? s_rho - 2.f * D : fmaxf(s_rho - 2.f * D, lam_sel - (exact_scores ? delta32 : D));
         tau = tau * (1.f - 1e-6f);  // keep the band closed under rounding of the bound itself
         const unsigned tkey = tau > 0.f ? __float_as_uint(tau) : 1u;
-        kc = cache ? collect(ck, m, tkey, sh) : collect(rk, m, tkey, sh);
+        if (listed && tkey >= tlo) kc = collect_list(tkey, below, sh);
+        else kc = cache ? collect(ck, m, tkey, sh) : collect(rk, m, tkey, sh);
         ST_ADD(2);
         if (kc <= (unsigned)SEL_KCAP || exact_scores) break;
         if (d.ovf_list) {
