@@ -22,14 +22,16 @@ namespace mpl {
 #ifdef MPL_SEL_TRACE
 // Per-signal phase cycle counters of the selection (diagnostic builds only):
 // [row cache, radix passes, collect, re-score, sort + state, calls]
-__device__ long long g_sel_trace[8192][8];
+__device__ long long g_sel_trace[8192][10];
 #define ST_BEGIN long long st0_ = clock64();
 #define ST_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += clock64() - st0_; st0_ = clock64(); } while (0)
 #define ST_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += 1; } while (0)
+#define ST_VAL(slot, v) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += (v); } while (0)
 #else
 #define ST_BEGIN
 #define ST_ADD(slot) do {} while (0)
 #define ST_CNT(slot) do {} while (0)
+#define ST_VAL(slot, v) do {} while (0)
 #endif
 
 namespace {
@@ -129,33 +131,57 @@ __device__ __forceinline__ unsigned key_of(const float* row, const uint32_t* msk
     return u;
 }
 
-// Copy the score row and the membership bitmap into shared memory (loads
-// batched eight deep so that they are in flight together).  Returns the largest
-// key this thread wrote.
+// Copy the score row and the membership bitmap into shared memory.  Thread t
+// owns atoms j = 4 (t + u nt) + e (u, e < 4): four float4 loads (scalar loads
+// when rows are not 16-byte aligned), all in flight together and issued before
+// the bitmap is staged, so both round trips overlap.  Returns the largest key
+// this thread wrote.
+__device__ __forceinline__ int own_atom(int tid, int nt, int u, int e) { return 4 * (tid + u * nt) + e; }
+
 __device__ unsigned fill_cache(const float* row, const uint32_t* msk_g, int m, SelSmem& sh) {
+    static_assert(SEL_ROWCACHE <= 16 * SEL_THREADS, "one pass covers the cached row");
     const int tid = threadIdx.x, nt = blockDim.x;
     unsigned* keys = reinterpret_cast<unsigned*>(sh.row);
     // the membership bitmap (m / 32 <= 256 words) staged in the histogram, free until the radix passes
     uint32_t* msk = sh.hist;
+    float4 v[4];
+    if ((m & 3) == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = own_atom(tid, nt, u, 0);
+            v[u] = j < m ? __ldcg(reinterpret_cast<const float4*>(row + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = own_atom(tid, nt, u, 0);
+            v[u].x = j + 0 < m ? row[j + 0] : 0.f;
+            v[u].y = j + 1 < m ? row[j + 1] : 0.f;
+            v[u].z = j + 2 < m ? row[j + 2] : 0.f;
+            v[u].w = j + 3 < m ? row[j + 3] : 0.f;
+        }
+    }
     for (int w = tid; w < (m + 31) / 32; w += nt) msk[w] = msk_g[w];
     __syncthreads();
     int nf = 0;
     unsigned tmax = 0;
-    for (int j0 = tid; j0 < m; j0 += 8 * nt) {
-        float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = j0 + u * nt;
-            v[u] = j < m ? row[j] : 0.f;
+    for (int u = 0; u < 4; ++u) {
+        const int j = own_atom(tid, nt, u, 0);
+        if (j >= m) continue;
+        const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        unsigned k4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            k4[e] = j + e < m ? key_of(f, msk, j + e, e, &nf) : 0u;
+            tmax = max(tmax, k4[e]);
         }
+        if (j + 3 < m) {
+            *reinterpret_cast<uint4*>(keys + j) = make_uint4(k4[0], k4[1], k4[2], k4[3]);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = j0 + u * nt;
-            if (j < m) {
-                const unsigned kj = key_of(v, msk, j, u, &nf);
-                keys[j] = kj;
-                tmax = max(tmax, kj);
-            }
+            for (int e = 0; e < 4; ++e)
+                if (j + e < m) keys[j + e] = k4[e];
         }
     }
     if (nf) sh.nonfinite = 1;
@@ -311,39 +337,40 @@ __device__ bool fast_kth(const unsigned* keys, int m, int kth, unsigned tmax, Se
         }
         v = __shfl_sync(0xffffffffu, v, jw - 1);
     }
-    if (tid == 0) sh.lcnt = 0;
+    if (tid == 0) { sh.lcnt = 0; sh.outmax = 0; }
     if (lane == 0) sh.wsum[warp] = v;
     __syncthreads();
-    unsigned T = 0xffffffffu;
-    for (int w = 0; w < nw; ++w) T = min(T, sh.wsum[w]);
-    if (T == 0u) return false;  // uniform: every thread read the same values
-    // the list: keys >= T (warp-aggregated slots); the largest key below T
-    unsigned omax = 0;
-    for (int jb = tid - lane; jb < m; jb += nt) {
-        const int j = jb + lane;
-        const unsigned kj = j < m ? keys[j] : 0u;
-        const bool take = j < m && kj >= T;
-        const unsigned bal = __ballot_sync(0xffffffffu, take);
-        unsigned base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&sh.lcnt, (unsigned)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take) {
-            const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (pos < (unsigned)nt) sh.key[pos] = ((unsigned long long)kj << 32) | (unsigned)j;
-        } else {
-            omax = max(omax, kj);
+    unsigned T = lane < nw ? sh.wsum[lane] : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) T = min(T, __shfl_xor_sync(0xffffffffu, T, o));
+    if (T == 0u) return false;  // uniform: every warp reduced the same values
+    // the list: keys >= T.  A thread whose largest key is below T has nothing to add,
+    // and that key is its largest below T; the few others scan their keys.
+    unsigned omax = tmax;
+    if (tmax >= T) {
+        omax = 0;
+        for (int q = 0; q < 16; ++q) {
+            const int j = own_atom(tid, nt, q >> 2, q & 3);
+            if (j >= m) break;
+            const unsigned kj = keys[j];
+            if (kj >= T) {
+                const unsigned pos = atomicAdd(&sh.lcnt, 1u);
+                if (pos < (unsigned)nt) sh.key[pos] = ((unsigned long long)kj << 32) | (unsigned)j;
+            } else {
+                omax = max(omax, kj);
+            }
         }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
-    if (tid == 0) sh.outmax = 0;
-    __syncthreads();
     if (lane == 0 && omax) atomicMax(&sh.outmax, omax);
+    __syncthreads();
     const unsigned c = sh.lcnt;
     if (c > (unsigned)nt) return false;  // uniform
     if (tid < (int)c) {
         const unsigned long long e = sh.key[tid];
         unsigned above = 0;
+#pragma unroll 8
         for (unsigned u = 0; u < c; ++u) above += sh.key[u] > e ? 1u : 0u;
         if (above == (unsigned)kth - 1u) sh.bin = (unsigned)(e >> 32);
     }
@@ -426,6 +453,31 @@ __device__ void sort_desc(SelSmem& sh, int len) {
             __syncthreads();
         }
     }
+}
+
+// sh.key[0..cnt) (distinct keys) in descending order.  Up to one key per
+// thread: each key's rank is the number of keys above it, and it is written
+// there (two barriers); otherwise the bitonic network over len (a power of two
+// >= cnt, keys [cnt, len) zero).  The row cache is free by then and holds the
+// ranked copy.
+__device__ void sort_keys_desc(SelSmem& sh, int cnt, int len) {
+    if (cnt <= 1) return;
+    if (cnt > (int)blockDim.x) {
+        sort_desc(sh, len);
+        return;
+    }
+    unsigned long long* tmp = reinterpret_cast<unsigned long long*>(sh.row);
+    const int t = threadIdx.x;
+    if (t < cnt) {
+        const unsigned long long e = sh.key[t];
+        int r = 0;
+#pragma unroll 8
+        for (int u = 0; u < cnt; ++u) r += sh.key[u] > e ? 1 : 0;
+        tmp[r] = e;
+    }
+    __syncthreads();
+    if (t < cnt) sh.key[t] = tmp[t];
+    __syncthreads();
 }
 
 // Proposal network forward pass for one candidate by one warp (weights in
@@ -521,6 +573,8 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         unsigned kkey = 0, tlo = 0, below = 0;
         const bool listed = cache && fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);
         if (!listed) kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
+        ST_VAL(7, listed ? 1 : 0);
+        ST_VAL(8, listed ? sh.lcnt : 0);
         ST_ADD(1);
         const float s_rho = __uint_as_float(kkey);
         kth_floor = (s_rho - D) * (1.f - 1e-6f);
@@ -550,6 +604,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         delta = delta32;
     }
     kc = min(kc, (unsigned)SEL_KCAP);
+    ST_VAL(6, kc);
 
     // Re-score the candidates (one warp each) and mark the violators.
     if (tid == 0) { sh.vc = 0; sh.offmax = 0.f; }
@@ -618,7 +673,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         while (len2 < (int)kw) len2 <<= 1;
         for (int t = kw + tid; t < len2; t += blockDim.x) sh.key[t] = 0ull;
         __syncthreads();
-        if (kw > 1) sort_desc(sh, len2);
+        sort_keys_desc(sh, (int)kw, len2);
         const int W = min((int)kw, pa.W);
         const float f1 = logf(fmaxf(rn, 1e-30f) / lam);
         const float gscale = rsqrtf(1.f + (float)m / (float)n);
@@ -671,7 +726,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         __syncthreads();
         for (int t = tid; t < len3; t += blockDim.x) sh.key[t] = t < n2 ? sh.key[SEL_KCAP / 2 + t] : 0ull;
         __syncthreads();
-        if (n2 > 1) sort_desc(sh, len3);
+        sort_keys_desc(sh, n2, len3);
         if (tid == 0) {
             d.outer[i] += 1;
             int q = 0;
@@ -710,7 +765,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     while (len < vc) len <<= 1;
     for (int t = vc + tid; t < len; t += blockDim.x) sh.key[t] = 0ull;
     __syncthreads();
-    if (vc > 1) sort_desc(sh, len);
+    sort_keys_desc(sh, vc, len);
 
     // State transition (one thread).
     ST_ADD(4);
@@ -866,9 +921,9 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
 extern "C" int mpl_debug_sel_trace(long long* out, int count, int reset) {
     if (count > 8192) count = 8192;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-    if (cudaMemcpyFromSymbol(out, g_sel_trace, sizeof(long long) * 8 * (size_t)count) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, g_sel_trace, sizeof(long long) * 10 * (size_t)count) != cudaSuccess) return -1;
     if (reset) {
-        static long long zero[8192][8];
+        static long long zero[8192][10];
         if (cudaMemcpyToSymbol(g_sel_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
     }
     return count;
