@@ -1156,21 +1156,27 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         }
         for (int a = tid; a < np; a += nt) cm = fmax(cm, fabs(sh.w[a] + lam * (double)sh.sg[sh.P[a]]));
         double* r64 = d.R64 + (size_t)i * n;
-        double rr = 0.0, rb = 0.0, rs = 0.0;
+        double rr = 0.0, rb = 0.0, rs = 0.0, es = 0.0, ts = 0.0;
         for (int k = tid; k < n; k += nt) {
             const double v = (double)rh[k] + (double)rl[k];
             r64[k] = v;
             if (rsm) { d.R32[(size_t)i * n + k] = rh[k]; d.R32lo[(size_t)i * n + k] = rl[k]; }
-            if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(rh[k]);
-            if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = __float2bfloat16_rn(rh[k]);
+            const __nv_bfloat16 q = __float2bfloat16_rn(rh[k]);
+            if (d.R16) d.R16[(size_t)i * n + k] = q;
+            if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = q;
             rr += v * v;
             rb += v * (double)b[k];
             rs += (double)rh[k] * (double)rh[k];
+            const double fq = (double)__bfloat162float(q), e = (double)rh[k] - fq;
+            es += e * e;
+            ts += fq * fq;
         }
         const double L1 = bsum(l1, sh.red);
         const double RR = bsum(rr, sh.red);
         const double RB = bsum(rb, sh.red);
         const double RS = bsum(rs, sh.red);
+        const double ES = bsum(es, sh.red);
+        const double TS = bsum(ts, sh.red);
 #pragma unroll
         for (int o = 16; o; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
         __syncthreads();
@@ -1183,6 +1189,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             d.rr[i] = RR;
             d.rb[i] = RB;
             d.rnorm[i] = (float)(sqrt(RS) * (1.0 + 1e-5));
+            d.r16e[i] = (float)(sqrt(ES) * (1.0 + 1e-5));
+            d.r16t[i] = (float)(sqrt(TS) * (1.0 + 1e-5));
             if (d.xl1) d.xl1[i] = __double2float_ru(L1 * (1.0 + 1e-6));
             d.kkt_in[i] = kkt_on;
             d.ginf[i] = fmax(CM, cmax_s);

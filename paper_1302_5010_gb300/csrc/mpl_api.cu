@@ -45,6 +45,7 @@ struct mpl_ctx {
     float* colnorm = nullptr;
     float* scal = nullptr;  // device scalars: [0] = max column norm
     float colmax = 0.f;
+    float bf_ea = 0.f, bf_ta = 0.f;  // max_j ||a_j - bf(a_j)||, max_j ||bf(a_j)|| (rounded up)
     // options
     int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
     int sync_every = 2, profile = 0;
@@ -203,6 +204,8 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
                     &d.list_apg, &d.explore, &d.early};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
+    CK(alloc(h, &d.r16e, (size_t)P));
+    CK(alloc(h, &d.r16t, (size_t)P));
     CK(alloc(h, &d.bnorm, (size_t)P));
     CK(alloc(h, &d.xl1, (size_t)P));
     CK(alloc(h, &d.f0, (size_t)P));
@@ -267,6 +270,33 @@ void set_bounds(mpl_ctx* h, Dev& d) {
     } else {
         d.bound_c = (float)(c32 * 1.01);
     }
+    // the measured form of the same bound: a^T r - bf(a)^T bf(r) = (a - bf(a))^T r +
+    // bf(a)^T (r - bf(r)) exactly, each term bounded by Cauchy-Schwarz, plus the
+    // accumulation term on sum |bf(a_k) bf(r_k)| <= ||bf(a)|| ||bf(r)||
+    d.bf_ea = h->bf_ea;
+    d.bf_ta = h->bf_ta;
+    d.bf_acc = (float)(1.25 * (double)h->n * std::ldexp(1.0, -22));
+}
+
+// The BF16 copy of the dictionary (once per handle), with the rounding constants of
+// its measured error bound.
+static mpl_status_t ensure_a16(mpl_ctx* h, cudaStream_t st, int64_t* nl) {
+    if (h->A16) return MPL_OK;
+    const int n = h->n, m = h->m;
+    float* err2 = nullptr;
+    CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
+    CK(cudaMalloc(&err2, 2 * (size_t)m * sizeof(float)));
+    cudaError_t e = launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, nl, err2);
+    if (e == cudaSuccess) e = launch_max_reduce(err2, m, h->scal + 1, st, nl);
+    if (e == cudaSuccess) e = launch_max_reduce(err2 + m, m, h->scal + 2, st, nl);
+    float v[2] = {0.f, 0.f};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, h->scal + 1, 2 * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err2);
+    CK(e);
+    h->bf_ea = v[0];
+    h->bf_ta = v[1];
+    return MPL_OK;
 }
 
 // Phase index of the identity-route correlation (timed apart from the GEMM).
@@ -716,9 +746,9 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     cudaStream_t st = h->main;
     CK(cudaEventRecord(h->ev_in, caller));
     CK(cudaStreamWaitEvent(st, h->ev_in, 0));
-    if (h->precision == 1 && !h->A16) {
-        CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
-        CK(launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, &nl));
+    if (h->precision == 1) {
+        const mpl_status_t sa = ensure_a16(h, st, &nl);
+        if (sa != MPL_OK) return sa;
     }
     // arguments: B and lambda into the handle's fixed buffers (device or host source)
     CK(cudaMemcpyAsync(h->Bint, B, (size_t)n * p * sizeof(float), cudaMemcpyDefault, st));
@@ -845,9 +875,9 @@ mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void
     if (ws != MPL_OK) return ws;
     const int n = h->n, m = h->m;
     int64_t nl = 0;
-    if (h->precision == 1 && !h->A16) {
-        CK(cudaMalloc(&h->A16, (size_t)n * m * sizeof(__nv_bfloat16)));
-        CK(launch_colnorm(h->A32, n, m, h->colnorm, h->A16, st, &nl));
+    if (h->precision == 1) {
+        const mpl_status_t sa = ensure_a16(h, st, &nl);
+        if (sa != MPL_OK) return sa;
     }
     const float* Rd = R;
     if (!is_device_ptr(R)) {
@@ -985,10 +1015,10 @@ static mpl_status_t prop_setup(mpl_ctx* h) {
         CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     }
-    if (h->precision == 1 && !h->A16) {
+    if (h->precision == 1) {
         int64_t nl = 0;
-        CK(cudaMalloc(&h->A16, (size_t)h->n * h->m * sizeof(__nv_bfloat16)));
-        CK(launch_colnorm(h->A32, h->n, h->m, h->colnorm, h->A16, h->main, &nl));
+        const mpl_status_t sa = ensure_a16(h, h->main, &nl);
+        if (sa != MPL_OK) return sa;
     }
     return ensure_rownorms(h, h->main);
 }

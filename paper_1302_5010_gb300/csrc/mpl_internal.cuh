@@ -43,6 +43,12 @@ struct Dev {
     double tol;
     float colmax;                // max_j ||a_j|| (rounded up)
     float bound_c;               // |score_gemm - a_j^T r| <= bound_c * colmax * ||r||
+    // BF16 GEMM, measured rounding: |score - a_j^T r| <= bf_ea ||r|| + bf_ta (||r - bf(r)|| +
+    // bf_acc ||bf(r)||) + bound_c32 colmax ||r||, with bf_ea >= max_j ||a_j - bf(a_j)|| and
+    // bf_ta >= max_j ||bf(a_j)|| (per dictionary), the residual terms per signal (r16e, r16t)
+    float bf_ea, bf_ta, bf_acc;
+    float* r16e;                 // p ||r - bf(r)|| upper bound (mixed)
+    float* r16t;                 // p ||bf(r)|| upper bound (mixed)
     float bound_c32;             // same for the fixed-order FP32 re-score
     float bound_f32;             // FP32 correlation GEMM (either precision)
     float bound_q;               // identity route: |score - a_j^T r| <= bound_q*colmax*(||b|| + colmax*||x||_1)
@@ -157,8 +163,9 @@ cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl);
 cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, int64_t* nl);
 cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl);
 cudaError_t launch_pack_stats(const Dev& d, mpl_signal_stats_t* out, cudaStream_t s, int64_t* nl);
+// err2 (2m floats, may be null): ||a_j - bf(a_j)|| and ||bf(a_j)||, rounded up.
 cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
-                           cudaStream_t s, int64_t* nl);
+                           cudaStream_t s, int64_t* nl, float* err2 = nullptr);
 cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t s, int64_t* nl);
 
 // Proposal network support (proposal.cu).

@@ -4,7 +4,10 @@
 //
 // One CTA per active signal.  The correlation scores come from a GEMM whose
 // error against the exact a_j^T r is bounded by delta = bound_c*colmax*||r||
-// (FP32: gamma_n; BF16 operands: 2^-7 plus the accumulation term).  The atoms
+// (FP32: gamma_n; BF16 operands: 2^-7 plus the accumulation term), or for the
+// BF16 GEMM by the measured form ||a_j - bf(a_j)|| ||r|| + ||bf(a_j)|| ||r - bf(r)||
+// plus the accumulation term (maxima over j kept per dictionary, the residual
+// terms per signal), whichever is smaller.  The atoms
 // whose GEMM score can still matter,
 //     K = { j not in S : s_j >= max(s_(rho) - 2D, lambda(1+tol) - D) },
 // with s_(rho) the rho-th largest GEMM score and D the bound between a GEMM
@@ -550,6 +553,13 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     // |score - a^T r| for the route that produced this iteration's scores
     float delta = route == ROUTE_Q ? d.bound_q * d.colmax * (d.bnorm[i] + d.colmax * d.xl1[i])
                                    : (route == ROUTE_GEMM_F32 ? d.bound_f32 : d.bound_c) * d.colmax * rn;
+    if (route == ROUTE_GEMM && d.precision == 1 && d.bf_ta > 0.f) {
+        // the BF16 GEMM's bound from the measured rounding of this dictionary and this
+        // residual (both bounds hold; the measured one is the tighter in practice)
+        const float meas = (d.bf_ea * rn + d.bf_ta * (d.r16e[i] + d.bf_acc * d.r16t[i])) * 1.001f +
+                           d.bound_c32 * d.colmax * rn;
+        delta = fminf(delta, meas);
+    }
     if (tid == 0) sh.nonfinite = 0;
     __syncthreads();
 

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
     const float* b = d.B + (size_t)i * n;
     float* r32 = d.R32 + (size_t)i * n;
     double* r64 = d.R64 + (size_t)i * n;
-    double ss = 0.0;
+    double ss = 0.0, es = 0.0, ts = 0.0;
     int nf = 0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const float v = b[k];
@@ -75,14 +75,24 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         r32[k] = v;
         d.R32lo[(size_t)i * n + k] = 0.f;
         r64[k] = (double)v;
-        if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(v);
-        if (d.pos) d.R16c[(size_t)i * n + k] = __float2bfloat16_rn(v);  // active list = identity
+        const __nv_bfloat16 q = __float2bfloat16_rn(v);
+        if (d.R16) d.R16[(size_t)i * n + k] = q;
+        if (d.pos) d.R16c[(size_t)i * n + k] = q;  // active list = identity
         ss += (double)v * (double)v;
+        const double fq = (double)__bfloat162float(q), e = (double)v - fq;
+        es += e * e;
+        ts += fq * fq;
     }
     uint32_t* mw = d.mask + (size_t)i * d.mw;
     for (int w = threadIdx.x; w < d.mw; w += blockDim.x) mw[w] = 0u;
     nf = __syncthreads_or(nf);
     const double bb = block_sum_d(ss, red);
+    const double ee = block_sum_d(es, red);
+    const double tt = block_sum_d(ts, red);
+    if (threadIdx.x == 0) {
+        d.r16e[i] = __double2float_ru(sqrt(ee) * (1.0 + 1e-6));
+        d.r16t[i] = __double2float_ru(sqrt(tt) * (1.0 + 1e-6));
+    }
     if (threadIdx.x == 0) {
         const float lam = d.lam[i];
         const bool bad = nf || !(lam >= 0.f) || !isfinite(lam);  // lambda = 0: least squares
@@ -651,7 +661,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     __shared__ int nzi[1024];
     __shared__ float nzv[1024];
     __shared__ int cntnz;
-    __shared__ float red[32];
+    __shared__ float red[96];
     if (threadIdx.x == 0) cntnz = 0;
     __syncthreads();
     const float* xi = d.xS + (size_t)i * smax;
@@ -680,7 +690,14 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     }
     const float* b = d.B + (size_t)i * n;
     float* r32 = d.R32 + (size_t)i * n;
-    float ss = 0.f;
+    float ss = 0.f, es = 0.f, ts = 0.f;  // ||r||^2, ||r - bf(r)||^2, ||bf(r)||^2
+    const bool r16 = d.R16 || d.pos;
+    auto bf_terms = [&](float v) {
+        const float fq = __bfloat162float(__float2bfloat16_rn(v));
+        const float e = v - fq;  // exact (Sterbenz)
+        es = fmaf(e, e, es);
+        ts = fmaf(fq, fq, ts);
+    };
     if ((n & 3) == 0) {
         // float4 columns, four atoms per pass with their loads issued first
         for (int k = threadIdx.x * 4; k < n; k += blockDim.x * 4) {
@@ -720,6 +737,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
             }
             ss = fmaf(acc.x, acc.x, ss); ss = fmaf(acc.y, acc.y, ss);
             ss = fmaf(acc.z, acc.z, ss); ss = fmaf(acc.w, acc.w, ss);
+            if (r16) { bf_terms(acc.x); bf_terms(acc.y); bf_terms(acc.z); bf_terms(acc.w); }
         }
     } else {
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -729,11 +747,15 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
             if (d.R16) d.R16[(size_t)i * n + k] = __float2bfloat16_rn(acc);
             if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = __float2bfloat16_rn(acc);
             ss = fmaf(acc, acc, ss);
+            if (r16) bf_terms(acc);
         }
     }
-    const float t = block_sum(ss, red);
+    // FP32 sums: a few roundings per term and a 256-way tree, far inside the 1e-5 margin
+    block_sum3(ss, es, ts, red);
     if (threadIdx.x == 0) {
-        d.rnorm[i] = sqrtf(t) * (1.f + 1e-5f);
+        d.rnorm[i] = sqrtf(ss) * (1.f + 1e-5f);
+        d.r16e[i] = sqrtf(es) * (1.f + 1e-5f);
+        d.r16t[i] = sqrtf(ts) * (1.f + 1e-5f);
         d.nnz[i] = nz;
     }
 }
@@ -849,20 +871,37 @@ __global__ void k_scatter(Dev d, float* X, double* X64) {
 }
 
 // ------------------------------------------------------------------ dictionary prep
-__global__ void k_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16) {
+__global__ void k_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16, float* err2) {
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (j >= m) return;
     const float* a = A32 + (size_t)j * n;
-    double ss = 0.0;
+    double ss = 0.0, es = 0.0, ts = 0.0;
     for (int k = lane; k < n; k += 32) {
         const float v = a[k];
         ss += (double)v * (double)v;
-        if (A16) A16[(size_t)j * n + k] = __float2bfloat16_rn(v);
+        if (A16) {
+            const __nv_bfloat16 q = __float2bfloat16_rn(v);
+            A16[(size_t)j * n + k] = q;
+            const double fq = (double)__bfloat162float(q), e = (double)v - fq;  // both exact in FP64
+            es += e * e;
+            ts += fq * fq;
+        }
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) colnorm[j] = __double2float_ru(sqrt(ss));
+    for (int o = 16; o; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        es += __shfl_xor_sync(0xffffffffu, es, o);
+        ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    }
+    if (lane == 0) {
+        colnorm[j] = __double2float_ru(sqrt(ss));
+        // FP64 sums of at most n squares: relative error far below the 1e-6 margin
+        if (err2) {
+            err2[j] = __double2float_ru(sqrt(es) * (1.0 + 1e-6));
+            err2[m + j] = __double2float_ru(sqrt(ts) * (1.0 + 1e-6));
+        }
+    }
 }
 
 __global__ void k_max_reduce(const float* v, int len, float* out) {
@@ -1048,9 +1087,9 @@ cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, 
 }
 
 cudaError_t launch_colnorm(const float* A32, int n, int m, float* colnorm, __nv_bfloat16* A16,
-                           cudaStream_t s, int64_t* nl) {
+                           cudaStream_t s, int64_t* nl, float* err2) {
     const int per = 8;  // warps per block
-    k_colnorm<<<(m + per - 1) / per, per * 32, 0, s>>>(A32, n, m, colnorm, A16);
+    k_colnorm<<<(m + per - 1) / per, per * 32, 0, s>>>(A32, n, m, colnorm, A16, err2);
     ++*nl;
     return cudaGetLastError();
 }
