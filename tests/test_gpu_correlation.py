@@ -5,6 +5,8 @@ bounds that the selection's candidate band relies on:
   FP32 SIMT path:   |c - a^T r| <= gamma_n * sum_k |a_k r_k|
   BF16 tensor path: |c - a16^T r16| <= n 2^-22 * sum_k |a16_k r16_k|   (accumulation)
                     |c - a^T r| <= (2^-7 + 2^-16 + n 2^-22) * ||a|| ||r||   (operands)
+                    |c - a^T r| <= ||a - a16|| ||r|| + ||a16|| (||r - r16|| + n 2^-22 ||r16||)
+                                                       (the measured form the selection uses)
 """
 import numpy as np
 import pytest
@@ -68,3 +70,23 @@ def test_bf16_path_within_bounds(n, m, p):
     assert np.all(np.abs(C - exact) <= bound)
     # and it is a real bf16 product, not a float32 one in disguise
     assert np.abs(C - exact).max() > 1e-6 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("n,m,p", SHAPES)
+def test_bf16_path_within_measured_bound(n, m, p):
+    """The measured form, with the dictionary terms maximised over the atoms as the
+    selection keeps them, holds for every score; it is far below the worst case."""
+    At, R = _data(n, m, p, 11 * n + m + p)
+    C = _run(At, R, 1)
+    A64, R64 = At.astype(np.float64), R.astype(np.float64)
+    A16, R16 = _bf16(At).astype(np.float64), _bf16(R).astype(np.float64)
+    ea = np.linalg.norm(A64 - A16, axis=1).max()
+    ta = np.linalg.norm(A16, axis=1).max()
+    rn = np.linalg.norm(R64, axis=1)
+    er = np.linalg.norm(R64 - R16, axis=1)
+    tr = np.linalg.norm(R16, axis=1)
+    bound = ea * rn + ta * (er + 1.25 * n * 2.0 ** -22 * tr)
+    err = np.abs(C - R64 @ A64.T)
+    assert np.all(err <= bound[:, None]), (err / bound[:, None]).max()
+    worst = (2.0 ** -7 + 2.0 ** -16 + n * 2.0 ** -22) * rn * np.linalg.norm(A64, axis=1).max()
+    assert np.all(bound < 0.6 * worst)
