@@ -36,6 +36,7 @@ __device__ __forceinline__ float4 load4(const float* row, int k, int n) {
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
+    pdl_enter();
     const int act_n = d.cnt->act_n_of(cur);
     // signal tiles vary fastest, so the blocks in flight share their atom tile in L2
     // (the dictionary streams from HBM once per launch)
@@ -134,8 +135,9 @@ cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s,
     if (act_n_ub <= 0) return cudaSuccess;
     dim3 grid((act_n_ub + BN - 1) / BN, (d.m + BM - 1) / BM);
     const bool vec = (d.n % 4) == 0;
-    if (vec) k_corr_f32<true><<<grid, 256, 0, s>>>(d, cur);
-    else k_corr_f32<false><<<grid, 256, 0, s>>>(d, cur);
+    const cudaError_t e = vec ? launch_chain(k_corr_f32<true>, grid, dim3(256), 0, s, d, cur)
+                              : launch_chain(k_corr_f32<false>, grid, dim3(256), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }

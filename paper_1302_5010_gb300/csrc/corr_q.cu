@@ -23,6 +23,7 @@ namespace {
 constexpr int QT = 256;  // threads per block; each thread scores 4 consecutive atoms
 
 __global__ void __launch_bounds__(QT) k_corr_q(Dev d, int cur) {
+    pdl_enter();
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(QT) k_corr_q(Dev d, int cur) {
 
 // beta_i <- score row of signal i (the iteration's residual is b_i).
 __global__ void k_save_beta(Dev d, int cur) {
+    pdl_enter();
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
@@ -118,6 +120,7 @@ __global__ void k_gram_q_prep(Counters* cnt, int* act, int m) {
 constexpr int GQ_BUF = 10240;  // floats of the staging buffer for the h chains
 
 __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
+    pdl_enter();
     const int g = blockIdx.x;
     if (g >= d.cnt->grow_n) return;
     const int i = d.list_grow[g];
@@ -130,13 +133,28 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     __shared__ __align__(16) float hbuf[GQ_BUF];
     for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
     __syncthreads();
-    // new columns (and, by symmetry, rows) of G_SS: independent loads, all in flight
+    // new columns (and, by symmetry, rows) of G_SS: eight independent loads per thread
+    // in flight before their stores (the stores could alias them as far as the compiler knows)
     const int total = s * q;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int a = e / q, c = e - a * q;
-        const float v = __ldg(d.Q + (size_t)sidx[a] * m + sidx[s0 + c]);
-        Gi[(size_t)a * smax + s0 + c] = v;
-        Gi[(size_t)(s0 + c) * smax + a] = v;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < total) {
+                const int a = e / q, c = e - a * q;
+                v[u] = __ldg(d.Q + (size_t)sidx[a] * m + sidx[s0 + c]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < total) {
+                const int a = e / q, c = e - a * q;
+                Gi[(size_t)a * smax + s0 + c] = v[u];
+                Gi[(size_t)(s0 + c) * smax + a] = v[u];
+            }
+        }
     }
     // h of the new atoms, one FMA chain per atom (thread), over k ascending.  The
     // atoms' columns and b pass through shared memory kc entries at a time (coalesced
@@ -193,7 +211,8 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
 
 cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
-    k_gram_gather<<<ub, 256, 0, s>>>(d);
+    const cudaError_t e = launch_chain(k_gram_gather, dim3(ub), dim3(256), 0, s, d);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
@@ -201,14 +220,16 @@ cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl
 cudaError_t launch_corr_q(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
     dim3 grid(act_n_ub, (d.m + 4 * QT - 1) / (4 * QT));
-    k_corr_q<<<grid, QT, 0, s>>>(d, cur);
+    const cudaError_t e = launch_chain(k_corr_q, grid, dim3(QT), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_save_beta(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
-    k_save_beta<<<act_n_ub, 256, 0, s>>>(d, cur);
+    const cudaError_t e = launch_chain(k_save_beta, dim3(act_n_ub), dim3(256), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }

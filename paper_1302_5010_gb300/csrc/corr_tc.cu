@@ -139,6 +139,7 @@ struct TcSmem {
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_corr_bf16(Dev d, int cur, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmR) {
+    pdl_enter();
     using L = TcSmem<BN, STAGES>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -331,7 +332,9 @@ cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(tmap);
     const int tiles = ((d.m + TC_BM - 1) / TC_BM) * ((act_n_ub + TC_BN - 1) / TC_BN);
     const int grid = tiles < sms ? tiles : sms;
-    k_corr_bf16<TC_BN, TC_STAGES><<<grid, TC_THREADS, L::TOTAL, s>>>(d, cur, maps[0], maps[1]);
+    const cudaError_t e = launch_chain(k_corr_bf16<TC_BN, TC_STAGES>, dim3(grid), dim3(TC_THREADS), (size_t)L::TOTAL, s, d,
+                                       cur, maps[0], maps[1]);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }

@@ -8,6 +8,40 @@
 
 namespace mpl {
 
+// Programmatic dependent launch for the kernels of the outer-iteration chain: each is
+// launched with the programmatic-serialisation attribute, so that its launch is set up
+// while its predecessor on the stream drains (the predecessor's CTAs trigger it as they
+// exit), and it waits (griddepcontrol.wait: the predecessor grid complete, its writes
+// visible) before touching anything.  Launched without the attribute (or after a
+// non-kernel node) the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+#if !defined(MPL_NO_PDL)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#if defined(MPL_PDL_EARLY)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+#endif
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_chain(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t c{};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+#if defined(MPL_NO_PDL)
+    at[0].val.programmaticStreamSerializationAllowed = 0;
+#else
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+#endif
+    c.attrs = at;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, k, static_cast<P>(args)...);
+}
+
 // Per-signal phase decided by the selection kernel each outer iteration.
 enum SigState : int {
     ST_GROW = 1,      // new atoms were appended: Gram growth, master problem, residual

@@ -904,12 +904,16 @@ __device__ void compact_body(const Dev& d, int cur) {
     }
 }
 
-__global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) { compact_body(d, cur); }
+__global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
+    pdl_enter();
+    compact_body(d, cur);
+}
 
 // The selection of one outer iteration; with fuse set, the last CTA to finish
 // (counted with a fenced atomic) also runs the compaction, saving a launch.
 __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa, int route,
                                                            int fuse) {
+    pdl_enter();
     select_body(d, cur, no_grow, pa, route);
     if (!fuse) return;
     __shared__ int last;
@@ -957,13 +961,15 @@ cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cuda
     const size_t sm = sizeof(SelSmem) + (a.mode != SEL_NORMAL ? PROP_NPARAM * sizeof(float) : 0);
     cudaError_t e = prepare_select();
     if (e != cudaSuccess) return e;
-    k_select<<<act_n_ub, SEL_THREADS, sm, s>>>(d, cur, no_grow, a, route, fuse_compact);
+    e = launch_chain(k_select, dim3(act_n_ub), dim3(SEL_THREADS), sm, s, d, cur, no_grow, a, route, fuse_compact);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl) {
-    k_compact<<<1, 1024, 0, s>>>(d, cur);
+    const cudaError_t e = launch_chain(k_compact, dim3(1), dim3(1024), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }

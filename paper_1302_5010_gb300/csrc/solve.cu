@@ -60,6 +60,7 @@ __device__ __forceinline__ float softf(float v, float t) {
 
 // ------------------------------------------------------------------ init
 __global__ void __launch_bounds__(256) k_init(Dev d) {
+    pdl_enter();
     const int i = blockIdx.x;
     if (i >= d.p) return;
     __shared__ double red[32];
@@ -150,6 +151,7 @@ __device__ __forceinline__ float4 gram_load(const float* row, int k, int n) {
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_gram(Dev d) {
+    pdl_enter();
     const int g = blockIdx.x;
     if (g >= d.cnt->grow_n) return;
     const int i = d.list_grow[g];
@@ -238,6 +240,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <int BM, int BN, int TR, int TC>
 __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
+    pdl_enter();
     static_assert((BM / TR) * (BN / TC) == 256, "one output block per thread");
     constexpr int NX = BN / TC;                  // threads along the columns
     constexpr int CHUNKS = (BM + BN) * (GBK / 4);  // 16-byte chunks per slice
@@ -437,6 +440,7 @@ __device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* 
 }
 
 __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) {
+    pdl_enter();
     extern __shared__ __align__(16) float gsm[];
     __shared__ ApgVec sh;
     const int tid = threadIdx.x;
@@ -654,6 +658,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
 
 // ------------------------------------------------------------------ residual
 __global__ void __launch_bounds__(256) k_residual(Dev d) {
+    pdl_enter();
     const int g = blockIdx.x;
     if (g >= d.cnt->apg_n) return;
     const int i = d.list_apg[g];
@@ -768,6 +773,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
 // Gram block are compacted with the order of the remaining entries kept; the
 // signal's FP64 factor workspace (idle while it grows) stages the Gram block.
 __global__ void __launch_bounds__(256) k_smpl_prune(Dev d) {
+    pdl_enter();
     const int g = blockIdx.x;
     if (g >= d.cnt->grow_n) return;
     const int i = d.list_grow[g];
@@ -858,6 +864,7 @@ __global__ void __launch_bounds__(256) k_smpl_prune(Dev d) {
 
 // ------------------------------------------------------------------ output
 __global__ void k_scatter(Dev d, float* X, double* X64) {
+    pdl_enter();
     const int i = blockIdx.x;
     if (i >= d.p) return;
     const int s = d.ssize[i];
@@ -920,6 +927,7 @@ __global__ void k_max_reduce(const float* v, int len, float* out) {
 }
 
 __global__ void k_gather_r16(Dev d, int cur) {
+    pdl_enter();
     const int k = blockIdx.x;
     if (k >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][k];
@@ -956,7 +964,8 @@ cudaError_t launch_prep_correlate(const Dev& d, const float* R, cudaStream_t s, 
 
 cudaError_t launch_init(const Dev& d, cudaStream_t s, int64_t* nl) {
     if (d.p <= 0) return cudaSuccess;
-    k_init<<<d.p, 256, 0, s>>>(d);
+    const cudaError_t e = launch_chain(k_init, dim3(d.p), dim3(256), 0, s, d);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
@@ -980,17 +989,19 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
         if (ep != cudaSuccess) return ep;
         if (qmax + 1 <= 16) {  // the new atoms and b fit one 16-column tile
             dim3 grid(ub, (d.smax + 31) / 32);
-            k_gram_async<32, 16, 1, 2><<<grid, 256, gram_smem<32, 16>(), s>>>(d);
+            ep = launch_chain(k_gram_async<32, 16, 1, 2>, grid, dim3(256), gram_smem<32, 16>(), s, d);
         } else if (qmax + 1 <= 64) {  // one 64-column pass (e.g. a warm start's first iteration)
             dim3 grid(ub, (d.smax + 63) / 64);
-            k_gram_async<64, 64, 4, 4><<<grid, 256, gram_smem<64, 64>(), s>>>(d);
+            ep = launch_chain(k_gram_async<64, 64, 4, 4>, grid, dim3(256), gram_smem<64, 64>(), s, d);
         } else {
             dim3 grid(ub, (d.smax + 63) / 64);
-            k_gram_async<64, 32, 2, 4><<<grid, 256, gram_smem<64, 32>(), s>>>(d);
+            ep = launch_chain(k_gram_async<64, 32, 2, 4>, grid, dim3(256), gram_smem<64, 32>(), s, d);
         }
+        if (ep != cudaSuccess) return ep;
     } else {
         dim3 grid(ub, (d.smax + GBM - 1) / GBM);
-        k_gram<false><<<grid, 256, 0, s>>>(d);
+        const cudaError_t eg = launch_chain(k_gram<false>, grid, dim3(256), 0, s, d);
+        if (eg != cudaSuccess) return eg;
     }
     ++*nl;
     return cudaGetLastError();
@@ -1031,20 +1042,23 @@ cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, 
     if (e != cudaSuccess) return e;
     int grid = sms * (per_sm > 0 ? per_sm : 1);
     if (grid > ub) grid = ub;
-    k_apg<<<grid, APG_THREADS, dyn, s>>>(d, vcap, gcap);
+    e = launch_chain(k_apg, dim3(grid), dim3(APG_THREADS), dyn, s, d, vcap, gcap);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
-    k_residual<<<ub, 256, 0, s>>>(d);
+    const cudaError_t e = launch_chain(k_residual, dim3(ub), dim3(256), 0, s, d);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 // Per-signal statistics packed on the device into the host struct layout (one copy back).
 __global__ void k_pack_stats(Dev d, mpl_signal_stats_t* out) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.p) return;
     mpl_signal_stats_t s;
@@ -1067,21 +1081,24 @@ __global__ void k_pack_stats(Dev d, mpl_signal_stats_t* out) {
 
 cudaError_t launch_pack_stats(const Dev& d, mpl_signal_stats_t* out, cudaStream_t s, int64_t* nl) {
     if (d.p <= 0) return cudaSuccess;
-    k_pack_stats<<<(d.p + 127) / 128, 128, 0, s>>>(d, out);
+    const cudaError_t e = launch_chain(k_pack_stats, dim3((d.p + 127) / 128), dim3(128), 0, s, d, out);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
-    k_smpl_prune<<<ub, 256, 0, s>>>(d);
+    const cudaError_t e = launch_chain(k_smpl_prune, dim3(ub), dim3(256), 0, s, d);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Dev& d, float* X, double* X64, cudaStream_t s, int64_t* nl) {
     if (d.p <= 0) return cudaSuccess;
-    k_scatter<<<d.p, 128, 0, s>>>(d, X, X64);
+    const cudaError_t e = launch_chain(k_scatter, dim3(d.p), dim3(128), 0, s, d, X, X64);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
@@ -1102,7 +1119,8 @@ cudaError_t launch_max_reduce(const float* v, int len, float* out, cudaStream_t 
 
 cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
-    k_gather_r16<<<act_n_ub, 128, 0, s>>>(d, cur);
+    const cudaError_t e = launch_chain(k_gather_r16, dim3(act_n_ub), dim3(128), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }
