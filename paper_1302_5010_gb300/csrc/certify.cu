@@ -294,16 +294,29 @@ __device__ void solve_warp_reg(const T* M, int ld, int np, const T* rdiag, T* v)
 // block with the right-hand side in registers, then all threads apply the block to
 // the remaining unknowns (rows of L below it going forward, its columns going back).
 template <typename T>
-__device__ void solve_cta(const T* M, int ld, int np, const T* rdiag, T* v) {
+__device__ void fwd_cta(const T* M, int ld, int np, const T* rdiag, T* v, T* scr = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     for (int b0 = 0; b0 < np; b0 += 32) {  // forward: L y = v
         const int bw = min(32, np - b0);
+        // the diagonal block: from M, or (a factor in global memory) from a shared-memory
+        // copy, so that warp 0's dependent chain waits on shared memory, not on L2
+        const T* D = M + (size_t)b0 * ld + b0;
+        int dld = ld;
+        if (scr) {
+            for (int e = tid; e < bw * bw; e += nt) {
+                const int r = e / bw, c = e - r * bw;
+                if (c < r) scr[r * 33 + c] = D[(size_t)r * ld + c];
+            }
+            __syncthreads();
+            D = scr;
+            dld = 33;
+        }
         if (tid < 32) {
             T y = lane < bw ? v[b0 + lane] : T(0);
             for (int j = 0; j < bw; ++j) {
                 const T yj = __shfl_sync(0xffffffffu, y, j) * rdiag[b0 + j];
                 if (lane == j) y = yj;
-                if (lane > j && lane < bw) y -= M[(size_t)(b0 + lane) * ld + b0 + j] * yj;
+                if (lane > j && lane < bw) y -= D[(size_t)lane * dld + j] * yj;
             }
             if (lane < bw) v[b0 + lane] = y;
         }
@@ -311,25 +324,46 @@ __device__ void solve_cta(const T* M, int ld, int np, const T* rdiag, T* v) {
         for (int r = b0 + bw + tid; r < np; r += nt) {
             const T* Lr = M + (size_t)r * ld + b0;
             T acc = T(0);
+#pragma unroll 8
             for (int c = 0; c < bw; ++c) acc += Lr[c] * v[b0 + c];
             v[r] -= acc;
         }
         __syncthreads();
     }
+}
+
+// scr: null, or 32 x 33 elements of shared memory for the diagonal blocks (worth it
+// when M is in global memory).
+template <typename T>
+__device__ void solve_cta(const T* M, int ld, int np, const T* rdiag, T* v, T* scr = nullptr) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    fwd_cta(M, ld, np, rdiag, v, scr);
     for (int b1 = np; b1 > 0; b1 -= 32) {  // backward: L^T x = y
         const int b0 = max(0, b1 - 32), bw = b1 - b0;
+        const T* D = M + (size_t)b0 * ld + b0;
+        int dld = ld;
+        if (scr) {
+            for (int e = tid; e < bw * bw; e += nt) {
+                const int r = e / bw, c = e - r * bw;
+                if (c < r) scr[r * 33 + c] = D[(size_t)r * ld + c];
+            }
+            __syncthreads();
+            D = scr;
+            dld = 33;
+        }
         if (tid < 32) {
             T y = lane < bw ? v[b0 + lane] : T(0);
             for (int j = bw - 1; j >= 0; --j) {
                 const T xj = __shfl_sync(0xffffffffu, y, j) * rdiag[b0 + j];
                 if (lane == j) y = xj;
-                if (lane < j) y -= M[(size_t)(b0 + j) * ld + b0 + lane] * xj;
+                if (lane < j) y -= D[(size_t)j * dld + lane] * xj;
             }
             if (lane < bw) v[b0 + lane] = y;
         }
         __syncthreads();
         for (int r = tid; r < b0; r += nt) {
             T acc = T(0);
+#pragma unroll 8
             for (int c = 0; c < bw; ++c) acc += M[(size_t)(b0 + c) * ld + r] * v[b0 + c];
             v[r] -= acc;
         }
@@ -361,6 +395,7 @@ struct Factor {
     double* rdd;     // reciprocal diagonal for the FP64 factor
     float* vf;       // FP32 right-hand side scratch
     float* stage;    // panel staging (np x FAC_PANEL_GLOBAL) for an FP32 factor in global memory, else null
+    int stage_n;     // floats at stage
     int ldf, ldd;
     int fp64;        // which factor is current
 };
@@ -379,7 +414,8 @@ __device__ void fsolve(const Factor& F, int np, double* v) {
         for (int a = threadIdx.x; a < np; a += blockDim.x) F.vf[a] = (float)v[a];
         __syncthreads();
         if (np > 64) {
-            solve_cta(F.Mf, F.ldf, np, F.rdf, F.vf);
+            // the staging area is free outside factorisations: the diagonal blocks go there
+            solve_cta(F.Mf, F.ldf, np, F.rdf, F.vf, F.stage_n >= 32 * 33 ? F.stage : nullptr);
         } else {
             if (threadIdx.x < 32) solve_warp_reg(F.Mf, F.ldf, np, F.rdf, F.vf);
             __syncthreads();
@@ -407,6 +443,7 @@ struct FinShared {
     double dval[4];
     int fac_np;  // rows of the FP32 factor that match P in its order (-1: rebuild next step)
     float cs[2]; // rotation of the factor update
+    float rot[2][2];  // rotations of the CTA-wide update, alternating slots
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -427,7 +464,8 @@ __device__ int build_support(int s, FinShared& sh) {
 }
 
 // Incremental changes of the FP32 factor of G_PP when the support loses or
-// gains one atom, instead of refactoring (up to FAC_INC_MAX atoms).
+// gains one atom, instead of refactoring: by warp 0 up to FAC_INC_MAX atoms, by the
+// whole CTA above that.
 constexpr int FAC_INC_MAX = 64;
 
 // Drop factor row/column k: the trailing factor absorbs the dropped column by a
@@ -527,6 +565,139 @@ __device__ __noinline__ int fac_append(FinShared& sh, const float* Gi, int smax,
     return sh.ival[0] ? -1 : 0;
 }
 
+// Drop factor row/column k of a factor of any size (np <= 4 blockDim.x + 1), by the
+// CTA.  The trailing factor absorbs the dropped column by the same rank-one update as
+// fac_remove: thread t owns trailing rows k + 1 + t + q nt (q < 4) and keeps their
+// entries of the dropped column in registers.  Rotation j (row J = k + 1 + j) is
+// worked out by the owner of row J from its own entries, so one barrier per rotation
+// suffices (two slots alternate); the entries of column J + 1, which rotation j does
+// not touch, are loaded while it runs.  Then rows below k move up by one row and,
+// right of column k, one column left, a few rows at a time (every source read before
+// the barrier that precedes the writes of its chunk, and a destination is never a
+// source of a later chunk); P and the reciprocal diagonal follow.
+__device__ __noinline__ void fac_remove_cta(FinShared& sh, int k, int np) {
+    constexpr int RQ = 4;
+    float* M = sh.F.Mf;
+    const int ld = sh.F.ldf;
+    const int m = np - k - 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float x[RQ], nx[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = tid + q * nt;
+        x[q] = i < m ? M[(size_t)(k + 1 + i) * ld + k] : 0.f;
+        nx[q] = i < m ? M[(size_t)(k + 1 + i) * ld + k + 1] : 0.f;  // column J of rotation 0
+    }
+    for (int j = 0; j < m; ++j) {
+        const int J = k + 1 + j;
+        float cur[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            cur[q] = nx[q];
+            const int i = tid + q * nt;
+            nx[q] = (i > j && i < m) ? M[(size_t)(k + 1 + i) * ld + J + 1] : 0.f;  // i > j: j + 1 < m
+        }
+        if (tid == j % nt) {
+            const int qo = j / nt;
+            float ljj = 0.f, xj = 0.f;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q)
+                if (q == qo) { ljj = cur[q]; xj = x[q]; }
+            const float r = sqrtf(ljj * ljj + xj * xj);
+            sh.rot[j & 1][0] = r / ljj;
+            sh.rot[j & 1][1] = xj / ljj;
+            M[(size_t)J * ld + J] = r;
+            sh.F.rdf[J] = 1.f / r;
+        }
+        __syncthreads();
+        const float c = sh.rot[j & 1][0], sn = sh.rot[j & 1][1];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const int i = tid + q * nt;
+            if (i > j && i < m) {
+                const float ln = (cur[q] + sn * x[q]) / c;
+                M[(size_t)(k + 1 + i) * ld + J] = ln;
+                x[q] = c * x[q] - sn * ln;
+            }
+        }
+    }
+    __syncthreads();
+    // rows k + 1 .. np - 1 up by one; their columns right of k left by one
+    const int rows = max(1, (8 * nt) / np);
+    for (int r0 = k + 1; r0 < np; r0 += rows) {
+        const int r1 = min(np, r0 + rows);
+        const int tot = (r1 - r0) * np;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * nt;
+            v[u] = 0.f;
+            if (e < tot) {
+                const int r = r0 + e / np, c = e % np;  // destination column c of row r - 1
+                if (c < r) v[u] = M[(size_t)r * ld + (c < k ? c : c + 1)];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = tid + u * nt;
+            if (e < tot) {
+                const int r = r0 + e / np, c = e % np;
+                if (c < r) M[(size_t)(r - 1) * ld + c] = v[u];
+            }
+        }
+        __syncthreads();
+    }
+    float rd[RQ];
+    int pr[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = k + tid + q * nt;
+        if (i < np - 1) { rd[q] = sh.F.rdf[i + 1]; pr[q] = sh.P[i + 1]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = k + tid + q * nt;
+        if (i < np - 1) { sh.F.rdf[i] = rd[q]; sh.P[i] = pr[q]; }
+    }
+    __syncthreads();
+}
+
+// Append the support atom at position a as row np of a factor of any size, by the
+// CTA: the forward sweep L y = G_Pa in the FP32 scratch vector, l_nn = sqrt(G_aa -
+// y^T y).  Returns 0, or -1 when the new pivot is not positive (the caller refactors).
+__device__ __noinline__ int fac_append_cta(FinShared& sh, const float* Gi, int smax, int a, int np) {
+    float* M = sh.F.Mf;
+    const int ld = sh.F.ldf;
+    float* v = sh.F.vf;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int r = tid; r < np; r += nt) v[r] = Gi[(size_t)sh.P[r] * smax + a];
+    __syncthreads();
+    fwd_cta(M, ld, np, sh.F.rdf, v, sh.F.stage_n >= 32 * 33 ? sh.F.stage : nullptr);
+    double ss = 0.0;
+    for (int r = tid; r < np; r += nt) ss += (double)v[r] * (double)v[r];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) sh.red[warp] = ss;
+    __syncthreads();
+    double tot = 0.0;
+    for (int q = 0; q < nw; ++q) tot += sh.red[q];
+    const float dnn = (float)((double)Gi[(size_t)a * smax + a] - tot);
+    const bool ok = dnn > 0.f;
+    if (ok) {
+        for (int r = tid; r < np; r += nt) M[(size_t)np * ld + r] = v[r];
+        if (tid == 0) {
+            const float dg = sqrtf(dnn);
+            M[(size_t)np * ld + np] = dg;
+            sh.F.rdf[np] = 1.f / dg;
+            sh.P[np] = a;
+        }
+    }
+    __syncthreads();
+    return ok ? 0 : -1;
+}
+
 // After atoms of P were zeroed (sign 0): drop them from the FP32 factor, last
 // first, or leave the factor to be rebuilt.
 __device__ void drop_zeroed(FinShared& sh, int np) {
@@ -537,8 +708,12 @@ __device__ void drop_zeroed(FinShared& sh, int np) {
         return;
     }
     int cur = np;
-    for (int a = np - 1; a >= 0; --a)
-        if (sh.sg[sh.P[a]] == 0) fac_remove(sh, a, cur--);
+    for (int a = np - 1; a >= 0; --a) {
+        if (sh.sg[sh.P[a]] != 0) continue;
+        if (cur <= FAC_INC_MAX) fac_remove(sh, a, cur);
+        else fac_remove_cta(sh, a, cur);
+        --cur;
+    }
     __syncthreads();
     if (threadIdx.x == 0) sh.fac_np = cur;
     __syncthreads();
@@ -547,9 +722,9 @@ __device__ void drop_zeroed(FinShared& sh, int np) {
 // The atom at position a joins P: append it to the FP32 factor, or leave the
 // factor to be rebuilt.
 __device__ void join_support(FinShared& sh, const float* Gi, int smax, int a, int np) {
-    const bool ok = sh.fac_np >= 0 && !sh.F.fp64 && np < FAC_INC_MAX;
+    const bool ok = sh.fac_np >= 0 && !sh.F.fp64;
     __syncthreads();
-    const int res = ok ? fac_append(sh, Gi, smax, a, np) : -1;
+    const int res = !ok ? -1 : (np < FAC_INC_MAX ? fac_append(sh, Gi, smax, a, np) : fac_append_cta(sh, Gi, smax, a, np));
     if (threadIdx.x == 0) sh.fac_np = res == 0 ? np + 1 : -1;
     __syncthreads();
 }
@@ -839,6 +1014,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         sh.F.Mf = fsm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
         if (msm) q += (size_t)msm * ((msm + 1) | 1);
         sh.F.stage = msm ? nullptr : q;  // panel staging for a factor in global memory
+        sh.F.stage_n = msm ? 0 : FAC_PANEL_GLOBAL * scap;
         if (!msm) q += (size_t)FAC_PANEL_GLOBAL * scap;
         sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
@@ -915,7 +1091,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
             fsolve(sh.F, np, sh.z);
             FT_ADD(1);
         }
-        if (tid == 0) sh.fac_np = (!sh.F.fp64 && np <= FAC_INC_MAX) ? np : -1;
+        if (tid == 0) sh.fac_np = !sh.F.fp64 ? np : -1;
         __syncthreads();
         // ---- first sign crossing on the segment x -> z.  Skipped right after the
         // exact check admitted an atom: its coefficient may be below the FP32
