@@ -386,7 +386,131 @@ __device__ void solve_block(const T* M, int ld, int np, const T* rdiag, T* v) {
 // FP32-accurate; refinement with exact residuals recovers full accuracy), or
 // FP64 in the global workspace when FP32 refinement stagnates.  Every thread
 // of the CTA returns the same result.
-constexpr int FAC_PANEL_GLOBAL = 8;   // panel width of a factor in global memory
+constexpr int FAC_TILE_W = 16;  // panel width of the tiled factorisation (factor in global memory)
+
+// Floats of shared-memory staging for a global-memory factor of up to scap rows: the
+// panel (FAC_TILE_W x scap rounded up to the 64-row tiles), its diagonal block, slack.
+__host__ __device__ inline int fac_stage_floats(int scap) {
+    return FAC_TILE_W * ((scap + 63) / 64) * 64 + FAC_TILE_W * (FAC_TILE_W + 1) + 16;
+}
+
+// Blocked right-looking Cholesky of a factor in global memory, by the CTA, panels of
+// W = FAC_TILE_W columns.  Per panel: the W x W diagonal block is factored by warp 0
+// in shared memory; each thread takes panel rows below it (forward substitution
+// against the block, W values in registers) and writes them to M and, k-major, to the
+// shared staging area; then the trailing lower triangle gets the rank-W update in
+// 64 x 64 tiles, each thread a 4 x 4 register block fed by float4 reads of the staged
+// panel, with the tile's 16 global values loaded before the products.  Per element the
+// trailing triangle is read and written once per W columns (np^3 / (3W) touches in
+// all) instead of once per 4 or 8.  stage: fac_stage_floats(rows) floats, 16-byte
+// aligned.  Returns 0 or -1 (non-positive pivot); flag likewise.
+static_assert(FIN_THREADS == 256, "chol_tiled maps 256 threads onto 16 x 16 blocks of a 64 x 64 tile");
+__device__ __noinline__ int chol_tiled(float* M, int ld, int np, float* rdiag, int* flag, float* stage) {
+    constexpr int W = FAC_TILE_W, DS = W + 1;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    float* D = stage;                 // W x W diagonal block, stride DS
+    // k-major panel PT[k * PS + (r - j1)], 16-byte aligned for the float4 reads
+    float* PT = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(stage + W * DS) + 15) & ~(uintptr_t)15);
+    const int ty = tid >> 4, tx = tid & 15;   // 16 x 16 threads of 4 x 4 blocks (nt = 256)
+    for (int j0 = 0; j0 < np; j0 += W) {
+        const int w = min(W, np - j0), j1 = j0 + w, nr = np - j1;
+        const int PS = ((nr + 63) / 64) * 64;
+        for (int e = tid; e < w * w; e += nt) {
+            const int r = e / w, c = e - r * w;
+            if (c <= r) D[r * DS + c] = M[(size_t)(j0 + r) * ld + j0 + c];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int bad = 0;
+            for (int k = 0; k < w; ++k) {
+                const float dkk = D[k * DS + k];
+                if (!(dkk > 0.f)) { bad = 1; break; }  // the same value on every lane
+                const float dg = sqrtf(dkk), inv = 1.f / dg;
+                __syncwarp();
+                if (lane == k) { D[k * DS + k] = dg; rdiag[j0 + k] = inv; }
+                if (lane > k && lane < w) D[lane * DS + k] *= inv;
+                __syncwarp();
+                if (lane > k && lane < w) {
+                    const float lk = D[lane * DS + k];
+                    for (int c = k + 1; c <= lane; ++c) D[lane * DS + c] -= lk * D[c * DS + k];
+                }
+                __syncwarp();
+            }
+            if (lane == 0) *flag = bad;
+        }
+        __syncthreads();
+        if (*flag) return -1;
+        for (int e = tid; e < w * w; e += nt) {
+            const int r = e / w, c = e - r * w;
+            if (c <= r) M[(size_t)(j0 + r) * ld + j0 + c] = D[r * DS + c];
+        }
+        // panel rows below the block
+        for (int r = j1 + tid; r < np; r += nt) {
+            float* Rr = M + (size_t)r * ld + j0;
+            float l[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) l[k] = k < w ? Rr[k] : 0.f;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (k < w) {
+                    float v = l[k];
+#pragma unroll
+                    for (int q = 0; q < k; ++q) v -= l[q] * D[k * DS + q];
+                    l[k] = v * rdiag[j0 + k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (k < w) {
+                    Rr[k] = l[k];
+                    PT[k * PS + (r - j1)] = l[k];
+                }
+            }
+        }
+        __syncthreads();
+        // trailing triangle: 64 x 64 tiles (ti >= tj), element (r, c) with c <= r
+        const int T = (nr + 63) / 64;
+        for (int t = 0; t < T * (T + 1) / 2; ++t) {
+            int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while (ti * (ti + 1) / 2 > t) --ti;
+            const int tj = t - ti * (ti + 1) / 2;
+            const int rr0 = ti * 64 + ty * 4, cc0 = tj * 64 + tx * 4;  // offsets from j1
+            float a[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = rr0 + u, c = cc0 + v;
+                    a[u][v] = (r < nr && c <= r) ? M[(size_t)(j1 + r) * ld + j1 + c] : 0.f;
+                }
+            float acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+            for (int k = 0; k < w; ++k) {
+                const float4 x = *reinterpret_cast<const float4*>(PT + k * PS + rr0);
+                const float4 y = *reinterpret_cast<const float4*>(PT + k * PS + cc0);
+                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xs[u], ys[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = rr0 + u, c = cc0 + v;
+                    if (r < nr && c <= r) M[(size_t)(j1 + r) * ld + j1 + c] = a[u][v] - acc[u][v];
+                }
+        }
+        __syncthreads();
+    }
+    return 0;
+}
+
 
 struct Factor {
     float* Mf;       // FP32 factor, leading dimension ldf
@@ -394,7 +518,7 @@ struct Factor {
     double* Md;      // FP64 factor (global workspace), leading dimension ldd
     double* rdd;     // reciprocal diagonal for the FP64 factor
     float* vf;       // FP32 right-hand side scratch
-    float* stage;    // panel staging (np x FAC_PANEL_GLOBAL) for an FP32 factor in global memory, else null
+    float* stage;    // staging (fac_stage_floats) for an FP32 factor in global memory, else null
     int stage_n;     // floats at stage
     int ldf, ldd;
     int fp64;        // which factor is current
@@ -402,7 +526,7 @@ struct Factor {
 
 __device__ int factor(Factor& F, int np, int* flag) {
     if (!F.fp64) {
-        if (F.stage) return chol_panel<float, FAC_PANEL_GLOBAL>(F.Mf, F.ldf, np, F.rdf, flag, F.stage);
+        if (F.stage) return chol_tiled(F.Mf, F.ldf, np, F.rdf, flag, F.stage);
         return chol_panel<float, 4>(F.Mf, F.ldf, np, F.rdf, flag);
     }
     return chol_panel<double, 4>(F.Md, F.ldd, np, F.rdd, flag);
@@ -1014,8 +1138,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         sh.F.Mf = fsm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
         if (msm) q += (size_t)msm * ((msm + 1) | 1);
         sh.F.stage = msm ? nullptr : q;  // panel staging for a factor in global memory
-        sh.F.stage_n = msm ? 0 : FAC_PANEL_GLOBAL * scap;
-        if (!msm) q += (size_t)FAC_PANEL_GLOBAL * scap;
+        sh.F.stage_n = msm ? 0 : fac_stage_floats(scap);
+        if (!msm) q += (size_t)fac_stage_floats(scap);
         sh.P = reinterpret_cast<int*>(q);
         sh.sg = sh.P + scap;
         sh.Pi = sh.sg + scap;
@@ -1415,7 +1539,7 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     // shared-memory factor area: the whole bound while two CTAs still fit on an SM
     auto dyn_of = [&](int mf, int rs) {
         return 4 * (size_t)scap * sizeof(double) +
-               (2 * (size_t)scap + (mf ? (size_t)mf * ((mf + 1) | 1) : (size_t)FAC_PANEL_GLOBAL * scap)) * sizeof(float) +
+               (2 * (size_t)scap + (mf ? (size_t)mf * ((mf + 1) | 1) : (size_t)fac_stage_floats(scap))) * sizeof(float) +
                4 * (size_t)scap * sizeof(int) + (rs ? 2 * (size_t)d.n * sizeof(float) : 0);
     };
     const int rsm = d.n <= 4096 ? 1 : 0;
