@@ -1145,7 +1145,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
         sh.Pi = sh.sg + scap;
         sh.adds = sh.Pi + scap;
         // residual pair in shared memory when it fits (rsm), else in the global R32 / R32lo rows
-        float* rbase = reinterpret_cast<float*>(sh.adds + scap);
+        // (16-byte aligned: the residual rows are read and written as float4)
+        float* rbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sh.adds + scap) + 15) & ~(uintptr_t)15);
         sh.rh = rsm ? rbase : d.R32 + (size_t)i * d.n;
         sh.rl = rsm ? rbase + d.n : d.R32lo + (size_t)i * d.n;
         sh.F.Md = d.chol + (size_t)i * smax * smax;  // shares the workspace with a global FP32 factor
@@ -1540,7 +1541,7 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     auto dyn_of = [&](int mf, int rs) {
         return 4 * (size_t)scap * sizeof(double) +
                (2 * (size_t)scap + (mf ? (size_t)mf * ((mf + 1) | 1) : (size_t)fac_stage_floats(scap))) * sizeof(float) +
-               4 * (size_t)scap * sizeof(int) + (rs ? 2 * (size_t)d.n * sizeof(float) : 0);
+               4 * (size_t)scap * sizeof(int) + (rs ? 2 * (size_t)d.n * sizeof(float) + 16 : 0);
     };
     const int rsm = d.n <= 4096 ? 1 : 0;
     // (one CTA per SM with a larger area loses more to the halved concurrency than the

@@ -47,3 +47,20 @@ def test_large_dictionary_mixed_equals_plain(cfg, p, smax):
     assert_certified(rm)
     np.testing.assert_array_equal(rp.stats["outer_iters"], rm.stats["outer_iters"])
     np.testing.assert_array_equal(Xp, Xm)
+
+
+@pytest.mark.parametrize("cfg,p,smax,precision", [("c2", 8, 75, 0), ("c2", 8, 75, 1), ("c5", 16, 198, 1)])
+def test_active_set_capacity_not_a_multiple_of_four(cfg, p, smax, precision):
+    """The finish's shared-memory layout (factor or its staging, lists, then the residual
+    rows read as float4) with a capacity that is no multiple of 4 or 32: 75 keeps the
+    factor in shared memory, 198 on the 2048-row dictionary puts it in global memory."""
+    P = synth.make_config(cfg, p=p)
+    X, X64, res = solve_gpu(P, precision=precision, smax=smax)
+    st = res.stats
+    ok = st["status"] == 0
+    # signals whose support outgrows the capacity stop with MPL_SIG_CAPACITY; the rest
+    # are certified and equal the oracle's solution
+    assert np.all(ok | (st["status"] == 2))
+    assert ok.sum() >= 2
+    idx = np.flatnonzero(ok)
+    check_against_oracle(P, X64[idx], oracle_solve(P, idx), idx)
