@@ -368,6 +368,50 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
             "active_size_mean": float(np.mean(stats["active_size"]))}
 
 
+def omp_compare(args):
+    """lambda = 0 (least squares on the growing support, the reduction to orthogonal matching
+    pursuit in Sec. 2.5) on the shape of the paper's Sec. 5.1 batch comparison: A 4096 x 16384
+    Gaussian, k ~ U[400, 600], sigma = 1e-3, every signal stopped by ||xi|| <= r_2 (eq. stop1)
+    at 1.5 sigma sqrt(n).  rho = 1 is batch OMP (one atom per worst-case analysis, the Gram
+    block read from Q = A^T A); the multi-atom rows add rho atoms per analysis as Algorithm 1
+    does.  One JSON line per run (warm-up solve, then one event-timed solve)."""
+    import torch
+    from paper_1302_5010_gb300 import mpl, synth
+    P = synth.small_problem(4096, 16384, args.omp_compare, 400, 600, rho=1, lam_frac=0.0, sigma=1e-3, seed=51)
+    r2 = 1.5 * 1e-3 * np.sqrt(P.n)
+    dev = torch.device("cuda", 0)
+    At = torch.from_numpy(P.At).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    lam = torch.zeros(P.p, dtype=torch.float32, device=dev)
+    Xt = P.X_true.astype(np.float64)
+    supp_true = [set(np.flatnonzero(Xt[i]).tolist()) for i in range(P.p)]
+    for rho in (1, 25, 50, 100):
+        s = mpl.Solver(At, rho=rho, precision=1, smax=1024, stop_r2=r2, qgram=1, max_outer=1024)
+        X = torch.empty((P.p, P.m), dtype=torch.float32, device=dev)
+        s.solve(B, lam, X)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = s.solve(B, lam, X)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        X64 = np.zeros((P.p, P.m))
+        s.solution_f64(X64)
+        st = r.stats
+        exact = sum(set(np.flatnonzero(X64[i]).tolist()) == supp_true[i] for i in range(P.p))
+        rel = float(np.linalg.norm(X64 - Xt) / np.linalg.norm(Xt))
+        res = np.linalg.norm(P.B.astype(np.float64) - X64 @ P.At.astype(np.float64), axis=1)
+        print(json.dumps({"metric": "lambda = 0, 4096 x 16384, k~U[400,600]: time to ||xi|| <= r2",
+                          "rho": rho, "p": P.p, "ms": round(ms, 2), "signals_per_s": round(P.p / ms * 1e3, 1),
+                          "outer_mean": float(st["outer_iters"].mean()), "outer_max": int(st["outer_iters"].max()),
+                          "early_stopped": int(np.sum(st["status"] == mpl.MPL_SIG_EARLY_STOP)),
+                          "support_exact": int(exact), "rel_error_vs_x_true": rel,
+                          "max_residual_over_r2": float(res.max() / r2), "S_mean": float(st["active_size"].mean())}),
+              flush=True)
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,9 +433,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--corr-shape", type=int, nargs=3, metavar=("N", "M", "P"), default=None,
                     help="profile the correlation GEMM alone on this shape instead of the benchmark")
+    ap.add_argument("--omp-compare", type=int, default=0, metavar="P",
+                    help="lambda = 0 on the 4096 x 16384, k 400-600 shape for P signals: rho = 1 (batch "
+                         "OMP) against multi-atom growth, instead of the benchmark")
     args = ap.parse_args()
     if args.corr_shape:
         correlation_microbench(args)
+        return
+    if args.omp_compare:
+        omp_compare(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
