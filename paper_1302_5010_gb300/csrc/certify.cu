@@ -404,14 +404,16 @@ __host__ __device__ inline int fac_stage_floats(int scap) {
 // trailing triangle is read and written once per W columns (np^3 / (3W) touches in
 // all) instead of once per 4 or 8.  stage: fac_stage_floats(rows) floats, 16-byte
 // aligned.  Returns 0 or -1 (non-positive pivot); flag likewise.
-static_assert(FIN_THREADS == 256, "chol_tiled maps 256 threads onto 16 x 16 blocks of a 64 x 64 tile");
+// (blockDim.x a multiple of 256: each 256 threads take one 64 x 64 tile at a time as
+// 16 x 16 blocks of 4 x 4)
 __device__ __noinline__ int chol_tiled(float* M, int ld, int np, float* rdiag, int* flag, float* stage) {
     constexpr int W = FAC_TILE_W, DS = W + 1;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     float* D = stage;                 // W x W diagonal block, stride DS
     // k-major panel PT[k * PS + (r - j1)], 16-byte aligned for the float4 reads
     float* PT = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(stage + W * DS) + 15) & ~(uintptr_t)15);
-    const int ty = tid >> 4, tx = tid & 15;   // 16 x 16 threads of 4 x 4 blocks (nt = 256)
+    const int ty = (tid & 255) >> 4, tx = tid & 15;  // 16 x 16 threads of 4 x 4 blocks per tile
+    const int sub = tid >> 8, nsub = nt >> 8;        // tiles in flight at once
     for (int j0 = 0; j0 < np; j0 += W) {
         const int w = min(W, np - j0), j1 = j0 + w, nr = np - j1;
         const int PS = ((nr + 63) / 64) * 64;
@@ -470,7 +472,7 @@ __device__ __noinline__ int chol_tiled(float* M, int ld, int np, float* rdiag, i
         __syncthreads();
         // trailing triangle: 64 x 64 tiles (ti >= tj), element (r, c) with c <= r
         const int T = (nr + 63) / 64;
-        for (int t = 0; t < T * (T + 1) / 2; ++t) {
+        for (int t = sub; t < T * (T + 1) / 2; t += nsub) {
             int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
             while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
             while (ti * (ti + 1) / 2 > t) --ti;
@@ -1109,7 +1111,11 @@ __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
     return factor(sh.F, np, &sh.ival[0]);
 }
 
-__global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int msm, int rsm) {
+// NT = FIN_THREADS (two CTAs per SM) or FIN_THREADS_WIDE (one CTA per SM, taken when the
+// shared-memory layout allows only one anyway: the wider CTA shortens the latency-bound
+// sweeps over the support's columns).
+template <int NT>
+__global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int scap, int msm, int rsm) {
     const int g = blockIdx.x;
     if (g >= d.cnt->fin_n) return;
     const int i = d.list_fin[g];
@@ -1528,7 +1534,11 @@ __global__ void __launch_bounds__(FIN_THREADS, 2) k_finish(Dev d, int scap, int 
 cudaError_t prepare_finish() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIN_SMEM_MAX);
+    cudaError_t e = cudaFuncSetAttribute(k_finish<FIN_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FIN_SMEM_MAX);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_finish<FIN_THREADS_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FIN_SMEM_MAX);
     if (e == cudaSuccess) attr = true;
     return e;
 }
@@ -1550,7 +1560,8 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     const size_t dyn = dyn_of(msm, rsm);
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
-    k_finish<<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);
+    if (dyn > FIN_SMEM_TWO_CTAS) k_finish<FIN_THREADS_WIDE><<<ub, FIN_THREADS_WIDE, dyn, s>>>(d, scap, msm, rsm);
+    else k_finish<FIN_THREADS><<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);
     ++*nl;
     return cudaGetLastError();
 }

@@ -231,6 +231,7 @@ constexpr int APG_THREADS = 256;
 constexpr size_t FIN_SMEM_TWO_CTAS = 110 * 1024;  // dynamic shared memory that keeps 2 finish CTAs per SM
 constexpr size_t FIN_SMEM_MAX = 225 * 1024;       // the most one finish CTA takes
 constexpr int FIN_THREADS = 256;
+constexpr int FIN_THREADS_WIDE = 512;  // one finish CTA per SM (large active sets)
 constexpr int FIN_MAX_PIVOTS = 16;
 constexpr int FIN_MAX_FAILS = 6;
 
