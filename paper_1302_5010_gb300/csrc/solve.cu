@@ -42,6 +42,19 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
     return t;
 }
 
+// block_sum without its leading barrier, for callers where a barrier already separates
+// the previous readers of red from these writes.
+__device__ __forceinline__ float block_sum_after_barrier(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += red[w];  // same order in every thread
+    return t;
+}
+
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -639,8 +652,9 @@ __global__ void __launch_bounds__(APG_THREADS, 4) k_apg(Dev d, int vcap, int gca
                 sh.u[r] = z;
             }
             __syncthreads();
-            part = mvF(sh.u, sh.Gu);  // the block sum's barriers also publish Gu
-            const float Fn = block_sum(part, sh.red);
+            part = mvF(sh.u, sh.Gu);  // the block sum's barrier also publishes Gu
+            // (the barrier above already follows every read of red by the last block sum)
+            const float Fn = block_sum_after_barrier(part, sh.red);
             ++iters;
             if (Fn > F) {
                 // function-value restart: back to the previous point, momentum off;
