@@ -14,12 +14,10 @@ namespace mpl {
 // exit), and it waits (griddepcontrol.wait: the predecessor grid complete, its writes
 // visible) before touching anything.  Launched without the attribute (or after a
 // non-kernel node) the wait returns at once.
+// (MPL_NO_PDL builds the chain without the attribute, for measuring what it saves.)
 __device__ __forceinline__ void pdl_enter() {
 #if !defined(MPL_NO_PDL)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-#if defined(MPL_PDL_EARLY)
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-#endif
 #endif
 }
 
