@@ -35,7 +35,8 @@ FP32_LANES_PER_SM = 128
 # roofline block reports, from the ncu captures summarised under profiles/ (set to None when
 # the kernel changes after its capture).
 TRAFFIC = {
-    "k_finish": None,  # changed since its last capture (profiles/k_finish_c2.md)
+    "k_finish": {"bytes_per_launch": (15.539968e6 + 3.524864e6) / 2,
+                 "capture": "profiles/k_finish_c2.md (launches 5 and 6 of the 1024 x 8192, p = 256 solve)"},
     "k_corr_bf16": {"bytes_per_launch": 17.319424e6,
                     "capture": "profiles/k_corr_bf16_c2.md (first outer iteration, 256 signals)"},
     "k_corr_f32": None,
