@@ -452,7 +452,7 @@ __device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* 
     for (int w = 0; w < nw; ++w) { a += red[w]; b += red[32 + w]; c += red[64 + w]; }
 }
 
-__global__ void __launch_bounds__(APG_THREADS, 4) k_apg(Dev d, int vcap, int gcap) {
+__global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) {
     pdl_enter();
     extern __shared__ __align__(16) float gsm[];
     __shared__ ApgVec sh;
@@ -482,31 +482,7 @@ __global__ void __launch_bounds__(APG_THREADS, 4) k_apg(Dev d, int vcap, int gca
         const bool insm = s <= gcap;
         const float* G = insm ? gsm : Gg;
         const int ld = insm ? apg_ld(s) : smax;
-        const int s4 = (s + 3) & ~3;
-        if (insm && (smax & 3) == 0 && (ld & 3) == 0 && ld >= s4) {
-            // rows as float4 (16-byte aligned in both layouts; the columns s..s4-1 read past
-            // the block land in the row padding), four in flight per thread
-            const int c4 = s4 >> 2, tot = s * c4;
-            for (int e0 = tid; e0 < tot; e0 += 4 * blockDim.x) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * blockDim.x;
-                    if (e < tot) {
-                        const int r = e / c4, c = e - r * c4;
-                        v[u] = __ldg(reinterpret_cast<const float4*>(Gg + (size_t)r * smax) + c);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * blockDim.x;
-                    if (e < tot) {
-                        const int r = e / c4, c = e - r * c4;
-                        reinterpret_cast<float4*>(gsm + (size_t)r * ld)[c] = v[u];
-                    }
-                }
-            }
-        } else if (insm) {
+        if (insm) {
             // eight loads in flight per thread before their stores
             for (int e0 = tid; e0 < s * s; e0 += 8 * blockDim.x) {
                 float v[8];
