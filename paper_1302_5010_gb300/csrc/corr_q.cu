@@ -171,11 +171,27 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
             const int kw = min(kc, n - k0);
             __syncthreads();  // the previous chunk is consumed
             if (vec) {
-                const int v4 = kw >> 2;
-                for (int e = threadIdx.x; e < (qg + 1) * v4; e += blockDim.x) {
-                    const int r = e / v4, k4 = e - r * v4;
-                    const float* src = (r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b) + k0 + 4 * k4;
-                    *reinterpret_cast<float4*>(hbuf + r * ks + 4 * k4) = __ldg(reinterpret_cast<const float4*>(src));
+                // eight float4 loads per thread in flight before their stores
+                const int v4 = kw >> 2, tot = (qg + 1) * v4;
+                for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * blockDim.x) {
+                    float4 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = e0 + u * blockDim.x;
+                        if (e < tot) {
+                            const int r = e / v4, k4 = e - r * v4;
+                            const float* src = (r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b) + k0 + 4 * k4;
+                            v[u] = __ldg(reinterpret_cast<const float4*>(src));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = e0 + u * blockDim.x;
+                        if (e < tot) {
+                            const int r = e / v4, k4 = e - r * v4;
+                            *reinterpret_cast<float4*>(hbuf + r * ks + 4 * k4) = v[u];
+                        }
+                    }
                 }
             } else {
                 for (int e = threadIdx.x; e < (qg + 1) * kw; e += blockDim.x) {
