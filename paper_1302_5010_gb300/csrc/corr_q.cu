@@ -95,7 +95,37 @@ __global__ void k_save_beta(Dev d, int cur) {
     const int i = d.act[cur][kblk];
     const float* src = d.Cs + (size_t)kblk * d.m;
     float* dst = d.beta + (size_t)i * d.m;
-    for (int j = threadIdx.x; j < d.m; j += blockDim.x) dst[j] = src[j];
+    // eight loads per thread in flight before their stores (float4 rows when m % 4 == 0)
+    if ((d.m & 3) == 0) {
+        const int m4 = d.m >> 2;
+        for (int j0 = threadIdx.x; j0 < m4; j0 += 8 * blockDim.x) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < m4) v[u] = reinterpret_cast<const float4*>(src)[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < m4) reinterpret_cast<float4*>(dst)[j] = v[u];
+            }
+        }
+    } else {
+        for (int j0 = threadIdx.x; j0 < d.m; j0 += 8 * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < d.m) v[u] = src[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < d.m) dst[j] = v[u];
+            }
+        }
+    }
 }
 
 // Identity column list and counters for the Gram build (the FP32 correlation

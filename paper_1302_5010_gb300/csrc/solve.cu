@@ -83,19 +83,31 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
     double* r64 = d.R64 + (size_t)i * n;
     double ss = 0.0, es = 0.0, ts = 0.0;
     int nf = 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const float v = b[k];
-        if (!isfinite(v)) nf = 1;
-        r32[k] = v;
-        d.R32lo[(size_t)i * n + k] = 0.f;
-        r64[k] = (double)v;
-        const __nv_bfloat16 q = __float2bfloat16_rn(v);
-        if (d.R16) d.R16[(size_t)i * n + k] = q;
-        if (d.pos) d.R16c[(size_t)i * n + k] = q;  // active list = identity
-        ss += (double)v * (double)v;
-        const double fq = (double)__bfloat162float(q), e = (double)v - fq;
-        es += e * e;
-        ts += fq * fq;
+    // entries k = tid + j nt in order of j; four loads in flight before their stores
+    for (int k0 = threadIdx.x; k0 < n; k0 += 4 * blockDim.x) {
+        float bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * blockDim.x;
+            bv[u] = k < n ? b[k] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * blockDim.x;
+            if (k >= n) break;
+            const float v = bv[u];
+            if (!isfinite(v)) nf = 1;
+            r32[k] = v;
+            d.R32lo[(size_t)i * n + k] = 0.f;
+            r64[k] = (double)v;
+            const __nv_bfloat16 q = __float2bfloat16_rn(v);
+            if (d.R16) d.R16[(size_t)i * n + k] = q;
+            if (d.pos) d.R16c[(size_t)i * n + k] = q;  // active list = identity
+            ss += (double)v * (double)v;
+            const double fq = (double)__bfloat162float(q), e = (double)v - fq;
+            es += e * e;
+            ts += fq * fq;
+        }
     }
     uint32_t* mw = d.mask + (size_t)i * d.mw;
     for (int w = threadIdx.x; w < d.mw; w += blockDim.x) mw[w] = 0u;
@@ -722,6 +734,18 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
         for (int k = threadIdx.x * 4; k < n; k += blockDim.x * 4) {
             float4 acc = *reinterpret_cast<const float4*>(b + k);
             int a = 0;
+            for (; a + 7 < nz; a += 8) {  // eight atom columns' loads in flight, then in order
+                float4 cv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    cv[u] = __ldg(reinterpret_cast<const float4*>(d.A32 + (size_t)nzi[a + u] * n + k));
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float vu = nzv[a + u];
+                    acc.x = fmaf(-vu, cv[u].x, acc.x); acc.y = fmaf(-vu, cv[u].y, acc.y);
+                    acc.z = fmaf(-vu, cv[u].z, acc.z); acc.w = fmaf(-vu, cv[u].w, acc.w);
+                }
+            }
             for (; a + 3 < nz; a += 4) {
                 const float4 c0 = __ldg(reinterpret_cast<const float4*>(d.A32 + (size_t)nzi[a] * n + k));
                 const float4 c1 = __ldg(reinterpret_cast<const float4*>(d.A32 + (size_t)nzi[a + 1] * n + k));
