@@ -4,7 +4,7 @@
 // driven to the exact restricted minimiser by an active-set method on the
 // Gram block (the optimality conditions of the dual eq. 5 restricted to S):
 //
-//   P = supp(x), s = sign(x_P); solve G_PP z = h_P - lambda*s_P (FP64 Cholesky);
+//   P = supp(x), s = sign(x_P); solve G_PP z = h_P - lambda*s_P (Cholesky of G_PP);
 //   if sign(z) = s:  x <- z, else step from x towards z up to the first sign
 //                    crossing and drop that atom (the objective decreases
 //                    along the segment, which stays inside the orthant of s);
@@ -16,14 +16,18 @@
 // verified and refined with exact residuals r = b - A_P x and correlations
 // A^T r: these O(n|P|) sums run in double-FP32 arithmetic (error-free
 // products and sums via FMA, ~2^-44 relative) on the FP32 pipe, since GB300's
-// FP64 rate is a small fraction of its FP32 rate; the factorisation and the
-// small triangular solves stay in FP64.  The certified KKT violation on S and
-// the exact residual (FP32 hi/lo pair and FP64) are stored; the next
-// worst-case analysis certifies the atoms outside S (eq. 8).
+// FP64 rate is a small fraction of its FP32 rate.  The factor is FP32 (the
+// refinement with exact residuals restores full accuracy), updated in place when
+// an atom leaves or joins P; an FP64 factor, and then an exactly recomputed Gram
+// block, take over when the refinement stops contracting.  The certified KKT
+// violation on S and the exact residual (FP32 hi/lo pair and FP64) are stored;
+// the next worst-case analysis certifies the atoms outside S (eq. 8).
 //
-// One CTA per signal.  Shared memory is sized by the host from its bound on
+// One CTA per signal (256 threads, two CTAs per SM; 512 when the shared-memory
+// layout allows only one).  Shared memory is sized by the host from its bound on
 // |S|; the FP32 factor lives in shared memory when the bound fits there at two
-// CTAs per SM; larger FP32 factors and the FP64 factor use the signal's global
+// CTAs per SM (panel Cholesky), else in the signal's global workspace (tiled
+// Cholesky staged through shared memory); the FP64 factor always uses the
 // workspace.
 #include "mpl_internal.cuh"
 

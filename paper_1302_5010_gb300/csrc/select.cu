@@ -24,7 +24,8 @@ namespace mpl {
 
 #ifdef MPL_SEL_TRACE
 // Per-signal phase cycle counters of the selection (diagnostic builds only):
-// [row cache, radix passes, collect, re-score, sort + state, calls]
+// [row cache, k-th key, collect, re-score, sort + state, calls, band size, list-path
+//  k-th keys, list size]
 __device__ long long g_sel_trace[8192][10];
 #define ST_BEGIN long long st0_ = clock64();
 #define ST_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += clock64() - st0_; st0_ = clock64(); } while (0)
