@@ -14,6 +14,9 @@
 // bound_q * colmax * (||b|| + colmax ||x||_1) (FP32 beta and Q entries from
 // the FP32 GEMM, the FP32 sum, and the FP32 residual the re-score uses), which
 // the selection kernel takes as this route's band.
+//
+// Q also serves the Gram growth (MPL_OPT_QGRAM): the master problem's Gram block
+// G_SS is Q's S x S sub-block, so its new columns are read out of Q (k_gram_gather).
 #include "mpl_internal.cuh"
 
 namespace mpl {

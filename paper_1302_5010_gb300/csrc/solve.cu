@@ -11,6 +11,9 @@
 //               or s_max; persistent CTAs pull signals from a device queue
 //   k_residual  xi = b - A_S x_S (the residual update of Alg. 1), FP32 (+ BF16 copy)
 //   k_scatter   dense X from the active sets
+//   k_smpl_prune  Algorithm 2's pruning of the explored atoms back to rho
+// (the Gram growth read out of Q instead of k_gram is in corr_q.cu.)  The chain's
+// kernels start with pdl_enter (programmatic dependent launch).
 #include "mpl_internal.cuh"
 
 namespace mpl {
