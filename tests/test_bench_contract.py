@@ -38,3 +38,21 @@ def test_metric_matches_baseline_file():
     with open(os.path.join(ROOT, "BASELINE.json")) as f:
         base = json.load(f)
     assert bench.METRIC == base["metric"]
+
+
+def test_traffic_entries_name_committed_captures():
+    """The roofline block's `traffic` comes from an ncu capture summarised under
+    profiles/; each entry must name a summary that exists and quotes its command."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kernel, entry in bench.TRAFFIC.items():
+        if entry is None:
+            continue
+        assert entry["bytes_per_launch"] > 0, kernel
+        path = entry["capture"].split()[0]
+        assert path.startswith("profiles/"), kernel
+        full = os.path.join(ROOT, path)
+        assert os.path.isfile(full), path
+        with open(full) as f:
+            text = f.read()
+        assert "ncu" in text and "--clock-control none" in text, path
