@@ -3,9 +3,14 @@
 
 One step = one bmpl_solve of the whole batch (every outer iteration of every
 signal until each is certified), inputs resident in HBM when timing starts.
-Workload: the batch compressive-sensing configuration with the paper's
-Table I/II dictionary shape (A 1024 x 8192 Gaussian, unit-norm atoms,
-p = 256 signals, k ~ U[20, 60], lambda_i = 0.02 ||A^T b_i||_inf, rho = 15).
+Default workload: the large mixed-precision batch (A 4096 x 65536 Gaussian,
+unit-norm atoms, p = 1024 signals, k ~ U[100, 400], N(0, 1) values,
+sigma = 1e-3, lambda_i = 0.01 ||A^T b_i||_inf, rho = 100, active sets up to
+1024 atoms), the largest single-GPU batch of the method's workloads.  The
+reported path is BF16 correlation + learned warm start; plain FP32 without the
+warm start is timed alongside under the same autotuner policy.  The first 64
+signals are also solved by the FP64 oracle, which gives the per-result error
+and the host-core baseline.
 
 Prints one JSON line.  Under torchrun each rank solves its own batch (the
 signals are independent, eq. 3), so scaling is weak and there is no collective
@@ -32,15 +37,18 @@ TOL = 1e-6
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
-# roofline block reports, from the ncu captures summarised under profiles/ (set to None when
-# the kernel changes after its capture).
-TRAFFIC = {
-    "k_finish": {"bytes_per_launch": (15.539968e6 + 3.524864e6) / 2,
-                 "capture": "profiles/k_finish_c2.md (launches 5 and 6 of the 1024 x 8192, p = 256 solve)"},
-    "k_corr_bf16": {"bytes_per_launch": 17.319424e6,
-                    "capture": "profiles/k_corr_bf16_c2.md (first outer iteration, 256 signals)"},
-    "k_corr_f32": None,
-}
+# roofline block can report, per workload, from one ncu capture of that kernel (None until a
+# capture of the current kernel exists).
+TRAFFIC = {}
+
+# active-set capacity per workload (supports reach ~570 atoms on c3, ~290 on c5)
+SMAX = {"c1": None, "c2": None, "c3": 1024, "c4": 512, "c5": 512}
+# signals of the disjoint training stream for the warm-start proposal
+TRAIN_SIGNALS = {"c1": 256, "c2": 16384, "c3": 8192, "c4": 8192, "c5": 50000}
+# signals per step of the reference arm (the FP64 oracle on the host cores)
+REF_SIGNALS = {"c1": 1, "c2": 64, "c3": 16, "c4": 64, "c5": 32}
+# signals the oracle solves for the per-result error and the CPU baseline
+ERR_SIGNALS = 64
 
 
 def workload_desc(cfg: str, P, path: str) -> dict:
@@ -139,34 +147,73 @@ def peaks() -> dict:
             "source": "fallback"}
 
 
-def cpu_baseline(cfg: str, P, max_signals: int) -> dict:
+def cpu_baseline(cfg: str, P, max_signals: int, single_signals: int = None) -> tuple:
+    """The FP64 oracle on the host cores over the first signals of the batch (OpenMP across
+    signals), and on one core over fewer.  Returns (baseline entry, oracle solutions of the
+    all-cores sample)."""
     import oracle
     k = min(P.p, max_signals)
     idx = np.arange(k)
     threads = oracle.num_threads()
     t0 = time.perf_counter()
-    oracle.bmpl(P.At, P.B[idx], P.lam[idx], P.rho, threads=threads)
+    Xo, _ = oracle.bmpl(P.At, P.B[idx], P.lam[idx], P.rho, threads=threads)
     dt = time.perf_counter() - t0
     # the paper's convention is one core: the same oracle on one thread, a smaller sample
-    k1 = min(k, 32)
+    k1 = min(k, single_signals if single_signals else (32 if P.n * P.m <= (1 << 24) else 4))
     t1 = time.perf_counter()
     oracle.bmpl(P.At, P.B[:k1], P.lam[:k1], P.rho, threads=1)
     dt1 = time.perf_counter() - t1
-    return {"value": k / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {k} of the {P.p} signals of {cfg}, FP64 Algorithm 1 with exact finish, "
-                      f"OpenMP over signals, {dt:.2f} s wall",
-            "single_core": {"value": k1 / dt1, "unit": UNIT, "cores": 1,
-                            "sample": f"first {k1} signals of {cfg}, one thread, {dt1:.2f} s wall"}}
+    extra = (f"; rate extrapolated linearly to the whole batch of {P.p} (signals are independent): "
+             f"{P.p / (k / dt):.1f} s estimated" if k < P.p else "")
+    entry = {"value": k / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"first {k} of the {P.p} signals of {cfg}, FP64 Algorithm 1 with exact finish, "
+                       f"OpenMP over signals, {dt:.2f} s wall{extra}",
+             "extrapolated": k < P.p,
+             "single_core": {"value": k1 / dt1, "unit": UNIT, "cores": 1,
+                             "sample": f"first {k1} signals of {cfg}, one thread, {dt1:.2f} s wall"}}
+    return entry, Xo
+
+
+def error_vs_oracle(P, X64, Xo) -> dict:
+    """Per-result error of the GPU solutions against the FP64 oracle on the same signals:
+    relative objective difference, relative Frobenius error of X and support mismatches
+    (coefficients above 1e-3 max|x|), with the acceptance tolerances."""
+    k = Xo.shape[0]
+    A64 = P.At.astype(np.float64)
+    rel_obj = []
+    mism_sig, mism_ent = 0, 0
+    for i in range(k):
+        b = P.B[i].astype(np.float64)
+        lam = float(P.lam[i])
+        def f(x):
+            r = b - A64.T @ x
+            return lam * np.abs(x).sum() + 0.5 * r @ r
+        fo = f(Xo[i])
+        rel_obj.append(abs(f(X64[i]) - fo) / abs(fo) if fo != 0 else abs(f(X64[i])))
+        xm = np.abs(Xo[i]).max()
+        sg = np.abs(X64[i]) > 1e-3 * xm
+        so = np.abs(Xo[i]) > 1e-3 * xm
+        d = int(np.count_nonzero(sg ^ so))
+        mism_ent += d
+        mism_sig += int(d > 0)
+    den = np.linalg.norm(Xo)
+    xrel = float(np.linalg.norm(X64 - Xo) / den) if den > 0 else float(np.linalg.norm(X64))
+    ro = float(max(rel_obj)) if rel_obj else 0.0
+    return {"signals": k, "rel_objective_max": ro, "x_rel_fro": xrel, "support_mismatch_signals": mism_sig,
+            "support_mismatch_entries": mism_ent,
+            "tolerances": {"rel_objective": 1e-6, "x_rel_fro": 1e-4, "support_frac": 1e-3},
+            "within": bool(ro <= 1e-6 and xrel <= 1e-4 and mism_sig == 0)}
 
 
 def run_reference(args, rank: int, world: int) -> None:
-    """The oracle as the reference arm (CPU, rank 0 only)."""
+    """The oracle as the reference arm (CPU, rank 0 only): each step solves a bounded sample
+    of the workload's signals on the host cores; signals/s is that sample's rate."""
     if rank != 0:
         return
     from paper_1302_5010_gb300 import synth
     import oracle
     P = synth.make_config(args.config)
-    k = min(P.p, args.ref_signals)
+    k = min(P.p, args.ref_signals or REF_SIGNALS.get(args.config, 16))
     threads = oracle.num_threads()
     for _ in range(args.warmup):
         oracle.bmpl(P.At, P.B[:1], P.lam[:1], P.rho, threads=threads)
@@ -178,12 +225,15 @@ def run_reference(args, rank: int, world: int) -> None:
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = k * args.steps / tot
+    sample = (f"{k} of the {P.p} signals of {args.config} per step (consecutive slices), FP64 Algorithm 1 "
+              f"with exact finish, OpenMP over signals; signals are independent, so the rate stands for "
+              f"the whole batch")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": workload_desc(args.config, P, "oracle-fp64"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{k} signals per step of {args.config}"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -235,15 +285,62 @@ def train_proposal(args, mpl, torch, solver, P_train, dev) -> dict:
             "outer_iters_cold_mean": float(np.mean(res.stats["outer_iters"]))}
 
 
+def kernel_rooflines(P, precision: int, phase: dict, work: dict, pk: dict, sms: int) -> dict:
+    """Roofline entry of each phase's kernel: algorithmic work (device-counted FLOPs or bytes)
+    over the kernel's CUDA-event time inside the timed steps, against the measured peak of the
+    unit that bounds it (HBM copy bandwidth, dense BF16, or the FP32 FMA rate from unit counts
+    and the maximum SM clock)."""
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_note = f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x max SM clock (nominal units)"
+    hbm = pk["hbm_gbs"]
+    hbm_note = f"HBM copy bandwidth, of {pk['source']}"
+    out = {}
+
+    def entry(kernel, bound, amount, ms, peak, unit, note, amount_key):
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = amount / (ms / 1e3) / scale if ms > 0 else 0.0
+        return {"kernel": kernel, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak if peak else None, "peak_note": note, "ms_per_step": ms, amount_key: amount}
+
+    cols = work["gemm_columns"]
+    flops = 2.0 * P.n * P.m * cols
+    if precision == 0:
+        out["correlation"] = entry("k_corr_f32", "alu", flops, phase["correlation"], fp32_peak, "TFLOP/s",
+                                   fp32_note, "flop_per_step")
+    else:
+        out["correlation"] = entry("k_corr_bf16", "tensor", flops, phase["correlation"], pk["bf16_tflops"],
+                                   "TFLOP/s", f"dense bf16 burst, of {pk['source']}", "flop_per_step")
+    out["correlation"]["identity_route_ms_per_step"] = phase.get("qroute", 0.0)
+    out["correlation"]["identity_route_columns_per_step"] = work["qroute_columns"]
+    out["finish"] = entry("k_finish", "alu", work["finish_flops"], phase["finish"], fp32_peak, "TFLOP/s",
+                          fp32_note + "; dependent factor/solve sweeps keep it latency-bound", "flop_per_step")
+    if work["apg_global_elems"] > 0.5 * work["apg_elems"]:
+        out["master"] = entry("k_apg", "hbm", 4.0 * work["apg_global_elems"], phase["master"], hbm, "GB/s",
+                              hbm_note + "; Gram blocks above the shared-memory size streamed per product",
+                              "bytes_per_step")
+    else:
+        out["master"] = entry("k_apg", "alu", 2.0 * work["apg_elems"], phase["master"], fp32_peak, "TFLOP/s",
+                              fp32_note + "; Gram blocks resident in shared memory", "flop_per_step")
+    out["selection"] = entry("k_select", "hbm", 4.0 * P.m * cols, phase["selection"], hbm, "GB/s",
+                             hbm_note + "; one read of the score rows (the re-score band and any second "
+                                        "pass come on top)", "bytes_per_step")
+    out["residual"] = entry("k_residual", "hbm", work["residual_bytes"], phase["residual"], hbm, "GB/s",
+                            hbm_note, "bytes_per_step")
+    out["gram"] = entry("k_gram_gather" if work["qgram"] else "k_gram_async", "hbm", work["gram_bytes"],
+                        phase["gram"], hbm, "GB/s", hbm_note, "bytes_per_step")
+    return out
+
+
 def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local: int, warm: bool = False,
-               P_train=None) -> dict:
+               P_train=None, smax=None, want_x64: int = 0) -> dict:
     """Warm up, then time exactly args.steps solves of the whole batch (device events, L2
     flushed between steps), then the same through the C ABI with pinned host buffers."""
     At = torch.from_numpy(P.At).to(dev)
     B = torch.from_numpy(P.B).to(dev)
     lam = torch.from_numpy(P.lam).to(dev)
     X = torch.empty((P.p, P.m), dtype=torch.float32, device=dev)
-    solver = mpl.Solver(At, rho=P.rho, precision=precision)
+    opts = {"smax": smax} if smax else {}
+    solver = mpl.Solver(At, rho=P.rho, precision=precision, **opts)
     training = None
     if warm:
         training = train_proposal(args, mpl, torch, solver, P_train, dev)
@@ -262,6 +359,8 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         tune = {"qroute": qr, "sync_every": se, "qgram": qg, "fixed": True}
     elif not args.no_autotune:
         tune = solver.autotune(B, lam, TOL, stream)
+    nph = 15
+
     def timed_steps(profile: bool, clocks=None):
         """W untimed solves (they capture the iteration graphs of this mode), then exactly
         args.steps solves timed by device events, the L2 flushed before each."""
@@ -274,7 +373,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        step_ms, phase_tot, launches, certified = [], np.zeros(11), 0, True
+        step_ms, phase_tot, launches, certified = [], np.zeros(nph), 0, True
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -283,7 +382,10 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            phase_tot += np.array(mpl.mpl_get_phase_times(solver.h), dtype=np.float64)
+            ph = np.zeros(nph)
+            v = mpl.mpl_get_phase_times(solver.h)
+            ph[:len(v)] = v
+            phase_tot += ph
             launches += solver.launches()
             st = mpl.mpl_get_stats(solver.h, P.p)
             certified &= bool(rc == mpl.MPL_OK and np.all(st["status"] == mpl.MPL_SIG_CERTIFIED))
@@ -298,10 +400,17 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     step_ms, _, launches, certified, clk = timed_steps(False, clocks)
     tot_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     value = aggregate_rate(world, P.p, args.steps, tot_ms / 1e3)
-    # the kernels' own times for the roofline: the same steps again with event nodes in the
-    # captured graphs around the correlation and the exact finish
+    # the kernels' own times for the roofline: the same steps again with event nodes around
+    # every phase in the captured graphs
     prof_ms, phase_tot, _, certified_p, _ = timed_steps(True)
     certified &= certified_p
+    X64 = None
+    if want_x64:
+        # the certified FP64 iterates of the first signals, for the error against the oracle
+        Xd = torch.zeros((P.p, P.m), dtype=torch.float64, device=dev)
+        solver.solution_f64(Xd)
+        X64 = Xd[:want_x64].cpu().numpy()
+        del Xd
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     solver.set(mpl.MPL_OPT_PROFILE, 0)
@@ -320,50 +429,31 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     e2e = {"value": aggregate_rate(world, P.p, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(nbytes(Bh) + nbytes(lamh)), "d2h_bytes_per_step": int(nbytes(Xh))}
     stats = mpl.mpl_get_stats(solver.h, P.p)
+    qgram = int(solver.get(mpl.MPL_OPT_QGRAM))
     solver.close()
     del flush
-    # roofline: the correlation GEMM and the exact finish are timed by events inside the
-    # captured iteration graphs during the timed steps; the slower one is the dominant kernel
+    # roofline of every phase's kernel; the one with the most time per step is the dominant one
     pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     names = ["total", "correlation", "selection", "gram", "finish", "master", "residual"]
     phase = {nm: phase_tot[i] / args.steps for i, nm in enumerate(names)}
-    # signal columns the correlation GEMM processed per step (the identity route's excluded)
-    cols = (phase_tot[7] - phase_tot[9]) / args.steps
-    fin_flops = phase_tot[8] / args.steps   # algorithmic FLOPs of the exact finish per step
-    corr_ms, fin_ms = phase["correlation"], phase["finish"]
-    fp32_peak = 152 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    flops = 2.0 * P.n * P.m * cols
-    gemm_ach = flops / (corr_ms / 1e3) / 1e12 if corr_ms > 0 else 0.0
-    if precision == 0:
-        gemm = {"kernel": "k_corr_f32", "bound": "alu", "achieved": gemm_ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": gemm_ach / fp32_peak,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (nominal units)"}
-    else:
-        gemm = {"kernel": "k_corr_bf16", "bound": "tensor", "achieved": gemm_ach, "peak": pk["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": gemm_ach / pk["bf16_tflops"],
-                "peak_note": f"dense bf16, of {pk['source']}"}
-    gemm.update({"ms_per_step": corr_ms, "flop_per_step": flops,
-                 "identity_route_ms_per_step": phase_tot[10] / args.steps,
-                 "identity_route_columns_per_step": phase_tot[9] / args.steps})
-    if fin_ms > corr_ms:
-        ach = fin_flops / (fin_ms / 1e3) / 1e12 if fin_ms > 0 else 0.0
-        tr = TRAFFIC.get("k_finish")
-        roof = {"kernel": "k_finish", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": tr["bytes_per_launch"] if tr else None,
-                "traffic_unit": "bytes per launch", "traffic_source": tr["capture"] if tr else None,
-                "peak_note": "FP32 FMA peak from unit counts and max SM clock; the kernel is latency-bound "
-                             "(dependent factor/solve sweeps)",
-                "ms_per_step": fin_ms, "flop_per_step": fin_flops}
-    else:
-        tr = TRAFFIC.get(gemm["kernel"])
-        roof = dict(gemm, traffic=tr["bytes_per_launch"] if tr else None, traffic_unit="bytes per launch",
-                    traffic_source=tr["capture"] if tr else None)
+    phase["qroute"] = phase_tot[10] / args.steps
+    work = {"gemm_columns": (phase_tot[7] - phase_tot[9]) / args.steps, "qroute_columns": phase_tot[9] / args.steps,
+            "finish_flops": phase_tot[8] / args.steps, "apg_elems": phase_tot[11] / args.steps,
+            "apg_global_elems": phase_tot[12] / args.steps, "residual_bytes": phase_tot[13] / args.steps,
+            "gram_bytes": phase_tot[14] / args.steps, "qgram": qgram}
+    kern = kernel_rooflines(P, precision, phase, work, pk, sms)
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = dict(kern[dom])
+    tr = TRAFFIC.get((args.config, roof["kernel"]))
+    roof["traffic"] = tr
+    roof["traffic_unit"] = "bytes per launch"
     # summed event times per phase (the finish runs on a second stream, so phases overlap)
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if v > 0}
-
     roof["events_pass_ms_per_step"] = float(sum(prof_ms)) / args.steps
     return {"value": value, "tot_ms": tot_ms, "e2e": e2e, "launches": launches, "clocks": clk, "autotune": tune,
-            "certified": certified, "roofline": roof, "gemm": gemm, "training": training,
+            "certified": certified, "roofline": roof, "gemm": kern["correlation"], "kernels": kern,
+            "training": training, "X64": X64,
             "outer_iters_mean": float(np.mean(stats["outer_iters"])),
             "active_size_mean": float(np.mean(stats["active_size"]))}
 
@@ -418,18 +508,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c3")
     ap.add_argument("--path", default="mixed", choices=["plain", "mixed"],
                     help="path reported as value; the other one is timed alongside for comparison")
     ap.add_argument("--no-warm", action="store_true", help="report the reported path without the learned warm start")
-    ap.add_argument("--train-signals", type=int, default=16384)
+    ap.add_argument("--train-signals", type=int, default=None)
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-compare", action="store_true", help="skip the comparison path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default route and handshake cadence")
     ap.add_argument("--tune", default=None, metavar="QROUTE,SYNC[,QGRAM]",
                     help="fix the tuned settings instead of running the autotuner (profiling runs)")
-    ap.add_argument("--ref-signals", type=int, default=64)
-    ap.add_argument("--cpu-signals", type=int, default=256)
+    ap.add_argument("--ref-signals", type=int, default=None)
+    ap.add_argument("--cpu-signals", type=int, default=ERR_SIGNALS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--corr-shape", type=int, nargs=3, metavar=("N", "M", "P"), default=None,
                     help="profile the correlation GEMM alone on this shape instead of the benchmark")
@@ -464,11 +554,15 @@ def main():
 
     # each rank its own batch of independent signals (weak scaling)
     P = rank_problem(synth, args.config, rank)
+    smax = SMAX.get(args.config)
     precision = 1 if args.path == "mixed" else 0
     warm = not args.no_warm
     # disjoint training stream for the proposal network (same generator, other signal seed)
-    P_train = rank_problem(synth, args.config, rank, p=args.train_signals, seed_shift=9000) if warm else None
-    main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local, warm=warm, P_train=P_train)
+    ntrain = args.train_signals or TRAIN_SIGNALS.get(args.config, 8192)
+    P_train = rank_problem(synth, args.config, rank, p=ntrain, seed_shift=9000) if warm else None
+    n_err = min(P.p, args.cpu_signals) if (rank == 0 and not args.no_cpu_baseline) else 0
+    main_run = timed_path(args, mpl, torch, P, dev, precision, world, dist, local, warm=warm, P_train=P_train,
+                          smax=smax, want_x64=n_err)
     names = {1: "mixed-bf16", 0: "plain-fp32"}
     line = {"metric": METRIC, "value": main_run["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["tot_ms"] / args.steps, "higher_is_better": True,
@@ -478,16 +572,25 @@ def main():
             "certified_all": main_run["certified"], "e2e": main_run["e2e"],
             "gpu_launches": int(main_run["launches"]), "clocks": main_run["clocks"],
             "roofline": main_run["roofline"], "correlation_gemm": main_run["gemm"],
-            "outer_iters_mean": main_run["outer_iters_mean"], "warm_start_training": main_run["training"],
-            "autotune": main_run["autotune"]}
+            "kernels": main_run["kernels"],
+            "outer_iters_mean": main_run["outer_iters_mean"], "active_size_mean": main_run["active_size_mean"],
+            "warm_start_training": main_run["training"], "autotune": main_run["autotune"]}
+    line["config"]["smax"] = smax
     if not args.no_compare:
-        other = timed_path(args, mpl, torch, P, dev, 1 - precision, world, dist, local)
+        # the comparison path: the other precision without the warm start, everything else equal
+        # (same batch, capacity and autotuner candidates)
+        other = timed_path(args, mpl, torch, P, dev, 1 - precision, world, dist, local, smax=smax)
         line[names[1 - precision].replace("-", "_")] = {
             "value": other["value"], "ms_per_step": other["tot_ms"] / args.steps, "e2e": other["e2e"]["value"],
-            "certified_all": other["certified"], "roofline": other["roofline"], "outer_iters_mean": other["outer_iters_mean"],
-            "correlation_gemm": other["gemm"], "clocks": other["clocks"], "autotune": other["autotune"]}
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.config, P, args.cpu_signals)
+            "certified_all": other["certified"], "roofline": other["roofline"],
+            "outer_iters_mean": other["outer_iters_mean"], "correlation_gemm": other["gemm"],
+            "kernels": other["kernels"], "clocks": other["clocks"], "autotune": other["autotune"],
+            "warm_start": False}
+        line["speedup_vs_" + names[1 - precision].replace("-", "_")] = main_run["value"] / other["value"]
+    if n_err:
+        cb, Xo = cpu_baseline(args.config, P, n_err)
+        line["cpu_baseline"] = cb
+        line["error_vs_oracle"] = error_vs_oracle(P, main_run["X64"], Xo)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -194,14 +194,21 @@ mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void
  *   C  m x p column-major FP32 output, C[i*m + j] = a_j^T r_i, device memory.
  *   stream  cudaStream_t (NULL = legacy default stream); the call is
  *           asynchronous and stream-ordered.
- * Limits: 1 <= n <= 65536, m >= 1, 0 <= p <= MPL_NOALLOC_MAX_SIGNALS; a larger
- * p returns MPL_ERR_UNSUPPORTED, host pointers return MPL_ERR_ARG.
+ * A, R and C must be device (or managed) memory that the current device owns,
+ * each 16-byte aligned (a view that starts inside an allocation at an offset
+ * that is not a multiple of 4 floats is refused); anything else returns
+ * MPL_ERR_ARG before any launch.
+ * Limits: 1 <= n <= 65536, 1 <= m <= 2^26, 0 <= p <= MPL_NOALLOC_MAX_SIGNALS;
+ * a larger p returns MPL_ERR_UNSUPPORTED, a bad n or m MPL_ERR_ARG.
  * Scratch: a fixed MPL_NOALLOC_SCRATCH_BYTES device array inside the library,
  * held by every GPU that loads it until the process exits.  The first call on
  * a device looks up that array's address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every
- * call rewrites the scratch it reads, and all calls share it, so calls whose
- * GPU work overlaps (different streams, no ordering between them) race.
+ * device current and caches it with the current CUDA context; a later call
+ * that finds another context current (after cudaDeviceReset, say) looks it up
+ * again.  Make the first call on a device, and the first after such a reset,
+ * before any stream capture.  Every call rewrites the scratch it reads, and
+ * all calls share it, so calls whose GPU work overlaps (different streams, no
+ * ordering between them) race.
  */
 #define MPL_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define MPL_NOALLOC_MAX_SIGNALS ((int)((MPL_NOALLOC_SCRATCH_BYTES - 256u) / 4u))
@@ -260,8 +267,12 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
  * residual and correlation sums); entry 9 how many of the entry-7 columns the
  * identity route (MPL_OPT_QROUTE) scored instead of the GEMM; 7..9 always
  * filled.  Entry 10: device milliseconds of the identity-route scoring (entry
- * 1 then holds the GEMM alone).  Returns the number of values written (<= cap,
- * <= 11). */
+ * 1 then holds the GEMM alone).  Entries 11..14, always filled, count the
+ * algorithmic work of the memory-bound kernels over the whole solve: 11 the
+ * Gram-block entries read by the master problems' products, 12 how many of
+ * them came from global memory (blocks too large for shared memory), 13 the
+ * bytes the residual update reads and writes, 14 the bytes the Gram growth
+ * reads and writes.  Returns the number of values written (<= cap, <= 15). */
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
 
 /* Autotuner of the batched solve (no counterpart in the paper, which has no

@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     float* Gi = d.G + (size_t)i * smax * smax;
     __shared__ int sidx[1024];  // smax <= 1024
     __shared__ __align__(16) float hbuf[GQ_BUF];
+    if (threadIdx.x == 0)  // s q entries of Q read, 2 s q of G written, q atoms and b read, q of h written
+        atomicAdd(&d.cnt->gram_bytes, 12ull * s * q + 4ull * n * (q + 1) + 4ull * q);
     for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
     __syncthreads();
     // new columns (and, by symmetry, rows) of G_SS: eight independent loads per thread

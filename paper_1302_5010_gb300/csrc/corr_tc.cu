@@ -14,8 +14,11 @@
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (each warp its 32-lane
 //           quarter = 32 atoms), coalesced FP32 stores of the score rows
 //           C[k*m + j], then release the accumulator.
-// Every mbarrier wait is bounded; on expiry the CTA records DERR_TIMEOUT,
-// drains, frees its TMEM and exits.  No cluster multicast is used.
+// Every mbarrier wait is bounded; on expiry the CTA records DERR_TIMEOUT and
+// drains before it frees its TMEM: the producer waits (bounded) for every
+// stage whose TMA loads it issued, the MMA thread commits to a drain barrier
+// and waits (bounded) for the MMAs it issued, then the CTA deallocates and
+// exits.  No cluster multicast is used.
 #include <cuda.h>
 
 #include "mpl_internal.cuh"
@@ -52,6 +55,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
+constexpr uint64_t DRAIN_LIMIT_NS = 1000000000ull;  // a drain wait gives up after 1 s
+
 // Bounded wait for the phase with the given parity to complete.  Returns false
 // on expiry (WAIT_LIMIT_NS) or when another role of the CTA has given up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
@@ -71,6 +76,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
             const uint64_t now = globaltimer_ns();
             if (it == 0) t0 = now;
             else if (now - t0 > WAIT_LIMIT_NS || *abort_flag) return false;
+        }
+    }
+}
+
+// Drain wait after a give-up: bounded by time only (the abort flag is already set).
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 0u) {
+            const uint64_t now = globaltimer_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > DRAIN_LIMIT_NS) return false;
         }
     }
 }
@@ -134,6 +161,7 @@ struct TcSmem {
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert((2 * STAGES + 5) * 8 + 8 <= 256, "barriers, TMEM slot and abort flag fit their area");
 };
 
 template <int BN, int STAGES>
@@ -147,7 +175,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* drain = tempty + 2;  // the MMA thread's completion barrier after a give-up
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,6 +191,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -186,6 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
             int stage = 0;
             uint32_t ph = 0;
+            uint32_t armed = 0, armed_par = 0;  // stages with loads issued, and the phase they complete
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 const int tm = t / tiles_n, tn = t - tm * tiles_n;
                 for (int kb = 0; kb < nk; ++kb) {
@@ -195,8 +226,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(&full[stage], L::STAGE_BYTES);
                     tma_load_2d(sa, &tmA, &full[stage], kb * TC_BK, tm * TC_BM);
                     tma_load_2d(sb, &tmR, &full[stage], kb * TC_BK, tn * BN);
+                    armed |= 1u << stage;
+                    armed_par = (armed_par & ~(1u << stage)) | (ph << stage);
                     if (++stage == STAGES) { stage = 0; ph ^= 1u; }
                 }
+            }
+            if (*abort_flag) {
+                // no copy may still target this CTA's shared memory when it exits: wait for the
+                // last phase armed on each stage (a consumed one returns at once)
+                for (int st = 0; st < STAGES; ++st)
+                    if (armed & (1u << st)) mbar_wait_drain(&full[st], (armed_par >> st) & 1u);
             }
         }
     } else if (warp == 1) {
@@ -228,6 +267,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (!ok) break;
                 mma_commit(&tfull[acc]);
+            }
+            if (*abort_flag) {
+                // every MMA this thread issued completes before the accumulators are freed
+                mma_commit(drain);
+                mbar_wait_drain(drain, 0);
             }
         }
     } else {

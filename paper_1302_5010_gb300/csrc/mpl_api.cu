@@ -105,7 +105,7 @@ struct mpl_ctx {
     int last_p = 0;
     std::vector<mpl_signal_stats_t> stats;
     int64_t launches = 0;
-    double phase_ms[11] = {0};
+    double phase_ms[15] = {0};
     std::vector<cudaEvent_t> evpool;
 };
 
@@ -694,8 +694,7 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, doubl
     if (e != cudaSuccess) return e;
     int64_t cnt = 0;
     PhaseTimer gpt{h, run, {}, 0, true};
-    gpt.only_a = 1;  // correlation and exact finish: the two phases a roofline needs
-    gpt.only_b = 4;
+    gpt.only_a = -1;  // every phase (the profiling pass is timed apart from the reported one)
     cudaError_t el = launch_iteration(h, d, t, p, run, prof ? &gpt : nullptr, &cnt);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(run, &graph);
@@ -803,7 +802,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     int act_ub = p;
     const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
-    double graph_phase[11] = {0};
+    double graph_phase[15] = {0};
     for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
         if (graph) {
             size_t gi = 0;
@@ -856,6 +855,10 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
     h->phase_ms[8] = (double)h->cnt_h->fin_flops;  // algorithmic FLOPs of the exact finish
     h->phase_ms[9] = (double)h->cnt_h->qcols;      // of those columns, scored by the identity route
+    h->phase_ms[11] = (double)h->cnt_h->apg_elems;     // Gram-block entries the master problems read
+    h->phase_ms[12] = (double)h->cnt_h->apg_gl_elems;  // of those, from global memory
+    h->phase_ms[13] = (double)h->cnt_h->res_bytes;     // bytes of the residual update
+    h->phase_ms[14] = (double)h->cnt_h->gram_bytes;    // bytes of the Gram growth
     h->launches = nl;
     bool all_ok = true;
     std::memcpy(h->stats.data(), h->stats_pin, (size_t)p * sizeof(mpl_signal_stats_t));
@@ -1175,7 +1178,7 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
 
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
     if (!h || !ms_out) return 0;
-    const int k = std::min(cap, 11);
+    const int k = std::min(cap, 15);
     for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
     return k;
 }

@@ -61,6 +61,11 @@ struct Counters {
     unsigned long long fin_flops;  // algorithmic FLOPs of the exact finish (factor, solves, residual sums)
     unsigned long long qcols;  // signal columns scored by the identity route beta - Q_S x_S
     int sel_done;    // selection CTAs finished (the last one compacts the lists)
+    // algorithmic work of the memory-bound kernels (roofline accounting, all iterations)
+    unsigned long long apg_elems;     // Gram-block entries read by the master problems' products
+    unsigned long long apg_gl_elems;  // of those, read from global memory (blocks outside shared memory)
+    unsigned long long res_bytes;     // bytes the residual update reads (atoms, b) and writes (R)
+    unsigned long long gram_bytes;    // bytes the Gram growth reads (Q or atoms, b) and writes (G, h)
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 

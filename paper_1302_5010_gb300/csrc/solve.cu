@@ -159,6 +159,8 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->fin_flops = 0ull;
             d.cnt->qcols = 0ull;
             d.cnt->sel_done = 0;
+            d.cnt->apg_elems = d.cnt->apg_gl_elems = 0ull;
+            d.cnt->res_bytes = d.cnt->gram_bytes = 0ull;
         }
     }
 }
@@ -279,6 +281,8 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
     const int a0 = blockIdx.y * BM;
     if (a0 >= s || q == 0) return;
     const int n = d.n, smax = d.smax;
+    if (blockIdx.y == 0 && threadIdx.x == 0)  // s + 1 columns (atoms, b) read, 2 s q of G and q of h written
+        atomicAdd(&d.cnt->gram_bytes, 4ull * n * (s + 1) + 8ull * s * q + 4ull * q);
     const int* Si = d.S + (size_t)i * smax;
     float* Gi = d.G + (size_t)i * smax * smax;
     extern __shared__ __align__(16) float gsm[];
@@ -675,6 +679,11 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         AT_CNT(5, iters);
         if (tid == 0) {
             d.inner[i] += iters;
+            // products with the block: the power steps, G u at the warm start, one per iteration
+            const unsigned long long ss = (unsigned long long)s * (unsigned long long)s;
+            const unsigned long long nmv = (unsigned long long)(npow + 1 + iters);
+            atomicAdd(&d.cnt->apg_elems, ss * nmv);
+            atomicAdd(&d.cnt->apg_gl_elems, insm ? ss : ss * nmv);
             // early stopping, eq. (stop_con): decrease of f over this outer iteration's
             // master problem (F0 is f at x^{t-1}, new entries at zero)
             if (d.early && d.stop_eps >= 0.f && d.snew[i] > 0 &&
@@ -803,6 +812,9 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
         d.r16e[i] = sqrtf(es) * (1.f + 1e-5f);
         d.r16t[i] = sqrtf(ts) * (1.f + 1e-5f);
         d.nnz[i] = nz;
+        // atom columns and b read, the FP32 residual (and its BF16 copies) written
+        atomicAdd(&d.cnt->res_bytes, (unsigned long long)n * (4ull * (nz + 2) + (d.R16 ? 2ull : 0ull) +
+                                                              (d.pos ? 2ull : 0ull)));
     }
 }
 

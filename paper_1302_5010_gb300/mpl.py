@@ -271,8 +271,8 @@ def mpl_get_solution_f64(h, p: int, X64) -> None:
 
 
 def mpl_get_phase_times(h) -> list:
-    buf = (ctypes.c_double * 11)()
-    k = load().mpl_get_phase_times(h, buf, 11)
+    buf = (ctypes.c_double * 15)()
+    k = load().mpl_get_phase_times(h, buf, 15)
     return [buf[i] for i in range(k)]
 
 
@@ -290,7 +290,8 @@ def mpl_get_launch_count(h) -> int:
 
 
 PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "corr_columns",
-          "finish_flops", "qroute_columns", "qroute")
+          "finish_flops", "qroute_columns", "qroute", "apg_elems", "apg_global_elems", "residual_bytes",
+          "gram_bytes")
 
 
 @dataclass
@@ -320,6 +321,9 @@ class Solver:
 
     def set(self, key: int, value: float) -> None:
         mpl_set_option(self.h, key, value)
+
+    def get(self, key: int) -> float:
+        return mpl_get_option(self.h, key)
 
     def solve(self, B, lam, X, tol: float = 1e-6, stream=None) -> SolveResult:
         p = B.shape[0]

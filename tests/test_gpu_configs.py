@@ -28,11 +28,20 @@ def test_c5_shape_mixed_subset():
     check_against_oracle(P, X64, oracle_solve(P))
 
 
-def test_c3_shape_mixed_subset():
-    P = synth.make_config("c3", p=6)
+def test_c3_mixed_64_signal_subset():
+    """The benchmark's workload (4096 x 65536, rho = 100, active sets up to 1024 atoms) on
+    the first 64 signals of its batch: every signal against the FP64 oracle with the
+    acceptance tolerances, and every certificate re-checked in FP64."""
+    import oracle
+    P = synth.make_config("c3", p=64)
     X, X64, res = solve_gpu(P, precision=1, smax=1024)
     assert_certified(res)
-    check_against_oracle(P, X64, oracle_solve(P))
+    Xo = oracle_solve(P)
+    check_against_oracle(P, X64, Xo)
+    check_against_oracle(P, X, Xo)
+    for i in range(0, P.p, 8):
+        c = oracle.certify(P.At, P.B[i], float(P.lam[i]), X64[i])
+        assert c["kkt"] <= 1e-6 * (1 + 1e-9), (i, c)
 
 
 @pytest.mark.parametrize("cfg,p,smax", [("c3", 16, 1024), ("c5", 24, 512)])

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from oracle import checkers as ck
 from paper_1302_5010_gb300 import mpl, synth
+from parity import check_against_oracle
 from test_gpu_parity import solve_gpu
 
 pytestmark = pytest.mark.gpu
@@ -100,3 +101,58 @@ def test_least_squares_omp(seed):
         xo, S = refs[i]
         assert sorted(np.flatnonzero(X64[0]).tolist()) == sorted(S)
         np.testing.assert_allclose(X64[0], xo, rtol=0, atol=1e-6 * np.abs(xo).max())
+
+
+def _oracle_path(P, i, T):
+    """The oracle's exact iterates x^t, t = 0..T (x^0 = 0), of signal i: one solve per prefix
+    of the outer loop (max_outer = t), each the exact minimiser on the active set S_t."""
+    xs = [np.zeros(P.m)]
+    for t in range(1, T + 1):
+        x, r, _ = oracle.mpl(P.At, P.B[i], float(P.lam[i]), P.rho, max_outer=t)
+        xs.append(x)
+    return xs
+
+
+def _single(P, i):
+    return synth.Problem(P.name + f"[{i}]", P.At, P.B[i:i + 1].copy(), P.lam[i:i + 1].copy(), P.rho)
+
+
+@pytest.mark.parametrize("rule,precision", [("r2", 0), ("r2", 1), ("rinf", 0), ("eps", 0)])
+def test_early_stop_parity_midway_thresholds(rule, precision):
+    """Each early-stopping rule with its threshold halfway (geometrically) between the values
+    the rule sees at two consecutive outer iterations of the oracle's path, so that rounding
+    differences between the FP32 iterates and the oracle's exact ones cannot move the
+    iteration at which it fires: the GPU must stop at the same active set and return the
+    oracle's early-stopped solution (Sec. 2.5, eqs. stop1 and stop_con)."""
+    P = synth.small_problem(256, 1024, 4, 24, 36, rho=4, seed=41, lam_frac=0.01)
+    A = P.At.astype(np.float64)
+    tstar = 3
+    for i in range(P.p):
+        b = P.B[i].astype(np.float64)
+        xs = _oracle_path(P, i, tstar + 1)
+        if rule == "r2":
+            v = [np.linalg.norm(b - A.T @ x) for x in xs]
+            thr = np.sqrt(v[tstar] * v[tstar - 1])
+            opts = dict(stop_r2=thr)
+        elif rule == "rinf":
+            v = [np.abs(A @ (b - A.T @ x)).max() for x in xs]
+            thr = np.sqrt(v[tstar] * v[tstar - 1])
+            assert thr > P.lam[i] * 1.01
+            opts = dict(stop_rinf=thr)
+        else:
+            lam = float(P.lam[i])
+            f = [lam * np.abs(x).sum() + 0.5 * np.sum((b - A.T @ x) ** 2) for x in xs]
+            dec = [(f[t - 1] - f[t]) / abs(P.rho * 0.5 * (b @ b)) for t in range(1, tstar + 2)]
+            thr = np.sqrt(dec[tstar - 1] * dec[tstar - 2])  # fires after the master problem of t*
+            assert dec[tstar - 2] > 1.2 * dec[tstar - 1]
+            opts = dict(stop_eps=thr)
+        # the oracle with the rule on
+        key = {"stop_r2": "stop_r2", "stop_rinf": "stop_rinf", "stop_eps": "stop_eps"}
+        xo, ro, _ = oracle.mpl(P.At, P.B[i], float(P.lam[i]), P.rho, **{key[k]: v for k, v in opts.items()})
+        assert ro["status"] == 3, (rule, i, ro)
+        Pi = _single(P, i)
+        X, X64, res = solve_gpu(Pi, precision=precision, **opts)
+        st = res.stats
+        assert st["status"][0] == mpl.MPL_SIG_EARLY_STOP, (rule, i, st["status"])
+        assert st["active_size"][0] == ro["S_size"], (rule, i, st["active_size"][0], ro["S_size"])
+        check_against_oracle(Pi, X64, xo[None, :], [0])

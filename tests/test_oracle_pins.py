@@ -197,3 +197,42 @@ def test_edge_cases():
     # rho larger than the number of violators: takes all of them at once
     x, r, tr = oracle.mpl(P.At, P.B[0], P.lam[0], 64)
     assert r["status"] == 0 and ck.kkt_violation(P.At, P.B[0], x, float(P.lam[0])) < 1e-10
+
+
+@pytest.mark.parametrize("frac", [0.1, 0.4, 0.8])
+def test_gap_closed_form_orthonormal_at_zero(frac):
+    """Dual of eq. 5 with the scaled dual point alpha = r min(1, lambda/||A^T r||_inf): for an
+    orthonormal A at x = 0 (r = b, P = ||b||^2 / 2) the point is alpha = c b with
+    c = lambda/||A^T b||_inf, D = c ||b||^2 - c^2 ||b||^2 / 2, and the relative gap is
+    (P - D)/P = (1 - c)^2 (worked out by hand).  A sign slip in D, a wrong dual scale or a
+    division by D instead of P moves the value off this curve."""
+    rng = np.random.default_rng(70 + int(frac * 10))
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    At = Q.T.copy()
+    b = rng.standard_normal(40)
+    lam = frac * np.abs(At @ b).max()
+    c = oracle.certify(At, b, lam, np.zeros(40))
+    assert c["gap"] == pytest.approx((1.0 - frac) ** 2, rel=1e-12)
+    assert c["objective"] == pytest.approx(0.5 * b @ b, rel=1e-14)
+
+
+def test_gap_weak_duality_and_checker_agreement():
+    """At points away from the optimum the oracle's gap bounds the true suboptimality from
+    above (weak duality: D(alpha) <= P*, with P* from the independent coordinate-descent
+    solver), vanishes at the optimum, and agrees with the numpy certificate."""
+    P = synth.small_problem(96, 300, 3, 4, 10, rho=3, seed=71, lam_frac=0.05)
+    rng = np.random.default_rng(5)
+    for i in range(P.p):
+        b = P.B[i].astype(np.float64)
+        lam = float(P.lam[i])
+        xs = ck.cd_lasso(P.At, b, lam)
+        fstar = ck.objective(P.At, b, xs, lam)
+        c_opt = oracle.certify(P.At, b, lam, xs)
+        assert abs(c_opt["gap"]) < 1e-10
+        for scale in (0.0, 0.5, 0.9, 1.2):
+            x = scale * xs + (0.0 if scale == 0 else 0.01) * rng.standard_normal(P.m) * (xs != 0)
+            c = oracle.certify(P.At, b, lam, x)
+            f = ck.objective(P.At, b, x, lam)
+            assert c["objective"] == pytest.approx(f, rel=1e-12)
+            assert c["gap"] >= (f - fstar) / f - 1e-12
+            assert c["gap"] == pytest.approx(ck.duality_gap(P.At, b, x, lam), rel=1e-9, abs=1e-14)

@@ -55,8 +55,49 @@ def test_noalloc_rejects_oversize_and_host_buffers():
     import torch
     At, R = _data(64, 128, 4, 1)
     A_d = torch.from_numpy(At).cuda()
+    R_d = torch.from_numpy(R).cuda()
     C = torch.empty((4, 128), dtype=torch.float32, device="cuda")
     big = mpl.MPL_NOALLOC_MAX_SIGNALS + 1
-    assert mpl.mpl_correlate_noalloc(A_d, 64, 128, torch.from_numpy(R).cuda(), big, C) == mpl.MPL_ERR_UNSUPPORTED
-    assert mpl.mpl_correlate_noalloc(A_d, 64, 128, R, 4, C) == mpl.MPL_ERR_ARG  # host R
-    assert mpl.mpl_correlate_noalloc(A_d, 64, 128, torch.from_numpy(R).cuda(), 0, C) == mpl.MPL_OK
+    assert mpl.mpl_correlate_noalloc(A_d, 64, 128, R_d, big, C) == mpl.MPL_ERR_UNSUPPORTED
+    assert mpl.mpl_correlate_noalloc(A_d, 64, 128, torch.from_numpy(R_d.cpu().numpy()).cuda(), 0, C) == mpl.MPL_OK
+
+
+@pytest.mark.parametrize("case", ["host_A", "host_R", "host_C", "n_too_large", "m_too_large", "misaligned_A",
+                                  "misaligned_R", "misaligned_C"])
+def test_noalloc_refuses_before_any_launch(case):
+    """Every argument check that guards the kernel's loads and stores returns MPL_ERR_ARG
+    synchronously: host buffers, sizes outside the limits, and views whose start is not
+    16-byte aligned (the kernel reads and writes float4 rows)."""
+    import torch
+    n, m, p = 64, 128, 4
+    At, R = _data(n, m, p, 3)
+    A_d = torch.from_numpy(At).cuda()
+    R_d = torch.from_numpy(R).cuda()
+    C = torch.zeros((p, m), dtype=torch.float32, device="cuda")
+    # offset views one float into a larger allocation: contiguous, but 4-byte aligned only
+    A_off = torch.zeros(m * n + 4, dtype=torch.float32, device="cuda")[1:1 + m * n]
+    R_off = torch.zeros(p * n + 4, dtype=torch.float32, device="cuda")[1:1 + p * n]
+    C_off = torch.zeros(p * m + 4, dtype=torch.float32, device="cuda")[1:1 + p * m]
+    args = dict(A=A_d, n=n, m=m, R=R_d, C=C)
+    if case == "host_A":
+        args["A"] = At
+    elif case == "host_R":
+        args["R"] = R
+    elif case == "host_C":
+        args["C"] = np.zeros((p, m), dtype=np.float32)
+    elif case == "n_too_large":
+        args["n"] = 65537
+    elif case == "m_too_large":
+        args["m"] = (1 << 26) + 1
+    elif case == "misaligned_A":
+        args["A"] = A_off
+    elif case == "misaligned_R":
+        args["R"] = R_off
+    elif case == "misaligned_C":
+        args["C"] = C_off
+    torch.cuda.synchronize()
+    rc = mpl.mpl_correlate_noalloc(args["A"], args["n"], args["m"], args["R"], p, args["C"])
+    assert rc == mpl.MPL_ERR_ARG, (case, rc)
+    torch.cuda.synchronize()
+    # nothing was written
+    assert torch.count_nonzero(C).item() == 0
