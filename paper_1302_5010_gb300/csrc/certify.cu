@@ -37,12 +37,16 @@ namespace mpl {
 // Per-signal phase cycle counters of the exact finish (diagnostic builds only):
 // [factor, solve, crossing, gram-zero-check, verify, exact-zero-check, steps, refinements,
 //  of the factor: support + right-hand side, Gram gather]
-__device__ long long g_fin_trace[8192][10];
-#define FT_BEGIN long long ft0_ = clock64();
+__device__ long long g_fin_trace[8192][16];
+#define FT_BEGIN long long ft0_ = clock64(), fx_ = 0;
 #define FT_SPLIT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; } while (0)
 #define FT_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
 #define FT_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
+#define FX_BEGIN fx_ = clock64();
+#define FX_END(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - fx_; } while (0)
 #else
+#define FX_BEGIN
+#define FX_END(slot) do {} while (0)
 #define FT_BEGIN
 #define FT_ADD(slot) do {} while (0)
 #define FT_CNT(slot) do {} while (0)
@@ -574,6 +578,7 @@ struct FinShared {
     int fac_np;  // rows of the FP32 factor that match P in its order (-1: rebuild next step)
     float cs[2]; // rotation of the factor update
     float rot[2][2];  // rotations of the CTA-wide update, alternating slots
+    int cg;      // 1: solves by conjugate gradients on the Gram block (no factor)
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -1115,14 +1120,154 @@ __device__ int load_factor(FinShared& sh, const float* Gi, int smax, int np) {
     return factor(sh.F, np, &sh.ival[0]);
 }
 
+// ---------------------------------------------------------------- conjugate gradients
+// FP32 block sum in a fixed order (warp butterfly, then the warps' totals in order); every
+// thread returns the total.
+__device__ __forceinline__ float bsumf(float v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = (double)v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += (float)red[w];
+    return t;
+}
+
+// q_a = (G_SS v)_a for the support positions a = P[k] (v is zero outside P, so this is
+// G_PP v_P): a warp per pair of rows, the row's first s entries as float4 slices when the
+// block's leading dimension allows (else scalar), fixed butterfly per row.
+__device__ __noinline__ void gram_rows_mv(const float* __restrict__ Gi, int smax, int s, const int* P, int np,
+                             const float* v, float* q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool vec = (smax & 3) == 0;
+    for (int k = 2 * warp; k < np; k += 2 * nw) {
+        const int ra = P[k], rb = k + 1 < np ? P[k + 1] : P[k];
+        const float* ga = Gi + (size_t)ra * smax;
+        const float* gb = Gi + (size_t)rb * smax;
+        float sa = 0.f, sb = 0.f;
+        for (int c0 = 4 * lane; c0 < s; c0 += 512) {
+            float4 a4[4], b4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    if (vec) {
+                        a4[u] = __ldg(reinterpret_cast<const float4*>(ga + c));
+                        b4[u] = __ldg(reinterpret_cast<const float4*>(gb + c));
+                    } else {
+                        a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
+                        b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
+                    }
+                } else {
+                    a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    // v has zeros from s up to the next multiple of 4 (and outside P)
+                    const float4 x = *reinterpret_cast<const float4*>(v + c);
+                    sa = fmaf(a4[u].x, x.x, sa); sa = fmaf(a4[u].y, x.y, sa);
+                    sa = fmaf(a4[u].z, x.z, sa); sa = fmaf(a4[u].w, x.w, sa);
+                    sb = fmaf(b4[u].x, x.x, sb); sb = fmaf(b4[u].y, x.y, sb);
+                    sb = fmaf(b4[u].z, x.z, sb); sb = fmaf(b4[u].w, x.w, sb);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (lane == 0) {
+            q[ra] = sa;
+            if (k + 1 < np) q[rb] = sb;
+        }
+    }
+}
+
+// Conjugate gradients for G_PP z = rhs in FP32 (supports whose FP32 factor would not fit
+// shared memory; the Gram blocks of these workloads are well conditioned).  io holds the
+// right-hand side on entry and the solution on exit, both indexed by support slot k < np;
+// x0 (indexed by S position, may be null) is the warm start on P.  The four vectors are
+// kept by S position in `vec` (4 x ld floats, 16-byte aligned, ld >= s rounded up to 4):
+// z, r, p (zero outside P, the product's operand) and q = G p.  Stops when the recurred
+// residual is at most rtol ||rhs||; returns the iterations taken, or -1 when maxit is
+// reached or the curvature p^T G p is not positive (the caller falls back to a factor).
+__device__ __noinline__ int cg_solve(FinShared& sh, const float* Gi, int smax, int s, int np, double* io, const double* x0,
+                        float rtol, int maxit, float* vec, int ld) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* z = vec;
+    float* r = vec + ld;
+    float* p = vec + 2 * ld;
+    float* q = vec + 3 * ld;
+    const int sp = (s + 3) & ~3;
+    for (int a = tid; a < sp; a += nt) { p[a] = 0.f; z[a] = 0.f; }
+    __syncthreads();
+    float bb = 0.f;
+    for (int k = tid; k < np; k += nt) {
+        const int a = sh.P[k];
+        const float rhs = (float)io[k];
+        bb = fmaf(rhs, rhs, bb);
+        r[a] = rhs;
+        if (x0) { z[a] = (float)x0[a]; p[a] = z[a]; }
+    }
+    bb = bsumf(bb, sh.red);
+    if (x0) {  // r = rhs - G z0
+        gram_rows_mv(Gi, smax, s, sh.P, np, p, q);
+        __syncthreads();
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; r[a] -= q[a]; }
+        __syncthreads();
+    }
+    float rr = 0.f;
+    for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; rr = fmaf(r[a], r[a], rr); p[a] = r[a]; }
+    rr = bsumf(rr, sh.red);
+    const float stop2 = rtol * rtol * bb;
+    int it = 0;
+    int ok = 0;
+    for (;;) {
+        if (rr <= stop2) { ok = 1; break; }
+        if (it >= maxit) break;
+        gram_rows_mv(Gi, smax, s, sh.P, np, p, q);
+        __syncthreads();
+        float pq = 0.f;
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; pq = fmaf(p[a], q[a], pq); }
+        pq = bsumf(pq, sh.red);
+        if (!(pq > 0.f)) break;
+        const float alpha = rr / pq;
+        float rn = 0.f;
+        for (int k = tid; k < np; k += nt) {
+            const int a = sh.P[k];
+            z[a] = fmaf(alpha, p[a], z[a]);
+            const float ra = fmaf(-alpha, q[a], r[a]);
+            r[a] = ra;
+            rn = fmaf(ra, ra, rn);
+        }
+        rn = bsumf(rn, sh.red);
+        const float beta = rn / rr;
+        rr = rn;
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; p[a] = fmaf(beta, p[a], r[a]); }
+        __syncthreads();
+        ++it;
+    }
+    for (int k = tid; k < np; k += nt) io[k] = (double)z[sh.P[k]];
+    __syncthreads();
+    return ok ? it : -1;
+}
+
 // NT = FIN_THREADS (two CTAs per SM) or FIN_THREADS_WIDE (one CTA per SM, taken when the
 // shared-memory layout allows only one anyway: the wider CTA shortens the latency-bound
 // sweeps over the support's columns).
 template <int NT>
-__global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int scap, int msm, int rsm) {
+__global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int cur, int scap, int msm, int rsm) {
     const int g = blockIdx.x;
-    if (g >= d.cnt->fin_n) return;
-    const int i = d.list_fin[g];
+    if (g >= d.cnt->fin_par[cur]) return;
+    const int i = d.list_fin[cur][g];
     extern __shared__ __align__(16) double fsm[];
     __shared__ FinShared sh;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -1162,8 +1307,14 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         sh.F.Md = d.chol + (size_t)i * smax * smax;  // shares the workspace with a global FP32 factor
         sh.F.ldd = smax;
         sh.F.fp64 = 0;
+        // supports too large for a shared-memory factor are solved by conjugate gradients on
+        // the Gram block (their vectors in the staging area); a factor in global memory is the
+        // fallback when CG does not converge
+        sh.cg = (msm == 0 && s > FIN_CG_MIN_S) ? 1 : 0;
     }
     __syncthreads();
+    float* cgv = msm ? nullptr
+                     : reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sh.F.stage) + 15) & ~(uintptr_t)15);
     const double lam = (double)d.lam[i];
     const double tol = d.tol;
     const bool vec4 = (n & 3) == 0;  // float4 rows: block-cooperative residual and correlations
@@ -1205,28 +1356,42 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         if (np > 0) {
             for (int a = tid; a < np; a += nt) sh.z[a] = (double)hi[sh.P[a]] - lam * (double)sh.sg[sh.P[a]];
             FT_CNT(6);
-            if (!inc) {
-                flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
-                FT_SPLIT(8);
-                gather_gram(sh, Gi, smax, np);
-                FT_SPLIT(9);
-                const int fres = factor(sh.F, np, &sh.ival[0]);
-                FT_ADD(0);
-                if (fres != 0) {
-                    if (sh.F.fp64) break;
+            if (sh.cg) {
+                // the sign-fixed system from the current point (the master problem's solution)
+                const int it = cg_solve(sh, Gi, smax, s, np, sh.z, sh.x, 1e-6f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3);
+                FT_ADD(1);
+                if (it < 0) {  // not converging: factor this signal's blocks from now on
                     __syncthreads();
-                    if (tid == 0) sh.F.fp64 = 1;  // FP32 pivot breakdown: retry this step in FP64
+                    if (tid == 0) sh.cg = 0;
                     __syncthreads();
                     --step;
                     continue;
                 }
+                flops += (unsigned long long)(it + 1) * 2ull * np * np;
             } else {
-                flops += 2ull * np * np;
+                if (!inc) {
+                    flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
+                    FT_SPLIT(8);
+                    gather_gram(sh, Gi, smax, np);
+                    FT_SPLIT(9);
+                    const int fres = factor(sh.F, np, &sh.ival[0]);
+                    FT_ADD(0);
+                    if (fres != 0) {
+                        if (sh.F.fp64) break;
+                        __syncthreads();
+                        if (tid == 0) sh.F.fp64 = 1;  // FP32 pivot breakdown: retry this step in FP64
+                        __syncthreads();
+                        --step;
+                        continue;
+                    }
+                } else {
+                    flops += 2ull * np * np;
+                }
+                fsolve(sh.F, np, sh.z);
+                FT_ADD(1);
             }
-            fsolve(sh.F, np, sh.z);
-            FT_ADD(1);
         }
-        if (tid == 0) sh.fac_np = !sh.F.fp64 ? np : -1;
+        if (tid == 0) sh.fac_np = (!sh.F.fp64 && !sh.cg) ? np : -1;
         __syncthreads();
         // ---- first sign crossing on the segment x -> z.  Skipped right after the
         // exact check admitted an atom: its coefficient may be below the FP32
@@ -1318,8 +1483,13 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         for (int ref = 0; ref < 24; ++ref) {
             for (int a = tid; a < np; a += nt) xd[a] = to_df(sh.x[sh.P[a]]);
             __syncthreads();
-            if (vec4) residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
-            else residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+            FX_BEGIN
+            FT_CNT(11);
+            if (vec4) {
+                residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+            } else {
+                residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+            }
             __syncthreads();
             flops += 4ull * n * np;  // residual and on-support correlations
             double lmax = 0.0;
@@ -1341,28 +1511,54 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
 #pragma unroll
             for (int o = 16; o; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
             __syncthreads();
+            FX_END(10);
             if (lane == 0) sh.red[warp] = lmax;
             __syncthreads();
             dmax = 0.0;
             for (int q = 0; q < nw; ++q) dmax = fmax(dmax, sh.red[q]);
             if (np == 0 || dmax <= 0.1 * tol * lsc) break;
             if (ref > 0 && dmax > 0.25 * dprev) {
-                // slow contraction: the FP32 factor limits it, refactor once in FP64
-                if (!sh.F.fp64) {
+                // slow contraction: CG's FP32 block limits it (factor it), or the FP32 factor
+                // does (refactor once in FP64)
+                if (sh.cg) {
+                    __syncthreads();
+                    if (tid == 0) sh.cg = 0;
+                    __syncthreads();
+                    if (load_factor(sh, Gi, smax, np) != 0) { broke = true; break; }
+                } else if (!sh.F.fp64) {
                     __syncthreads();
                     if (tid == 0) sh.F.fp64 = 1;
                     __syncthreads();
+                    FX_BEGIN
+                    FT_CNT(13);
                     if (load_factor(sh, Gi, smax, np) != 0) { broke = true; break; }
+                    FX_END(14);
                 } else if (dmax >= dprev) {
                     if (exact_g) break;  // no further progress possible
                     exact_g = true;      // the FP32 Gram block limits it: rebuild it exactly
+                    FT_CNT(15);
                     if (exact_factor(sh, d.A32, n, np) != 0) { broke = true; break; }
                 }
             }
             dprev = dmax;
             FT_CNT(7);
-            flops += 2ull * np * np;
-            fsolve(sh.F, np, sh.w);
+            FX_BEGIN
+            if (sh.cg) {
+                const int it = cg_solve(sh, Gi, smax, s, np, sh.w, nullptr, 1e-4f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3);
+                if (it < 0) {
+                    // not converging: factor the block and evaluate the correction again
+                    __syncthreads();
+                    if (tid == 0) sh.cg = 0;
+                    __syncthreads();
+                    if (load_factor(sh, Gi, smax, np) != 0) { broke = true; break; }
+                    continue;
+                }
+                flops += (unsigned long long)(it + 1) * 2ull * np * np;
+            } else {
+                flops += 2ull * np * np;
+                fsolve(sh.F, np, sh.w);
+            }
+            FX_END(12);
             for (int a = tid; a < np; a += nt) sh.x[sh.P[a]] += sh.w[a];
             __syncthreads();
         }
@@ -1473,8 +1669,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             r64[k] = v;
             if (rsm) { d.R32[(size_t)i * n + k] = rh[k]; d.R32lo[(size_t)i * n + k] = rl[k]; }
             const __nv_bfloat16 q = __float2bfloat16_rn(rh[k]);
-            if (d.R16) d.R16[(size_t)i * n + k] = q;
-            if (d.pos) d.R16c[(size_t)d.pos[i] * n + k] = q;
+            if (d.R16) d.R16[(size_t)i * n + k] = q;  // (copied into the GEMM's rows on re-entry)
             rr += v * v;
             rb += v * (double)b[k];
             rs += (double)rh[k] * (double)rh[k];
@@ -1512,6 +1707,10 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             if (d.early && d.early[i]) {  // an early-stopping rule ended this signal
                 d.state[i] = ST_DONE;
                 d.sstatus[i] = MPL_SIG_EARLY_STOP;
+            } else {
+                // back into the active list two iterations on: the worst-case analysis of
+                // its exact residual certifies the atoms outside S (eq. 8)
+                d.reent[cur][atomicAdd(&d.cnt->reent_n[cur], 1)] = i;
             }
         }
     } else {
@@ -1527,7 +1726,8 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
                 d.sstatus[i] = MPL_SIG_UNCERTIFIED;
             } else {
                 d.eps[i] = fmaxf(d.eps[i] * 1e-2f, 1e-7f);
-                d.state[i] = ST_REFINE;  // picked up by the next iteration's compaction
+                d.state[i] = ST_REFINE;  // one more master problem after its re-entry
+                d.reent[cur][atomicAdd(&d.cnt->reent_n[cur], 1)] = i;
             }
         }
     }
@@ -1547,7 +1747,7 @@ cudaError_t prepare_finish() {
     return e;
 }
 
-cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl) {
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
     scap = ((scap + 31) / 32) * 32;
     if (scap > d.smax) scap = d.smax;
@@ -1564,8 +1764,8 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
     const size_t dyn = dyn_of(msm, rsm);
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
-    if (dyn > FIN_SMEM_TWO_CTAS) k_finish<FIN_THREADS_WIDE><<<ub, FIN_THREADS_WIDE, dyn, s>>>(d, scap, msm, rsm);
-    else k_finish<FIN_THREADS><<<ub, FIN_THREADS, dyn, s>>>(d, scap, msm, rsm);
+    if (dyn > FIN_SMEM_TWO_CTAS) k_finish<FIN_THREADS_WIDE><<<ub, FIN_THREADS_WIDE, dyn, s>>>(d, cur, scap, msm, rsm);
+    else k_finish<FIN_THREADS><<<ub, FIN_THREADS, dyn, s>>>(d, cur, scap, msm, rsm);
     ++*nl;
     return cudaGetLastError();
 }
@@ -1576,9 +1776,9 @@ cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_
 extern "C" int mpl_debug_fin_trace(long long* out, int count, int reset) {
     if (count > 8192) count = 8192;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 10 * (size_t)count) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 16 * (size_t)count) != cudaSuccess) return -1;
     if (reset) {
-        static long long zero[8192][10];
+        static long long zero[8192][16];
         if (cudaMemcpyToSymbol(mpl::g_fin_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
     }
     return count;

@@ -49,12 +49,17 @@ struct mpl_ctx {
     // options
     int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
     int sync_every = 2, profile = 0;
-    cudaStream_t side = nullptr;  // the exact finish runs here, overlapping the master problems
+    cudaStream_t side = nullptr;  // the exact finish of even iterations runs here (and of odd ones on side_odd),
+    cudaStream_t side_odd = nullptr;  // overlapping the master problems and the next iteration
     cudaStream_t main = nullptr;  // graph-mode solves run here (captured streams cannot be the legacy one)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t side2 = nullptr; // master problems with blocks outside shared memory, beside the others
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+    cudaEvent_t ev_sel = nullptr;                 // the selection of the current iteration is done
+    cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // the exact finish of the last iteration of each parity
     int use_graph = 1;
     struct GraphEntry {
-        int p, tk, par, nog, prof, route;
+        int p, tk, par, nog, prof, route, part;
         double tol;
         int64_t kernels;  // kernel launches captured in the graph
         cudaGraphExec_t exec;
@@ -200,8 +205,8 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.ritz, ps));
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
-                    &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin,
-                    &d.list_apg, &d.explore, &d.early};
+                    &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],
+                    &d.list_fin[1], &d.reent[0], &d.reent[1], &d.list_apg, &d.explore, &d.early};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
     CK(alloc(h, &d.r16e, (size_t)P));
@@ -422,10 +427,14 @@ void mpl_destroy(mpl_handle_t h) {
     clear_graphs(h);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->main) cudaStreamDestroy(h->main);
+    if (h->side2) cudaStreamDestroy(h->side2);
+    if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side_odd) cudaStreamDestroy(h->side_odd);
+    for (cudaEvent_t e : {h->ev_sel, h->ev_fin[0], h->ev_fin[1]})
+        if (e) cudaEventDestroy(e);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
 }
@@ -582,81 +591,73 @@ static int iteration_route(const mpl_ctx* h, const Dev& d, int t) {
     return sb <= h->qroute ? ROUTE_Q : ROUTE_GEMM;
 }
 
-// One outer iteration of Algorithm 1 for every active signal (kernels only).
+// One outer iteration of Algorithm 1 for every active signal, in two parts (kernels only):
+//   part 0  re-entry of the signals whose exact finish two iterations ago is done, the
+//           worst-case analysis (correlation) and the selection, which ends by building the
+//           work lists;
+//   part 1  Gram growth, master problems and residual update of the signals that took atoms.
+// Between the parts the host launches the exact finish of the signals without violators
+// (list_fin[t & 1]) on its own stream, where it overlaps part 1 and the whole next iteration.
 // pt == nullptr: no timing events (graph capture).
-static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub, cudaStream_t run,
-                                    PhaseTimer* pt, int64_t* nl) {
+static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int act_ub, cudaStream_t run,
+                               PhaseTimer* pt, int64_t* nl) {
     const int cur = t & 1;
-    const int no_grow = t >= h->max_outer;
-    const int route = iteration_route(h, d, t);
     cudaError_t e;
-    const int ph_corr = route == ROUTE_Q ? PH_QROUTE : 1;
-    cudaEvent_t e0 = pt ? pt->begin_if(ph_corr, run) : nullptr;
-    if (route == ROUTE_Q) {
-        if ((e = launch_corr_q(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-    } else if (h->precision == 1 && route == ROUTE_GEMM) {
-        // the residual writers keep the compacted BF16 rows current (d.pos); only a path
-        // without them needs the gather
-        if (!d.pos && (e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-        if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
-    } else {
-        if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-    }
-    if (t == 0 && h->qroute > 0 && (e = launch_save_beta(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-    if (pt) pt->end(ph_corr, e0, run);
-    e0 = pt ? pt->begin_if(2, run) : nullptr;
-    // without a second selection pass the selection's last CTA builds the work lists
-    const int fuse = d.ovf_list == nullptr ? 1 : 0;
-    if (t == 0 && h->warm == 2) {
-        // learned warm start: the first worst-case analysis also admits the atoms the
-        // proposal network accepts among the W largest correlations
+    if (part == 0) {
+        const int no_grow = t >= h->max_outer;
+        const int route = iteration_route(h, d, t);
+        if (t >= 2 && (e = launch_merge(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        const int ph_corr = route == ROUTE_Q ? PH_QROUTE : 1;
+        cudaEvent_t e0 = pt ? pt->begin_if(ph_corr, run) : nullptr;
+        if (route == ROUTE_Q) {
+            if ((e = launch_corr_q(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        } else if (h->precision == 1 && route == ROUTE_GEMM) {
+            // the residual writers keep the compacted BF16 rows current (d.pos); only a path
+            // without them needs the gather
+            if (!d.pos && (e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+            if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
+        } else {
+            if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        }
+        if (t == 0 && h->qroute > 0 && (e = launch_save_beta(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        if (pt) pt->end(ph_corr, e0, run);
+        e0 = pt ? pt->begin_if(2, run) : nullptr;
+        // without a second selection pass the selection's last CTA builds the work lists
+        const int fuse = d.ovf_list == nullptr ? 1 : 0;
         PropArgs pa{};
-        pa.mode = SEL_PROPOSE;
-        pa.W = std::min(h->warm_w, d.m);
-        pa.cap = h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax);
-        pa.thr = (float)h->warm_thr;
-        pa.w = h->pwb;
-        pa.rn = h->rn;
-        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, &pa, route, fuse)) != cudaSuccess) return e;
-    } else if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, nullptr, route, fuse)) != cudaSuccess) {
-        return e;
-    }
-    if (d.ovf_list) {
-        // second pass for the signals whose band overflowed: FP32 correlations of just
-        // those residuals, then their selection with the FP32 band
-        Dev d2 = d;
-        d2.act[cur] = d.ovf_list;
-        d2.cnt = d.ovf_cnt;
-        d2.ovf_list = nullptr;
-        if ((e = launch_corr_f32(d2, cur, act_ub, run, nl)) != cudaSuccess) return e;
-        if (t == 0 && h->warm == 2) {
-            PropArgs pa{};
+        const bool propose = t == 0 && h->warm == 2;
+        if (propose) {
+            // learned warm start: the first worst-case analysis also admits the atoms the
+            // proposal network accepts among the W largest correlations
             pa.mode = SEL_PROPOSE;
             pa.W = std::min(h->warm_w, d.m);
             pa.cap = h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax);
             pa.thr = (float)h->warm_thr;
             pa.w = h->pwb;
             pa.rn = h->rn;
-            if ((e = launch_select(d2, cur, no_grow, act_ub, run, nl, &pa, ROUTE_GEMM_F32)) != cudaSuccess) return e;
-        } else if ((e = launch_select(d2, cur, no_grow, act_ub, run, nl, nullptr, ROUTE_GEMM_F32)) != cudaSuccess) {
-            return e;
         }
+        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, propose ? &pa : nullptr, route, fuse)) != cudaSuccess)
+            return e;
+        if (d.ovf_list) {
+            // second pass for the signals whose band overflowed: FP32 correlations of just
+            // those residuals, then their selection with the FP32 band
+            Dev d2 = d;
+            d2.act[cur] = d.ovf_list;
+            d2.cnt = d.ovf_cnt;
+            d2.ovf_list = nullptr;
+            if ((e = launch_corr_f32(d2, cur, act_ub, run, nl)) != cudaSuccess) return e;
+            if ((e = launch_select(d2, cur, no_grow, act_ub, run, nl, propose ? &pa : nullptr, ROUTE_GEMM_F32)) !=
+                cudaSuccess)
+                return e;
+        }
+        if (!fuse && (e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
+        if (pt) pt->end(2, e0, run);
+        return cudaSuccess;
     }
-    if (!fuse && (e = launch_compact(d, cur, run, nl)) != cudaSuccess) return e;
-    if (pt) pt->end(2, e0, run);
-    // the exact finish touches only signals without violators: overlap it
-    // with the Gram growth / master problem / residual of the others
-    // bound on |S| after this iteration's growth: rho per iteration, plus what a warm start admits
     // bound on |S| after this iteration's growth: omega*rho explored atoms on top of rho per
     // earlier iteration (Algorithm 2 prunes back to rho), plus what a warm start admits
     const int scap = std::min(d.smax, t * d.rho + d.omega * d.rho + warm_additions(h, d));
-    if ((e = cudaEventRecord(h->ev_fork, run)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    e0 = pt ? pt->begin_if(4, h->side) : nullptr;
-    if ((e = launch_finish(d, act_ub, scap, h->side, nl)) != cudaSuccess) return e;
-    if (pt) pt->end(4, e0, h->side);
-    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
-    e0 = pt ? pt->begin_if(3, run) : nullptr;
+    cudaEvent_t e0 = pt ? pt->begin_if(3, run) : nullptr;
     const int qmax = (t == 0 && h->warm == 2) ? d.rho + warm_additions(h, d) : d.omega * d.rho;
     if (h->qgram) {
         if ((e = launch_gram_gather(d, act_ub, run, nl)) != cudaSuccess) return e;
@@ -665,27 +666,43 @@ static cudaError_t launch_iteration(mpl_ctx* h, const Dev& d, int t, int act_ub,
     }
     if (pt) pt->end(3, e0, run);
     e0 = pt ? pt->begin_if(5, run) : nullptr;
-    if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) return e;
+    if (apg_split(d, scap)) {
+        // blocks outside shared memory stream on a second stream while the shared-memory
+        // blocks are solved, so that neither class waits for the other's long poles
+        if ((e = cudaEventRecord(h->ev_fork2, run)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->side2, h->ev_fork2, 0)) != cudaSuccess) return e;
+        if ((e = launch_apg(d, act_ub, h->sms, scap, h->side2, nl, APG_GLOBAL)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
+        if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl, APG_SMEM)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(run, h->ev_join2, 0)) != cudaSuccess) return e;
+    } else if ((e = launch_apg(d, act_ub, h->sms, scap, run, nl)) != cudaSuccess) {
+        return e;
+    }
     if (d.omega > 1 && (e = launch_smpl_prune(d, act_ub, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(5, e0, run);
     e0 = pt ? pt->begin_if(6, run) : nullptr;
     if ((e = launch_residual(d, act_ub, run, nl)) != cudaSuccess) return e;
     if (pt) pt->end(6, e0, run);
-    return cudaStreamWaitEvent(run, h->ev_join, 0);
+    return cudaSuccess;
 }
 
-// Captured iteration for (p, t): iterations past the point where the
-// active-set bound saturates share one graph per parity.
-static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, double tol, cudaStream_t run,
+// Bound on |S| of the signals an iteration sends to the exact finish.
+static int finish_scap(const mpl_ctx* h, const Dev& d, int t) {
+    return std::min(d.smax, t * d.rho + d.omega * d.rho + warm_additions(h, d));
+}
+
+// Captured part of iteration (p, t): iterations past the point where the active-set bound
+// saturates share one graph per parity and part.
+static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int part, int p, double tol, cudaStream_t run,
                                    size_t* out, int64_t* nl) {
     const int tsat = (d.smax + d.rho - 1) / d.rho;  // beyond this the active-set bound is smax
-    const int tk = std::min(t, tsat + 1);
+    const int tk = std::min(t, tsat + 2);
     const int par = t & 1, nog = t >= h->max_outer ? 1 : 0, prof = h->profile ? 1 : 0;
     const int route = iteration_route(h, d, t) + 4 * (t == 0 && h->qroute > 0 ? 1 : 0);
     for (size_t gi = 0; gi < h->graphs.size(); ++gi) {
         const auto& g = h->graphs[gi];
         if (g.p == p && g.tk == tk && g.par == par && g.nog == nog && g.prof == prof && g.route == route &&
-            g.tol == tol) {
+            g.part == part && g.tol == tol) {
             *out = gi;
             return cudaSuccess;
         }
@@ -695,7 +712,7 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, doubl
     int64_t cnt = 0;
     PhaseTimer gpt{h, run, {}, 0, true};
     gpt.only_a = -1;  // every phase (the profiling pass is timed apart from the reported one)
-    cudaError_t el = launch_iteration(h, d, t, p, run, prof ? &gpt : nullptr, &cnt);
+    cudaError_t el = launch_part(h, d, t, part, p, run, prof ? &gpt : nullptr, &cnt);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(run, &graph);
     if (el != cudaSuccess) {
@@ -707,10 +724,26 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int p, doubl
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
-    h->graphs.push_back({p, tk, par, nog, prof, route, tol, cnt, exec, gpt.marks});
+    h->graphs.push_back({p, tk, par, nog, prof, route, part, tol, cnt, exec, gpt.marks});
     *out = h->graphs.size() - 1;
     (void)nl;
     return cudaSuccess;
+}
+
+// The library's streams and events, once per handle.  The outer-iteration chain is the
+// critical path: its blocks go first when an SM frees up; the exact finishes of converged
+// signals (two streams, by iteration parity) fill in behind it.
+static mpl_status_t ensure_streams(mpl_ctx* h) {
+    if (h->side) return MPL_OK;
+    int prio_lo = 0, prio_hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
+    CK(cudaStreamCreateWithPriority(&h->side_odd, cudaStreamNonBlocking, prio_lo));
+    CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
+    CK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, prio_hi));
+    cudaEvent_t* evs[] = {&h->ev_fork2, &h->ev_join2, &h->ev_in, &h->ev_out, &h->ev_sel, &h->ev_fin[0], &h->ev_fin[1]};
+    for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return MPL_OK;
 }
 
 mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lambda, float* X, double tol,
@@ -728,17 +761,9 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     if (ws != MPL_OK) return ws;
     const int n = h->n, m = h->m;
     int64_t nl = 0;
-    if (!h->side) {
-        // the outer-iteration chain is the critical path: its blocks go first when an SM
-        // frees up; the exact finishes of converged signals fill in behind it
-        int prio_lo = 0, prio_hi = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
-        CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
-        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    {
+        const mpl_status_t ss = ensure_streams(h);
+        if (ss != MPL_OK) return ss;
     }
     // all work runs on the library's stream, ordered after the caller's stream
     const bool graph = h->use_graph != 0;
@@ -783,7 +808,6 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         CK(corr_bf16_prepare(n, m, h->cap_p, h->A16, d.R16c, h->tmap));
         h->tmap_p = h->cap_p;
     }
-    const float* lamd = h->lamint;
     if (h->qroute > 0) {
         mpl_status_t qs = ensure_identity_route(h, p, st, &nl);
         if (qs != MPL_OK) return qs;
@@ -799,26 +823,49 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     PhaseTimer pt{h, st, {}, 0};
     cudaEvent_t t_all = pt.begin();
     CK(launch_init(d, st, &nl));
-    int act_ub = p;
-    const int hard_cap = h->max_outer + 2 * FIN_MAX_FAILS + 8;
+    // live: an upper bound on the signals not yet done (active, or in a finish of one of the
+    // last two iterations, whose re-entry is still to come); grids are sized by it outside
+    // graph mode (captured graphs are sized for p)
+    int live = p;
+    // every finish hands its work back through reent[], and each waits for the finish of the
+    // iteration before last (same parity), so a retry takes three iterations
+    const int hard_cap = h->max_outer + 3 * FIN_MAX_FAILS + 10;
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
     double graph_phase[15] = {0};
-    for (int t = 0; act_ub > 0 && t < hard_cap; ++t) {
-        if (graph) {
-            size_t gi = 0;
-            CK(iteration_graph(h, d, t, p, tol, st, &gi, &nl));
-            CK(cudaGraphLaunch(h->graphs[gi].exec, st));
-            nl += h->graphs[gi].kernels;
-            window.push_back(gi);
-        } else {
-            CK(launch_iteration(h, d, t, act_ub, st, &pt, &nl));
+    int t = 0;
+    for (; live > 0 && t < hard_cap; ++t) {
+        const int par = t & 1;
+        cudaStream_t fin_st = par ? h->side_odd : h->side;
+        // the finish of iteration t - 2 (same parity) is done before its signals re-enter
+        CK(cudaStreamWaitEvent(st, h->ev_fin[par], 0));
+        for (int part = 0; part < 2; ++part) {
+            if (graph) {
+                size_t gi = 0;
+                CK(iteration_graph(h, d, t, part, p, tol, st, &gi, &nl));
+                CK(cudaGraphLaunch(h->graphs[gi].exec, st));
+                nl += h->graphs[gi].kernels;
+                window.push_back(gi);
+            } else {
+                CK(launch_part(h, d, t, part, live, st, &pt, &nl));
+            }
+            if (part == 0) {
+                // the exact finish of the signals without violators, beside part 1 and the
+                // next iteration
+                CK(cudaEventRecord(h->ev_sel, st));
+                CK(cudaStreamWaitEvent(fin_st, h->ev_sel, 0));
+                cudaEvent_t f0 = pt.begin(fin_st);
+                CK(launch_finish(d, par, graph ? p : live, finish_scap(h, d, t), fin_st, &nl));
+                pt.end(4, f0, fin_st);
+                CK(cudaEventRecord(h->ev_fin[par], fin_st));
+            }
         }
         const bool last = t + 1 >= hard_cap;
         if ((t + 1) % h->sync_every == 0 || last) {
             CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
-            act_ub = h->cnt_h->act_n[(t & 1) ^ 1];
+            // active next iteration, plus the signals of the last two finishes
+            live = h->cnt_h->act_n[(t & 1) ^ 1] + h->cnt_h->fin_par[0] + h->cnt_h->fin_par[1];
             if (graph && h->profile) {
                 for (size_t gi : window)
                     for (auto& mk : h->graphs[gi].marks) {
@@ -830,6 +877,9 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
             window.clear();
         }
     }
+    // the last finishes, then the results
+    CK(cudaStreamWaitEvent(st, h->ev_fin[0], 0));
+    CK(cudaStreamWaitEvent(st, h->ev_fin[1], 0));
     CK(cudaMemsetAsync(Xd, 0, (size_t)m * p * sizeof(float), st));
     CK(launch_scatter(d, Xd, nullptr, st, &nl));
     pt.end(0, t_all);
@@ -845,10 +895,11 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     }
     CK(launch_pack_stats(d, h->stats_d, st, &nl));
     CK(cudaMemcpyAsync(h->stats_pin, h->stats_d, (size_t)p * sizeof(mpl_signal_stats_t), cudaMemcpyDeviceToHost, st));
-    (void)lamd;
+    CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->ev_out, st));
     CK(cudaStreamWaitEvent(caller, h->ev_out, 0));
     CK(cudaStreamSynchronize(st));
+    if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
     pt.collect();
     for (int k = 1; k < 7; ++k) h->phase_ms[k] += graph_phase[k];
     h->phase_ms[PH_QROUTE] += graph_phase[PH_QROUTE];
@@ -1006,17 +1057,9 @@ static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const floa
 
 static mpl_status_t prop_setup(mpl_ctx* h) {
     CK(cudaSetDevice(h->dev));
-    if (!h->side) {
-        // the outer-iteration chain is the critical path: its blocks go first when an SM
-        // frees up; the exact finishes of converged signals fill in behind it
-        int prio_lo = 0, prio_hi = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
-        CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
-        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    {
+        const mpl_status_t ss = ensure_streams(h);
+        if (ss != MPL_OK) return ss;
     }
     if (h->precision == 1) {
         int64_t nl = 0;

@@ -52,9 +52,13 @@ enum SigState : int {
 struct Counters {
     int act_n[2];    // active-list lengths (double-buffered by outer-iteration parity)
     int grow_n;      // signals that took new atoms
-    int fin_n;       // signals sent to the exact finish
+    int fin_n;       // signals sent to the exact finish (this iteration)
+    int fin_par[2];  // ... by outer-iteration parity (a finish runs while the next iteration does)
+    int reent_n[2];  // finished signals waiting to re-enter the active list, by the parity of
+                     // the iteration whose finish they left (merged two iterations later)
     int apg_n;       // signals in the master-problem list (grow + failed finishes)
     int apg_head;    // work-queue head of the persistent master-problem kernel
+    int apg_head2;   // head of its second queue (blocks streamed from global memory)
     int err;         // first device-side error code (0 = none)
     int sel_fallback;// candidate-buffer overflows in the selection
     unsigned long long cols;  // signal columns processed by the correlation (all iterations)
@@ -137,7 +141,8 @@ struct Dev {
     int* ovf_list;               // signals whose candidate band overflowed (second pass), or null
     Counters* ovf_cnt;           // its length in act_n[parity]
     int* list_grow;              // signals with new atoms
-    int* list_fin;               // signals sent to the exact finish
+    int* list_fin[2];            // signals sent to the exact finish, by outer-iteration parity
+    int* reent[2];               // finished signals to merge back into the active list, by parity
     int* list_apg;               // master-problem work list
     Counters* cnt;
     __device__ const int* act_of(int c) const { return act[c]; }
@@ -191,8 +196,19 @@ cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl);
 // Gram growth gathered from Q (MPL_OPT_QGRAM): same outputs, bit for bit, as launch_gram.
 cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
-cudaError_t launch_finish(const Dev& d, int ub, int scap, cudaStream_t s, int64_t* nl);
-cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl);
+// The exact finish of the signals the selection of an iteration with parity cur sent to it
+// (list_fin[cur]); each finished signal that is not done joins reent[cur].
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl);
+// Append reent[cur] to the active list of an iteration with parity cur (rows for the GEMM
+// included); the finishes that filled it must be complete.
+cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl);
+// Master-problem launches: every signal of the work list, or only those whose Gram block fits
+// shared memory, or only those streamed from global memory.
+enum ApgClass : int { APG_ALL = 0, APG_SMEM = 1, APG_GLOBAL = 2 };
+cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl, int cls = APG_ALL);
+// True when blocks up to the bound vcap may outgrow shared memory: the caller then runs an
+// APG_SMEM and an APG_GLOBAL launch (concurrently) instead of one APG_ALL launch.
+bool apg_split(const Dev& d, int vcap);
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 // Algorithm 2: keep the rho explored atoms with the largest |u| (compacts S, x_S, h, G).
 cudaError_t launch_smpl_prune(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
@@ -236,6 +252,8 @@ constexpr size_t FIN_SMEM_MAX = 225 * 1024;       // the most one finish CTA tak
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_THREADS_WIDE = 512;  // one finish CTA per SM (large active sets)
 constexpr int FIN_MAX_PIVOTS = 16;
+constexpr int FIN_CG_MAXIT = 60;  // CG iterations per solve before the finish falls back to a factor
+constexpr int FIN_CG_MIN_S = 128; // active sets above this size (with a factor outside shared memory) use CG
 constexpr int FIN_MAX_FAILS = 6;
 
 }  // namespace mpl

@@ -70,7 +70,7 @@ __global__ void k_noalloc_prep(Counters* cnt, int* act, int p) {
     if (i == 0) {
         cnt->act_n[0] = p;
         cnt->act_n[1] = 0;
-        cnt->grow_n = cnt->fin_n = cnt->apg_n = cnt->apg_head = 0;
+        cnt->grow_n = cnt->fin_n = cnt->apg_n = cnt->apg_head = cnt->apg_head2 = 0;
         cnt->err = 0;
         cnt->sel_fallback = 0;
     }

@@ -385,6 +385,100 @@ __device__ bool fast_kth(const unsigned* keys, int m, int kth, unsigned tmax, Se
     return true;
 }
 
+// fast_kth for a score row in global memory (m above the row cache): thread t owns atoms
+// 4 (t + u nt) + e (e < 4, u = 0, 1, ...), the cached layout extended to any m.  One scan
+// (float4 loads when the row is 16-byte aligned) gives each thread's largest key; the rest
+// is fast_kth's bound T, list and rank, with the list's owners reading their atoms again.
+// Returns false (radix passes) in the same cases.
+template <typename K>
+__device__ bool fast_kth_row(K key, const float* row, const uint32_t* msk, int m, int kth, SelSmem& sh,
+                             unsigned* kkey, unsigned* tlo, unsigned* below) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int jw = (kth + nw - 1) / nw;
+    if (jw > 32) return false;
+    unsigned tmax = 0;
+    int nf = 0;
+    if ((m & 3) == 0) {
+        for (int j0 = 4 * tid; j0 < m; j0 += 16 * nt) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 4 * u * nt;
+                v[u] = j < m ? __ldcg(reinterpret_cast<const float4*>(row + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + 4 * u * nt;
+                if (j < m) {
+                    const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) tmax = max(tmax, key_of(f, msk, j + e, e, &nf));
+                }
+            }
+        }
+    } else {
+        for (int j0 = 4 * tid; j0 < m; j0 += 4 * nt)
+            for (int e = 0; e < 4 && j0 + e < m; ++e) tmax = max(tmax, key(j0 + e, &nf));
+    }
+    if (nf) sh.nonfinite = 1;
+    unsigned v = tmax;
+    if (jw == 1) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    } else {
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const unsigned o = __shfl_xor_sync(0xffffffffu, v, j);
+                const bool desc = (lane & k) == 0, lower = (lane & j) == 0;
+                v = (desc == lower) ? max(v, o) : min(v, o);
+            }
+        }
+        v = __shfl_sync(0xffffffffu, v, jw - 1);
+    }
+    if (tid == 0) { sh.lcnt = 0; sh.outmax = 0; }
+    if (lane == 0) sh.wsum[warp] = v;
+    __syncthreads();
+    unsigned T = lane < nw ? sh.wsum[lane] : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) T = min(T, __shfl_xor_sync(0xffffffffu, T, o));
+    if (T == 0u) return false;
+    unsigned omax = tmax;
+    if (tmax >= T) {
+        omax = 0;
+        for (int j0 = 4 * tid; j0 < m; j0 += 4 * nt)
+            for (int e = 0; e < 4 && j0 + e < m; ++e) {
+                const int j = j0 + e;
+                const unsigned kj = key(j, &nf);
+                if (kj >= T) {
+                    const unsigned pos = atomicAdd(&sh.lcnt, 1u);
+                    if (pos < (unsigned)nt) sh.key[pos] = ((unsigned long long)kj << 32) | (unsigned)j;
+                } else {
+                    omax = max(omax, kj);
+                }
+            }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    if (lane == 0 && omax) atomicMax(&sh.outmax, omax);
+    __syncthreads();
+    const unsigned c = sh.lcnt;
+    if (c > (unsigned)nt) return false;
+    if (tid < (int)c) {
+        const unsigned long long e = sh.key[tid];
+        unsigned above = 0;
+#pragma unroll 8
+        for (unsigned u = 0; u < c; ++u) above += sh.key[u] > e ? 1u : 0u;
+        if (above == (unsigned)kth - 1u) sh.bin = (unsigned)(e >> 32);
+    }
+    __syncthreads();
+    *kkey = sh.bin;
+    *tlo = T;
+    *below = sh.outmax;
+    return true;
+}
+
 // The band { j : key >= tkey } from the list of fast_kth (tkey >= its T): into
 // sh.idx, with the largest key left outside (list keys below tkey, or below T).
 __device__ unsigned collect_list(unsigned tkey, unsigned below, SelSmem& sh) {
@@ -582,7 +676,8 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         const CachedKeys ck{reinterpret_cast<const unsigned*>(sh.row)};
         const RowKeys rk{row, msk};
         unsigned kkey = 0, tlo = 0, below = 0;
-        const bool listed = cache && fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);
+        const bool listed = cache ? fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below)
+                                  : fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below);
         if (!listed) kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_VAL(7, listed ? 1 : 0);
         ST_VAL(8, listed ? sh.lcnt : 0);
@@ -855,7 +950,9 @@ __device__ void compact_body(const Dev& d, int cur) {
         const int k = c0 + tid;
         int sig = -1, st = ST_DONE;
         if (k < nact) { sig = __ldcg(act + k); st = __ldcg(d.state + sig); }
-        const int f[3] = {st == ST_GROW || st == ST_REFINE, st == ST_FINALIZE, st != ST_DONE};
+        // the next active list: signals with a master problem to solve; the ones sent to the
+        // exact finish leave it and come back through reent[] once their finish is done
+        const int f[3] = {st == ST_GROW || st == ST_REFINE, st == ST_FINALIZE, st == ST_GROW || st == ST_REFINE};
         if (st == ST_REFINE) d.state[sig] = ST_GROW;  // master problem again, no new atoms
         int pre[3];
         const unsigned lt = (1u << lane) - 1u;
@@ -883,7 +980,7 @@ __device__ void compact_body(const Dev& d, int cur) {
             const int off = base[q] + (warp ? wsum[q][warp - 1] : 0) + pre[q];
             if (f[q]) {
                 if (q == 0) { d.list_grow[off] = sig; d.list_apg[off] = sig; }
-                else if (q == 1) d.list_fin[off] = sig;
+                else if (q == 1) d.list_fin[cur][off] = sig;
                 else {
                     nxt[off] = sig;
                     if (d.pos) d.pos[sig] = off;  // its GEMM row next iteration
@@ -900,8 +997,10 @@ __device__ void compact_body(const Dev& d, int cur) {
         d.cnt->grow_n = base[0];
         d.cnt->apg_n = base[0];
         d.cnt->fin_n = base[1];
+        d.cnt->fin_par[cur] = base[1];
         d.cnt->act_n[cur ^ 1] = base[2];
         d.cnt->apg_head = 0;
+        d.cnt->apg_head2 = 0;
     }
 }
 

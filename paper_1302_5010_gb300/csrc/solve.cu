@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         if (i == 0) {
             d.cnt->act_n[0] = d.p;
             d.cnt->act_n[1] = 0;
-            d.cnt->grow_n = d.cnt->fin_n = d.cnt->apg_n = d.cnt->apg_head = 0;
+            d.cnt->grow_n = d.cnt->fin_n = d.cnt->apg_n = d.cnt->apg_head = d.cnt->apg_head2 = 0;
             d.cnt->err = 0;
             d.cnt->sel_fallback = 0;
             d.cnt->cols = 0ull;
@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->qcols = 0ull;
             d.cnt->sel_done = 0;
             d.cnt->apg_elems = d.cnt->apg_gl_elems = 0ull;
+            d.cnt->fin_par[0] = d.cnt->fin_par[1] = 0;
+            d.cnt->reent_n[0] = d.cnt->reent_n[1] = 0;
             d.cnt->res_bytes = d.cnt->gram_bytes = 0ull;
         }
     }
@@ -449,6 +451,69 @@ __device__ __forceinline__ float gram_mv(const float* __restrict__ G, int ld, in
     return part;
 }
 
+// y = G x for a block in global memory (leading dimension ld, row r = column r by
+// symmetry): a warp per pair of rows, each row's s entries read as float4 slices (four per
+// lane in flight for each of the two rows) when ld allows, fixed butterfly per row.  x is
+// zero from s up to the next multiple of 4.  With h != nullptr lane 0 also returns its
+// rows' share of the restricted objective, lambda |x_r| + x_r (y_r / 2 - h_r).
+__device__ __forceinline__ float gram_mv_stream(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                                float* __restrict__ y, const float* h = nullptr, float lam = 0.f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool vec = (ld & 3) == 0;
+    float part = 0.f;
+    for (int r = 2 * warp; r < s; r += 2 * nw) {
+        const int rb = r + 1 < s ? r + 1 : r;
+        const float* ga = G + (size_t)r * ld;
+        const float* gb = G + (size_t)rb * ld;
+        float sa = 0.f, sb = 0.f;
+        for (int c0 = 4 * lane; c0 < s; c0 += 512) {
+            float4 a4[4], b4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    if (vec) {
+                        a4[u] = __ldg(reinterpret_cast<const float4*>(ga + c));
+                        b4[u] = __ldg(reinterpret_cast<const float4*>(gb + c));
+                    } else {
+                        a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
+                        b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
+                    }
+                } else {
+                    a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    const float4 xv = *reinterpret_cast<const float4*>(x + c);
+                    sa = fmaf(a4[u].x, xv.x, sa); sa = fmaf(a4[u].y, xv.y, sa);
+                    sa = fmaf(a4[u].z, xv.z, sa); sa = fmaf(a4[u].w, xv.w, sa);
+                    sb = fmaf(b4[u].x, xv.x, sb); sb = fmaf(b4[u].y, xv.y, sb);
+                    sb = fmaf(b4[u].z, xv.z, sb); sb = fmaf(b4[u].w, xv.w, sb);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (lane == 0) {
+            y[r] = sa;
+            if (h) part += lam * fabsf(x[r]) + x[r] * (0.5f * sa - h[r]);
+            if (r + 1 < s) {
+                y[r + 1] = sb;
+                if (h) part += lam * fabsf(x[r + 1]) + x[r + 1] * (0.5f * sb - h[r + 1]);
+            }
+        }
+    }
+    return part;
+}
+
 struct ApgVec {
     float *u, *up, *Gu, *Gup, *h, *v;
     float red[96];
@@ -471,7 +536,10 @@ __device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* 
     for (int w = 0; w < nw; ++w) { a += red[w]; b += red[32 + w]; c += red[64 + w]; }
 }
 
-__global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) {
+// STREAM: the APG_GLOBAL launch (every block streamed from global memory by warp rows);
+// otherwise blocks in shared memory (or, past gcap, read by the thread-per-row product).
+template <bool STREAM>
+__global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap, int cls) {
     pdl_enter();
     extern __shared__ __align__(16) float gsm[];
     __shared__ ApgVec sh;
@@ -482,14 +550,20 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
         sh.u = base; sh.up = base + vcap; sh.Gu = base + 2 * vcap;
         sh.Gup = base + 3 * vcap; sh.h = base + 4 * vcap; sh.v = base + 5 * vcap;
     }
+    int* head = cls == APG_GLOBAL ? &d.cnt->apg_head2 : &d.cnt->apg_head;
     for (;;) {
-        if (tid == 0) sh.item = atomicAdd(&d.cnt->apg_head, 1);
+        if (tid == 0) sh.item = atomicAdd(head, 1);
         __syncthreads();
         const int it = sh.item;
         if (it >= d.cnt->apg_n) break;
         const int i = d.list_apg[it];
-        AT_BEGIN
         const int s = d.ssize[i];
+        // a class launch takes only its own signals (the other launch takes the rest)
+        if ((cls == APG_SMEM && s > gcap) || (cls == APG_GLOBAL && s <= APG_SMEM_S)) {
+            __syncthreads();  // every thread has read sh.item before thread 0 takes the next
+            continue;
+        }
+        AT_BEGIN
         const float lam = d.lam[i];
         const float eps = d.eps[i];
         const float* Gg = d.G + (size_t)i * smax * smax;
@@ -523,25 +597,41 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap) 
                 }
             }
         }
-        // the block's matrix-vector product: split rows while the block is small
+        // the block's matrix-vector product: split rows while the block is small, warp rows
+        // streamed as float4 slices from global memory when it is not in shared memory
         auto mv = [&](const float* x, float* y) {
-            if (insm && s <= 64) gram_mv_split<4>(G, ld, s, x, y);
-            else if (insm && s <= 128) gram_mv_split<2>(G, ld, s, x, y);
-            else gram_mv(G, ld, s, x, y);
+            if constexpr (STREAM) {
+                gram_mv_stream(G, ld, s, x, y);
+            } else {
+                if (insm && s <= 64) gram_mv_split<4>(G, ld, s, x, y);
+                else if (insm && s <= 128) gram_mv_split<2>(G, ld, s, x, y);
+                else gram_mv(G, ld, s, x, y);
+            }
         };
         // y = G x and this thread's share of the restricted objective at x
         auto mvF = [&](const float* x, float* y) -> float {
-            if (insm && s <= 64) return gram_mv_split<4>(G, ld, s, x, y, sh.h, lam);
-            if (insm && s <= 128) return gram_mv_split<2>(G, ld, s, x, y, sh.h, lam);
-            return gram_mv(G, ld, s, x, y, sh.h, lam);
+            if constexpr (STREAM) {
+                return gram_mv_stream(G, ld, s, x, y, sh.h, lam);
+            } else {
+                if (insm && s <= 64) return gram_mv_split<4>(G, ld, s, x, y, sh.h, lam);
+                if (insm && s <= 128) return gram_mv_split<2>(G, ld, s, x, y, sh.h, lam);
+                return gram_mv(G, ld, s, x, y, sh.h, lam);
+            }
         };
         float* xi = d.xS + (size_t)i * smax;
         float* ritz = d.ritz + (size_t)i * smax;
         const int prev = s - d.snew[i];  // ritz vector valid for the first `prev` entries
-        for (int r = tid; r < s; r += blockDim.x) {
-            sh.u[r] = xi[r];
-            sh.h[r] = d.h[(size_t)i * smax + r];
-            sh.v[r] = (r < prev && d.outer[i] > 1) ? ritz[r] : 1.f;
+        // (entries from s up to the next multiple of 4 are zero: the streamed product reads
+        // its operand as float4 slices)
+        const int s4 = (s + 3) & ~3;
+        for (int r = tid; r < s4; r += blockDim.x) {
+            const bool in = r < s;
+            sh.u[r] = in ? xi[r] : 0.f;
+            sh.h[r] = in ? d.h[(size_t)i * smax + r] : 0.f;
+            sh.v[r] = !in ? 0.f : ((r < prev && d.outer[i] > 1) ? ritz[r] : 1.f);
+            sh.up[r] = 0.f;
+            sh.Gu[r] = 0.f;
+            sh.Gup[r] = 0.f;
         }
         __syncthreads();
         AT_ADD(0);
@@ -1077,25 +1167,42 @@ cudaError_t prepare_apg() {
     static bool attr = false;
     if (attr) return cudaSuccess;
     const int mx = (int)((apg_area(APG_SMEM_S) + 6 * 1024) * sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(k_apg, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = cudaFuncSetAttribute(k_apg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
-cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl) {
-    if (ub <= 0) return cudaSuccess;
+// Vector stride of the master problem for a bound vcap on |S|: a multiple of 32 (and so of
+// 4, the streamed product's float4 slices), at least the bound, at most the capacity rounded
+// up to 4.
+static int apg_vcap(const Dev& d, int vcap) {
     vcap = ((vcap + 31) / 32) * 32;
-    if (vcap > d.smax) vcap = d.smax;
-    const int gcap = vcap < APG_SMEM_S ? vcap : APG_SMEM_S;
-    const size_t dyn = (apg_area(gcap) + 6 * (size_t)vcap) * sizeof(float);
+    const int cap4 = (d.smax + 3) & ~3;
+    return vcap < cap4 ? vcap : cap4;
+}
+
+bool apg_split(const Dev& d, int vcap) { return apg_vcap(d, vcap) > APG_SMEM_S; }
+
+cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, int64_t* nl, int cls) {
+    if (ub <= 0) return cudaSuccess;
+    vcap = apg_vcap(d, vcap);
     cudaError_t ep = prepare_apg();
     if (ep != cudaSuccess) return ep;
+    // APG_ALL: one launch, blocks up to the bound (at most APG_SMEM_S) in shared memory;
+    // APG_SMEM: the blocks that fit shared memory; APG_GLOBAL: the others, without the block
+    // area, so that several CTAs per SM stream their blocks from L2/HBM
+    const int gcap = cls == APG_GLOBAL ? 0 : (vcap < APG_SMEM_S ? vcap : APG_SMEM_S);
+    const size_t dyn = (apg_area(gcap) + 6 * (size_t)vcap) * sizeof(float);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apg, APG_THREADS, dyn);
+    const bool stream = cls == APG_GLOBAL;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream ? k_apg<true> : k_apg<false>,
+                                                                  APG_THREADS, dyn);
     if (e != cudaSuccess) return e;
     int grid = sms * (per_sm > 0 ? per_sm : 1);
     if (grid > ub) grid = ub;
-    e = launch_chain(k_apg, dim3(grid), dim3(APG_THREADS), dyn, s, d, vcap, gcap);
+    e = stream ? launch_chain(k_apg<true>, dim3(grid), dim3(APG_THREADS), dyn, s, d, vcap, gcap, cls)
+               : launch_chain(k_apg<false>, dim3(grid), dim3(APG_THREADS), dyn, s, d, vcap, gcap, cls);
     if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
@@ -1110,6 +1217,47 @@ cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
 }
 
 // Per-signal statistics packed on the device into the host struct layout (one copy back).
+// ------------------------------------------------------------------ re-entry
+// Finished signals (reent[cur]) go back to the end of the active list of this iteration,
+// with their rows in the GEMM's compacted BF16 residual (the finish wrote the per-signal
+// copy); the counters are updated by k_merge_count once every row is in place.
+__global__ void __launch_bounds__(256) k_merge(Dev d, int cur) {
+    pdl_enter();
+    const int base = d.cnt->act_n[cur], cnt = d.cnt->reent_n[cur], n = d.n;
+    for (int b = blockIdx.x; b < cnt; b += gridDim.x) {
+        const int i = d.reent[cur][b];
+        const int row = base + b;
+        if (threadIdx.x == 0) {
+            d.act[cur][row] = i;
+            if (d.pos) d.pos[i] = row;
+        }
+        if (d.pos) {
+            const __nv_bfloat16* src = d.R16 + (size_t)i * n;
+            __nv_bfloat16* dst = d.R16c + (size_t)row * n;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+        }
+    }
+}
+
+__global__ void k_merge_count(Dev d, int cur) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        d.cnt->act_n[cur] += d.cnt->reent_n[cur];
+        d.cnt->reent_n[cur] = 0;
+    }
+}
+
+cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl) {
+    if (ub <= 0) return cudaSuccess;
+    const int grid = ub < 608 ? ub : 608;
+    cudaError_t e = launch_chain(k_merge, dim3(grid), dim3(256), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
+    e = launch_chain(k_merge_count, dim3(1), dim3(32), 0, s, d, cur);
+    if (e != cudaSuccess) return e;
+    *nl += 2;
+    return cudaGetLastError();
+}
+
 __global__ void k_pack_stats(Dev d, mpl_signal_stats_t* out) {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
