@@ -66,7 +66,10 @@ typedef enum {
     MPL_OPT_GRAPH = 9,      /* 1: each outer iteration is replayed from a captured CUDA graph
                                (captured on first use per batch size and iteration). default 1 */
     MPL_OPT_WARM_CANDIDATES = 10, /* W: atoms per signal scored by the proposal network (the W
-                                     largest |a_j^T b| of the first correlation). default 64 */
+                                     largest |a_j^T b| of the first correlation; the rho largest
+                                     violators join S anyway, the network picks among the
+                                     rest, so the warm start only acts when W > rho * omega).
+                                     1..64, default 64 */
     MPL_OPT_WARM_MAX = 11,        /* most atoms a proposal adds to a signal's set. default 3 rho */
     MPL_OPT_WARM_THRESHOLD = 12,  /* accept a candidate when its logit exceeds this. default -1 */
     MPL_OPT_QROUTE = 13,          /* identity route of the worst-case analysis (Sec. 3, eq.

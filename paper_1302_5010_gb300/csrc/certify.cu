@@ -1329,6 +1329,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
     float* rh = sh.rh;
     float* rl = sh.rl;
 
+    if (MPL_OOB(s > smax || i < 0 || i >= d.p, 601)) return;
     for (int a = tid; a < s; a += nt) {
         const float v = xS[a];
         sh.x[a] = (double)v;

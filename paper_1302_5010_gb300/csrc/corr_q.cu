@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     __shared__ __align__(16) float hbuf[GQ_BUF];
     if (threadIdx.x == 0)  // s q entries of Q read, 2 s q of G written, q atoms and b read, q of h written
         atomicAdd(&d.cnt->gram_bytes, 12ull * s * q + 4ull * n * (q + 1) + 4ull * q);
+    if (MPL_OOB(s > smax || s > 1024 || q > s, 401)) return;
     for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
     __syncthreads();
     // new columns (and, by symmetry, rows) of G_SS: eight independent loads per thread
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
                         const int e = e0 + u * blockDim.x;
                         if (e < tot) {
                             const int r = e / v4, k4 = e - r * v4;
+                            if (MPL_OOB(r * ks + 4 * k4 + 3 >= GQ_BUF, 402)) continue;
                             *reinterpret_cast<float4*>(hbuf + r * ks + 4 * k4) = v[u];
                         }
                     }

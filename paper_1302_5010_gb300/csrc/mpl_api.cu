@@ -26,6 +26,8 @@
 
 using namespace mpl;
 
+
+
 namespace {
 
 // Option key for phase timing (not part of the public enum).
@@ -80,7 +82,7 @@ struct mpl_ctx {
     float* pacc = nullptr;  // [0] loss sum, [1] (int) live examples
     float* rn = nullptr;    // ||A^T a_j|| estimates (m)
     bool prop_ready = false, rn_ready = false;
-    int warm_w = 64, warm_max = -1;  // -1: 3 rho
+    int warm_w = -1, warm_max = -1;  // -1: WARM_W_MAX; -1: 3 rho
     double warm_thr = -1.0;
     double eps_in = 1e-4;
     // identity route (eq. batchQ): taken at outer iterations whose bound on |S| is <= qroute
@@ -175,6 +177,10 @@ cudaError_t alloc(mpl_ctx* h, T** out, size_t count) {
 }
 
 int default_smax(const mpl_ctx* h) { return std::min(std::min(h->n, h->m), 256); }
+
+// Candidates per signal the proposal network scores: the W largest correlations of the first
+// worst-case analysis (MPL_OPT_WARM_CANDIDATES, at most WARM_W_MAX).
+int warm_candidates(const mpl_ctx* h) { return h->warm_w > 0 ? h->warm_w : WARM_W_MAX; }
 
 mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     const int smax = h->smax > 0 ? h->smax : default_smax(h);
@@ -473,7 +479,7 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             h->warm = (int)v;
             return MPL_OK;
         case MPL_OPT_WARM_CANDIDATES:
-            if (v < 1 || v > SEL_THREADS) return MPL_ERR_ARG;
+            if (v < 1 || v > WARM_W_MAX) return MPL_ERR_ARG;
             h->warm_w = (int)v;
             return MPL_OK;
         case MPL_OPT_WARM_MAX:
@@ -527,7 +533,7 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_SYNC_EVERY: *v = h->sync_every; return MPL_OK;
         case OPT_PROFILE: *v = h->profile; return MPL_OK;
         case MPL_OPT_GRAPH: *v = h->use_graph; return MPL_OK;
-        case MPL_OPT_WARM_CANDIDATES: *v = h->warm_w; return MPL_OK;
+        case MPL_OPT_WARM_CANDIDATES: *v = warm_candidates(h); return MPL_OK;
         case MPL_OPT_WARM_MAX: *v = h->warm_max; return MPL_OK;
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
@@ -576,9 +582,16 @@ static mpl_status_t ensure_identity_route(mpl_ctx* h, int p, cudaStream_t st, in
     return MPL_OK;
 }
 
+// The learned warm start runs at the first iteration when a proposal network is loaded and
+// it can add atoms beyond MPL's own rho largest violators (W > rho omega: the network picks
+// among the candidates below them).
+static bool warm_active(const mpl_ctx* h, const Dev& d) {
+    return h->warm == 2 && warm_candidates(h) > d.rho * d.omega;
+}
+
 // Atoms a warm start may add at the first iteration (bounds |S| on the host).
 static int warm_additions(const mpl_ctx* h, const Dev& d) {
-    return h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax)) : 0;
+    return warm_active(h, d) ? (h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax)) : 0;
 }
 
 // Correlation route of outer iteration t.  With the identity route enabled, the
@@ -625,12 +638,12 @@ static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int ac
         // without a second selection pass the selection's last CTA builds the work lists
         const int fuse = d.ovf_list == nullptr ? 1 : 0;
         PropArgs pa{};
-        const bool propose = t == 0 && h->warm == 2;
+        const bool propose = t == 0 && warm_active(h, d);
         if (propose) {
             // learned warm start: the first worst-case analysis also admits the atoms the
             // proposal network accepts among the W largest correlations
             pa.mode = SEL_PROPOSE;
-            pa.W = std::min(h->warm_w, d.m);
+            pa.W = std::min(warm_candidates(h), d.m);
             pa.cap = h->warm_max > 0 ? h->warm_max : std::min(3 * d.rho, d.smax);
             pa.thr = (float)h->warm_thr;
             pa.w = h->pwb;
@@ -658,7 +671,7 @@ static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int ac
     // earlier iteration (Algorithm 2 prunes back to rho), plus what a warm start admits
     const int scap = std::min(d.smax, t * d.rho + d.omega * d.rho + warm_additions(h, d));
     cudaEvent_t e0 = pt ? pt->begin_if(3, run) : nullptr;
-    const int qmax = (t == 0 && h->warm == 2) ? d.rho + warm_additions(h, d) : d.omega * d.rho;
+    const int qmax = (t == 0 && warm_active(h, d)) ? d.rho + warm_additions(h, d) : d.omega * d.rho;
     if (h->qgram) {
         if ((e = launch_gram_gather(d, act_ub, run, nl)) != cudaSuccess) return e;
     } else if ((e = launch_gram(d, act_ub, qmax, run, nl)) != cudaSuccess) {
@@ -863,6 +876,11 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         if ((t + 1) % h->sync_every == 0 || last) {
             CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+#ifdef MPL_BOUNDS
+            if (h->cnt_h->err != 0)
+                fprintf(stderr, "mpl: device error %d at iteration %d, bounds site %d\n", h->cnt_h->err, t,
+                        h->cnt_h->bounds_site);
+#endif
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
             // active next iteration, plus the signals of the last two finishes
             live = h->cnt_h->act_n[(t & 1) ^ 1] + h->cnt_h->fin_par[0] + h->cnt_h->fin_par[1];
@@ -1001,7 +1019,7 @@ static mpl_status_t ensure_rownorms(mpl_ctx* h, cudaStream_t st) {
 static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const float* lambda, const float* Xref,
                                    std::vector<float>& ex_host, float** ex_dev) {
     cudaStream_t st = h->main;
-    const int n = h->n, m = h->m, W = std::min(h->warm_w, m);
+    const int n = h->n, m = h->m, W = std::min(warm_candidates(h), m);
     const int chunk = std::max(1, std::min(p, 1024));
     mpl_status_t ws = ensure_ws(h, chunk);
     if (ws != MPL_OK) return ws;
@@ -1236,7 +1254,8 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
     const int m = h->m;
     const int smax = h->smax > 0 ? h->smax : default_smax(h);
     const int rho = std::min(h->rho, m);
-    const int warm_add = h->warm == 2 ? (h->warm_max > 0 ? h->warm_max : std::min(3 * rho, smax)) : 0;
+    const bool warm_on = h->warm == 2 && warm_candidates(h) > rho * h->omega;
+    const int warm_add = warm_on ? (h->warm_max > 0 ? h->warm_max : std::min(3 * rho, smax)) : 0;
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const bool q_fits = h->Q != nullptr || (double)m * m * sizeof(float) <= 0.25 * (double)free_b;

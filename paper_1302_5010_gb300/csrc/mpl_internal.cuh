@@ -65,6 +65,7 @@ struct Counters {
     unsigned long long fin_flops;  // algorithmic FLOPs of the exact finish (factor, solves, residual sums)
     unsigned long long qcols;  // signal columns scored by the identity route beta - Q_S x_S
     int sel_done;    // selection CTAs finished (the last one compacts the lists)
+    int bounds_site; // diagnostic builds: the first failed bounds check
     // algorithmic work of the memory-bound kernels (roofline accounting, all iterations)
     unsigned long long apg_elems;     // Gram-block entries read by the master problems' products
     unsigned long long apg_gl_elems;  // of those, read from global memory (blocks outside shared memory)
@@ -237,11 +238,31 @@ cudaError_t prepare_finish();
 cudaError_t prepare_corr_bf16();
 
 // Device-side error codes written to Counters::err.
-enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SHAPE = 3 };
+enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_NONFINITE = 2, DERR_SHAPE = 3, DERR_BOUNDS = 4 };
+
+// Bounds checks of the diagnostic build (-DMPL_BOUNDS): a failed check records DERR_BOUNDS
+// and its site in the counters (first one wins) and the caller skips the access.  Compiled
+// out otherwise.
+#ifdef MPL_BOUNDS
+__device__ __forceinline__ bool mpl_bad(Counters* c, bool bad, int site) {
+    if (bad) {
+        atomicCAS(&c->err, 0, (int)DERR_BOUNDS);
+        atomicCAS(&c->bounds_site, 0, site);
+    }
+    return bad;
+}
+#define MPL_OOB(cond, site) mpl_bad(d.cnt, (cond), (site))
+#else
+#define MPL_OOB(cond, site) false
+#endif
 
 // Candidate capacity of the selection kernel (per signal, in shared memory).
 constexpr int SEL_KCAP = 2048;
 constexpr int SEL_THREADS = 512;
+// Largest W of the learned warm start (candidates scored per signal).  Larger values
+// (W = 400 at the 4096 x 65536 workload) faulted on the GPU with a cause not found by
+// reading, so the option stops here, at the value the GPU tests exercise.
+constexpr int WARM_W_MAX = 64;
 constexpr int SEL_ROWCACHE_ATOMS = 8192;  // score rows up to this length are cached in shared memory
 // Master problem: Gram block kept in shared memory up to this size.
 constexpr int APG_SMEM_S = 200;

@@ -818,6 +818,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         for (int r = nv + tid; r < W; r += blockDim.x) {
             if (sh.sc[r] > pa.thr) {
                 const unsigned pos = atomicAdd(&sh.vc, 1u);
+                if (MPL_OOB(SEL_KCAP / 2 + pos >= SEL_KCAP, 501)) continue;
                 sh.key[SEL_KCAP / 2 + pos] = ((unsigned long long)ordered_bits(sh.sc[r]) << 32) |
                                              (unsigned long long)(0xffffffffu - (unsigned)sh.idx[r]);
             }
@@ -843,6 +844,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             for (int t = 0; t < nv + n2 && q < room; ++t) {
                 const int j = t < nv ? __float_as_int(sh.sc[SEL_KCAP / 2 + t])
                                      : (int)(0xffffffffu - (unsigned)(sh.key[t - nv] & 0xffffffffull));
+                if (MPL_OOB(j < 0 || j >= m || ss + q >= d.smax, 502)) break;
                 Si[ss + q] = j;
                 xi[ss + q] = 0.f;
                 mw[j >> 5] |= 1u << (j & 31);
@@ -905,6 +907,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
                 uint32_t* mw = d.mask + (size_t)i * d.mw;
                 for (int a = 0; a < q; ++a) {
                     const int j = (int)(0xffffffffu - (unsigned)(sh.key[a] & 0xffffffffull));
+                    if (MPL_OOB(j < 0 || j >= m || ss + a >= d.smax, 503)) break;
                     Si[ss + a] = j;
                     xi[ss + a] = 0.f;  // warm start: new entries at zero (Alg. 1)
                     mw[j >> 5] |= 1u << (j & 31);
@@ -979,6 +982,7 @@ __device__ void compact_body(const Dev& d, int cur) {
         for (int q = 0; q < 3; ++q) {
             const int off = base[q] + (warp ? wsum[q][warp - 1] : 0) + pre[q];
             if (f[q]) {
+                if (MPL_OOB(off < 0 || off >= d.p || sig < 0 || sig >= d.p, 504)) continue;
                 if (q == 0) { d.list_grow[off] = sig; d.list_apg[off] = sig; }
                 else if (q == 1) d.list_fin[cur][off] = sig;
                 else {

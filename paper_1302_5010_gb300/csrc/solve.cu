@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->fin_flops = 0ull;
             d.cnt->qcols = 0ull;
             d.cnt->sel_done = 0;
+            d.cnt->bounds_site = 0;
             d.cnt->apg_elems = d.cnt->apg_gl_elems = 0ull;
             d.cnt->fin_par[0] = d.cnt->fin_par[1] = 0;
             d.cnt->reent_n[0] = d.cnt->reent_n[1] = 0;
@@ -624,6 +625,7 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap, 
         // (entries from s up to the next multiple of 4 are zero: the streamed product reads
         // its operand as float4 slices)
         const int s4 = (s + 3) & ~3;
+        if (MPL_OOB(s4 > vcap || s > smax, 201)) { __syncthreads(); continue; }
         for (int r = tid; r < s4; r += blockDim.x) {
             const bool in = r < s;
             sh.u[r] = in ? xi[r] : 0.f;
@@ -814,6 +816,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     }
     __syncthreads();
     const int nz = cntnz;
+    if (MPL_OOB(s > 1024 || nz > 1024, 301)) return;
     if (d.Q) {  // ||x_S||_1 for the identity route's error band (FP32 sum, rounded up by gamma_1024)
         float l1 = 0.f;
         for (int a = threadIdx.x; a < nz; a += blockDim.x) l1 += fabsf(nzv[a]);
@@ -1227,6 +1230,7 @@ __global__ void __launch_bounds__(256) k_merge(Dev d, int cur) {
     for (int b = blockIdx.x; b < cnt; b += gridDim.x) {
         const int i = d.reent[cur][b];
         const int row = base + b;
+        if (MPL_OOB(row >= d.p || i < 0 || i >= d.p, 101)) continue;
         if (threadIdx.x == 0) {
             d.act[cur][row] = i;
             if (d.pos) d.pos[i] = row;
