@@ -312,8 +312,11 @@ def kernel_rooflines(P, precision: int, phase: dict, work: dict, pk: dict, sms: 
                                    "TFLOP/s", f"dense bf16 burst, of {pk['source']}", "flop_per_step")
     out["correlation"]["identity_route_ms_per_step"] = phase.get("qroute", 0.0)
     out["correlation"]["identity_route_columns_per_step"] = work["qroute_columns"]
-    out["finish"] = entry("k_finish", "alu", work["finish_flops"], phase["finish"], fp32_peak, "TFLOP/s",
-                          fp32_note + "; dependent factor/solve sweeps keep it latency-bound", "flop_per_step")
+    # the finish streams the support's atom columns (exact residuals and correlations) and
+    # Gram rows (its solves): at peak its bytes take longer than its FP32 work, so HBM bounds it
+    out["finish"] = entry("k_finish", "hbm", work["finish_bytes"], phase["finish"], hbm, "GB/s",
+                          hbm_note + "; one CTA per signal, latency-bound sweeps", "bytes_per_step")
+    out["finish"]["flop_per_step"] = work["finish_flops"]
     if work["apg_global_elems"] > 0.5 * work["apg_elems"]:
         out["master"] = entry("k_apg", "hbm", 4.0 * work["apg_global_elems"], phase["master"], hbm, "GB/s",
                               hbm_note + "; Gram blocks above the shared-memory size streamed per product",
@@ -359,7 +362,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
         tune = {"qroute": qr, "sync_every": se, "qgram": qg, "fixed": True}
     elif not args.no_autotune:
         tune = solver.autotune(B, lam, TOL, stream)
-    nph = 15
+    nph = 16
 
     def timed_steps(profile: bool, clocks=None):
         """W untimed solves (they capture the iteration graphs of this mode), then exactly
@@ -441,7 +444,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     work = {"gemm_columns": (phase_tot[7] - phase_tot[9]) / args.steps, "qroute_columns": phase_tot[9] / args.steps,
             "finish_flops": phase_tot[8] / args.steps, "apg_elems": phase_tot[11] / args.steps,
             "apg_global_elems": phase_tot[12] / args.steps, "residual_bytes": phase_tot[13] / args.steps,
-            "gram_bytes": phase_tot[14] / args.steps, "qgram": qgram}
+            "gram_bytes": phase_tot[14] / args.steps, "finish_bytes": phase_tot[15] / args.steps, "qgram": qgram}
     kern = kernel_rooflines(P, precision, phase, work, pk, sms)
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
     roof = dict(kern[dom])

@@ -100,7 +100,7 @@ typedef enum {
                                      solution on its S and status MPL_SIG_EARLY_STOP; lambda = 0
                                      (least squares, the OMP reduction of Sec. 2.5 with rho = 1)
                                      needs one of these rules or MPL_OPT_MAX_OUTER to end. */
-    MPL_OPT_QGRAM = 18            /* 1: the Gram growth reads the new entries of A_S^T A_S from
+    MPL_OPT_QGRAM = 18,           /* 1: the Gram growth reads the new entries of A_S^T A_S from
                                      Q = A^T A (Sec. 3: Q is precomputed off-line for the batch,
                                      and the master problem's Gram block Q_SS is a sub-block of
                                      it) instead of multiplying the atoms' columns; the entries
@@ -109,6 +109,10 @@ typedef enum {
                                      MPL_OPT_QROUTE, by one FMA chain per entry in the order
                                      the computed Gram block uses, so the solution is
                                      bit-identical either way.  0 = compute (default). */
+    MPL_OPT_GEMM_TILE = 19        /* signals per output tile of the BF16 tensor-core GEMM
+                                     (MPL_OPT_PRECISION = 1): 64, 128 (default) or 256; every
+                                     score is accumulated in the same order whatever the
+                                     tile, so the solution does not depend on it. */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */
@@ -275,7 +279,9 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64);
  * Gram-block entries read by the master problems' products, 12 how many of
  * them came from global memory (blocks too large for shared memory), 13 the
  * bytes the residual update reads and writes, 14 the bytes the Gram growth
- * reads and writes.  Returns the number of values written (<= cap, <= 15). */
+ * reads and writes, 15 the bytes the exact finish streams (Gram rows of its
+ * solves, the support's atom columns of its exact residuals and correlations).
+ * Returns the number of values written (<= cap, <= 16). */
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
 
 /* Autotuner of the batched solve (no counterpart in the paper, which has no
@@ -285,8 +291,9 @@ int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap);
  * iterations after the first (MPL_OPT_QROUTE = k rho plus the warm-start
  * additions; k > 0 only when Q = A^T A fits in a quarter of the free device
  * memory) and MPL_OPT_SYNC_EVERY in {1, 2, 4}; then, where Q fits, the best
- * of those with MPL_OPT_QGRAM = 1 at each MPL_OPT_SYNC_EVERY -- and keeps the
- * fastest on the handle.  Every candidate computes the same solution, so only time is
+ * of those with MPL_OPT_QGRAM = 1 at each MPL_OPT_SYNC_EVERY; then, for the
+ * BF16 path, the other GEMM tile widths (MPL_OPT_GEMM_TILE 64, 128, 256) with
+ * the best of those -- and keeps the fastest on the handle.  Every candidate computes the same solution, so only time is
  * compared.  Each candidate runs once untimed (graph capture, Q build) and
  * three times timed with events on `stream`; the median counts.  The solutions
  * go to a scratch buffer the call allocates and frees; the handle's last-solve
@@ -300,6 +307,7 @@ typedef struct {
     double ms_default;   /* median solve time with qroute 0, sync_every 2, qgram 0 */
     int candidates;      /* settings timed */
     int qgram;           /* chosen MPL_OPT_QGRAM */
+    int gemm_tile;       /* chosen MPL_OPT_GEMM_TILE (timed last, BF16 path only) */
 } mpl_tune_result_t;
 mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* lambda, double tol,
                           void* stream, mpl_tune_result_t* out);

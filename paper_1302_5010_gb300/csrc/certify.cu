@@ -1348,6 +1348,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
     __syncthreads();
     int steps = 0;
     unsigned long long flops = 0;  // algorithmic work (thread 0 keeps the tally)
+    unsigned long long bytes = 0;  // algorithmic bytes streamed: Gram rows, atom columns, b
     for (int step = 0; step < max_steps; ++step, ++steps) {
         // the FP32 factor of the previous step, updated for the atoms that left or joined P,
         // or a new support list and factor
@@ -1369,9 +1370,11 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
                     continue;
                 }
                 flops += (unsigned long long)(it + 1) * 2ull * np * np;
+                bytes += (unsigned long long)(it + 1) * 4ull * np * s;  // rows of G_PS per product
             } else {
                 if (!inc) {
                     flops += (unsigned long long)np * np * np / 3 + 2ull * np * np;
+                    bytes += 2ull * np * (np + 1);  // the lower triangle of G_PP gathered
                     FT_SPLIT(8);
                     gather_gram(sh, Gi, smax, np);
                     FT_SPLIT(9);
@@ -1493,6 +1496,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             }
             __syncthreads();
             flops += 4ull * n * np;  // residual and on-support correlations
+            bytes += 8ull * n * np + 4ull * n;  // the support's columns twice, and b
             double lmax = 0.0;
             if (vec4) {
                 dots_df_warp(d.A32, n, sh.Pi, np, rh, rl, sh.w);
@@ -1555,6 +1559,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
                     continue;
                 }
                 flops += (unsigned long long)(it + 1) * 2ull * np * np;
+                bytes += (unsigned long long)(it + 1) * 4ull * np * s;
             } else {
                 flops += 2ull * np * np;
                 fsolve(sh.F, np, sh.w);
@@ -1579,6 +1584,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             continue;
         }
         flops += 2ull * n * (unsigned long long)(s - np);
+        bytes += 4ull * n * (unsigned long long)(s - np);  // the zero entries' columns
         // exact check of the zero entries of S
         double cmax = 0.0;
         int worst = -1;
@@ -1652,7 +1658,10 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         break;
     }
 
-    if (tid == 0) atomicAdd(&d.cnt->fin_flops, flops);
+    if (tid == 0) {
+        atomicAdd(&d.cnt->fin_flops, flops);
+        atomicAdd(&d.cnt->fin_bytes, bytes);
+    }
     if (ok) {
         double* x64 = d.xS64 + (size_t)i * smax;
         double l1 = 0.0, cm = 0.0;

@@ -343,8 +343,32 @@ cudaError_t encode_rows(CUtensorMap* map, const void* ptr, int rows, int n, int 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-constexpr int TC_BN = 128;
-constexpr int TC_STAGES = 6;
+// Tile widths (signals per output tile) with their ring depths: the operand ring takes
+// ~190 KB of shared memory in each, so one CTA per SM; the two accumulators take 2 BN of
+// the 512 TMEM columns.
+constexpr int TC_BN_LIST[3] = {64, 128, 256};
+template <int BN> struct TcStages;
+template <> struct TcStages<64> { static constexpr int v = 8; };
+template <> struct TcStages<128> { static constexpr int v = 6; };
+template <> struct TcStages<256> { static constexpr int v = 4; };
+
+int bn_slot(int bn) { return bn == 64 ? 0 : (bn == 256 ? 2 : 1); }
+
+template <int BN>
+cudaError_t set_attr() {
+    using L = TcSmem<BN, TcStages<BN>::v>;
+    return cudaFuncSetAttribute(k_corr_bf16<BN, TcStages<BN>::v>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                L::TOTAL);
+}
+
+template <int BN>
+cudaError_t launch_bn(const Dev& d, int cur, const CUtensorMap* maps, int act_n_ub, int sms, cudaStream_t s) {
+    using L = TcSmem<BN, TcStages<BN>::v>;
+    const int tiles = ((d.m + TC_BM - 1) / TC_BM) * ((act_n_ub + BN - 1) / BN);
+    const int grid = tiles < sms ? tiles : sms;
+    return launch_chain(k_corr_bf16<BN, TcStages<BN>::v>, dim3(grid), dim3(TC_THREADS), (size_t)L::TOTAL, s, d, cur,
+                        maps[0], maps[1 + bn_slot(BN)]);
+}
 
 }  // namespace
 
@@ -353,31 +377,30 @@ cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16, 
     if ((n % 8) != 0 || !A16 || !R16c) return cudaErrorNotSupported;
     CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(tmap);
     cudaError_t e = encode_rows(&maps[0], A16, m, n, TC_BM);
-    if (e != cudaSuccess) return e;
-    return encode_rows(&maps[1], R16c, pmax, n, TC_BN);
+    // one residual map per tile width (the box is the tile's rows)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = encode_rows(&maps[1 + k], R16c, pmax, n, TC_BN_LIST[k]);
+    return e;
 }
 
 cudaError_t prepare_corr_bf16() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    using L = TcSmem<TC_BN, TC_STAGES>;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_corr_bf16<TC_BN, TC_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    cudaError_t e = set_attr<64>();
+    if (e == cudaSuccess) e = set_attr<128>();
+    if (e == cudaSuccess) e = set_attr<256>();
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms, cudaStream_t s,
-                             int64_t* nl) {
+                             int64_t* nl, int bn) {
     if (act_n_ub <= 0) return cudaSuccess;
-    using L = TcSmem<TC_BN, TC_STAGES>;
     cudaError_t ep = prepare_corr_bf16();
     if (ep != cudaSuccess) return ep;
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(tmap);
-    const int tiles = ((d.m + TC_BM - 1) / TC_BM) * ((act_n_ub + TC_BN - 1) / TC_BN);
-    const int grid = tiles < sms ? tiles : sms;
-    const cudaError_t e = launch_chain(k_corr_bf16<TC_BN, TC_STAGES>, dim3(grid), dim3(TC_THREADS), (size_t)L::TOTAL, s, d,
-                                       cur, maps[0], maps[1]);
+    const cudaError_t e = bn == 64    ? launch_bn<64>(d, cur, maps, act_n_ub, sms, s)
+                          : bn == 256 ? launch_bn<256>(d, cur, maps, act_n_ub, sms, s)
+                                      : launch_bn<128>(d, cur, maps, act_n_ub, sms, s);
     if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();

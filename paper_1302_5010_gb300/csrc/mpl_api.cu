@@ -106,13 +106,14 @@ struct mpl_ctx {
     float* Xst = nullptr;
     size_t Bst_b = 0, lamst_b = 0, Xst_b = 0;
     // tensor-map block for the BF16 GEMM (A16, R16c)
-    alignas(64) unsigned char tmap[256];
+    alignas(64) unsigned char tmap[TC_TMAP_BYTES];
+    int gemm_bn = 128;  // signals per tile of the BF16 GEMM (MPL_OPT_GEMM_TILE)
     int tmap_p = -1;
     // last solve
     int last_p = 0;
     std::vector<mpl_signal_stats_t> stats;
     int64_t launches = 0;
-    double phase_ms[15] = {0};
+    double phase_ms[16] = {0};
     std::vector<cudaEvent_t> evpool;
 };
 
@@ -508,6 +509,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v != 0 && v != 1) return MPL_ERR_ARG;
             h->qgram = (int)v;
             return MPL_OK;
+        case MPL_OPT_GEMM_TILE:
+            if (v != 64 && v != 128 && v != 256) return MPL_ERR_ARG;
+            h->gemm_bn = (int)v;
+            return MPL_OK;
         case MPL_OPT_OMEGA:
             if (v < 1 || v > 16) return MPL_ERR_ARG;
             h->omega = (int)v;
@@ -538,6 +543,7 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_WARM_THRESHOLD: *v = h->warm_thr; return MPL_OK;
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
         case MPL_OPT_QGRAM: *v = h->qgram; return MPL_OK;
+        case MPL_OPT_GEMM_TILE: *v = h->gemm_bn; return MPL_OK;
         case MPL_OPT_OMEGA: *v = h->omega; return MPL_OK;
         case MPL_OPT_STOP_RINF: *v = h->stop_rinf; return MPL_OK;
         case MPL_OPT_STOP_R2: *v = h->stop_r2; return MPL_OK;
@@ -628,7 +634,7 @@ static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int ac
             // the residual writers keep the compacted BF16 rows current (d.pos); only a path
             // without them needs the gather
             if (!d.pos && (e = launch_gather_r16(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
-            if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl)) != cudaSuccess) return e;
+            if ((e = launch_corr_bf16(d, cur, h->tmap, act_ub, h->sms, run, nl, h->gemm_bn)) != cudaSuccess) return e;
         } else {
             if ((e = launch_corr_f32(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
         }
@@ -844,7 +850,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     // iteration before last (same parity), so a retry takes three iterations
     const int hard_cap = h->max_outer + 3 * FIN_MAX_FAILS + 10;
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
-    double graph_phase[15] = {0};
+    double graph_phase[16] = {0};
     int t = 0;
     for (; live > 0 && t < hard_cap; ++t) {
         const int par = t & 1;
@@ -928,6 +934,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     h->phase_ms[12] = (double)h->cnt_h->apg_gl_elems;  // of those, from global memory
     h->phase_ms[13] = (double)h->cnt_h->res_bytes;     // bytes of the residual update
     h->phase_ms[14] = (double)h->cnt_h->gram_bytes;    // bytes of the Gram growth
+    h->phase_ms[15] = (double)h->cnt_h->fin_bytes;     // bytes the exact finish streams
     h->launches = nl;
     bool all_ok = true;
     std::memcpy(h->stats.data(), h->stats_pin, (size_t)p * sizeof(mpl_signal_stats_t));
@@ -968,7 +975,7 @@ mpl_status_t mpl_correlate(mpl_handle_t h, const float* R, int p, float* C, void
             h->tmap_p = h->cap_p;
         }
         CK(launch_gather_r16(d, 0, p, st, &nl));
-        CK(launch_corr_bf16(d, 0, h->tmap, p, h->sms, st, &nl));
+        CK(launch_corr_bf16(d, 0, h->tmap, p, h->sms, st, &nl, h->gemm_bn));
     } else {
         CK(launch_corr_f32(d, 0, p, st, &nl));
     }
@@ -1052,7 +1059,7 @@ static mpl_status_t build_examples(mpl_ctx* h, const float* B, int p, const floa
                 h->tmap_p = h->cap_p;
             }
             CK(launch_gather_r16(d, 0, pc, st, &nl));
-            CK(launch_corr_bf16(d, 0, h->tmap, pc, h->sms, st, &nl));
+            CK(launch_corr_bf16(d, 0, h->tmap, pc, h->sms, st, &nl, h->gemm_bn));
         } else {
             CK(launch_corr_f32(d, 0, pc, st, &nl));
         }
@@ -1239,7 +1246,7 @@ mpl_status_t mpl_get_solution_f64(mpl_handle_t h, int p, double* X64) {
 
 int mpl_get_phase_times(mpl_handle_t h, double* ms_out, int cap) {
     if (!h || !ms_out) return 0;
-    const int k = std::min(cap, 15);
+    const int k = std::min(cap, 16);
     for (int i = 0; i < k; ++i) ms_out[i] = h->phase_ms[i];
     return k;
 }
@@ -1272,8 +1279,9 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int keep_q = h->qroute, keep_se = h->sync_every, keep_prof = h->profile, keep_g = h->qgram;
+    const int keep_bn = h->gemm_bn;
     h->profile = 0;
-    mpl_tune_result_t best{keep_q, keep_se, 1e300, 0.0, 0, keep_g};
+    mpl_tune_result_t best{keep_q, keep_se, 1e300, 0.0, 0, keep_g, keep_bn};
     mpl_status_t first_err = MPL_OK;
     // stage 0: identity route x handshake interval with the computed Gram; stage 1: the
     // Gram gathered from Q with the stage-0 route at each handshake interval
@@ -1307,6 +1315,35 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
             if (med < best.ms) { best.ms = med; best.qroute = qr; best.sync_every = se; best.qgram = stage; }
         }
     }
+    // stage 2 (BF16 GEMM only): the tile width with the chosen route, cadence and Gram source
+    best.gemm_tile = keep_bn;
+    if (h->precision == 1 && best.candidates > 0) {
+        for (int bn : {64, 128, 256}) {
+            if (bn == keep_bn) continue;  // timed above
+            h->qroute = best.qroute;
+            h->sync_every = best.sync_every;
+            h->qgram = best.qgram;
+            h->gemm_bn = bn;
+            clear_graphs(h);
+            mpl_status_t rc = bmpl_solve(h, B, p, lambda, X, tol, stream);
+            std::vector<float> t;
+            for (int r = 0; r < 3 && (rc == MPL_OK || rc == MPL_ERR_NOT_CONVERGED); ++r) {
+                cudaEventRecord(e0, st);
+                rc = bmpl_solve(h, B, p, lambda, X, tol, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t.push_back(ms);
+            }
+            if (rc != MPL_OK && rc != MPL_ERR_NOT_CONVERGED) continue;
+            std::sort(t.begin(), t.end());
+            const double med = t[t.size() / 2];
+            ++best.candidates;
+            if (med < best.ms) { best.ms = med; best.gemm_tile = bn; }
+        }
+    }
+    h->gemm_bn = best.gemm_tile;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(X);
@@ -1316,6 +1353,7 @@ mpl_status_t mpl_autotune(mpl_handle_t h, const float* B, int p, const float* la
         h->qroute = keep_q;
         h->sync_every = keep_se;
         h->qgram = keep_g;
+        h->gemm_bn = keep_bn;
         return first_err != MPL_OK ? first_err : MPL_ERR_CUDA;
     }
     h->qroute = best.qroute;

@@ -71,6 +71,7 @@ struct Counters {
     unsigned long long apg_gl_elems;  // of those, read from global memory (blocks outside shared memory)
     unsigned long long res_bytes;     // bytes the residual update reads (atoms, b) and writes (R)
     unsigned long long gram_bytes;    // bytes the Gram growth reads (Q or atoms, b) and writes (G, h)
+    unsigned long long fin_bytes;     // bytes the exact finish streams (Gram rows, atom columns, b)
     __host__ __device__ int act_n_of(int c) const { return act_n[c]; }
 };
 
@@ -175,11 +176,13 @@ struct PropArgs {
 // Each returns the CUDA error of its launch and adds its launches to *nl.
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
 // BF16 tensor-core correlation (tcgen05 + TMA).  prepare() encodes the TMA
-// descriptors for A16 (m x n) and R16c (pmax x n) into tmap (256 bytes).
+// descriptors for A16 (m x n) and R16c (pmax x n, one per tile width) into tmap
+// (TC_TMAP_BYTES).  bn: signals per output tile, 64, 128 or 256.
+constexpr int TC_TMAP_BYTES = 4 * 128;
 cudaError_t corr_bf16_prepare(int n, int m, int pmax, const __nv_bfloat16* A16,
                               const __nv_bfloat16* R16c, void* tmap);
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms,
-                             cudaStream_t s, int64_t* nl);
+                             cudaStream_t s, int64_t* nl, int bn = 128);
 cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
 // Correlation routes of one outer iteration (selects the selection kernel's error band).
 enum CorrRoute : int { ROUTE_GEMM = 0, ROUTE_GEMM_F32 = 1, ROUTE_Q = 2 };

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->apg_elems = d.cnt->apg_gl_elems = 0ull;
             d.cnt->fin_par[0] = d.cnt->fin_par[1] = 0;
             d.cnt->reent_n[0] = d.cnt->reent_n[1] = 0;
-            d.cnt->res_bytes = d.cnt->gram_bytes = 0ull;
+            d.cnt->res_bytes = d.cnt->gram_bytes = d.cnt->fin_bytes = 0ull;
         }
     }
 }

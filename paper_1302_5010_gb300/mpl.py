@@ -46,6 +46,7 @@ MPL_OPT_STOP_RINF = 15
 MPL_OPT_STOP_R2 = 16
 MPL_OPT_STOP_EPS = 17
 MPL_OPT_QGRAM = 18
+MPL_OPT_GEMM_TILE = 19
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -75,7 +76,8 @@ class SignalStats(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("qroute", ctypes.c_int32), ("sync_every", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32), ("qgram", ctypes.c_int32)]
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32), ("qgram", ctypes.c_int32),
+                ("gemm_tile", ctypes.c_int32)]
 
 
 class MplError(RuntimeError):
@@ -271,8 +273,8 @@ def mpl_get_solution_f64(h, p: int, X64) -> None:
 
 
 def mpl_get_phase_times(h) -> list:
-    buf = (ctypes.c_double * 15)()
-    k = load().mpl_get_phase_times(h, buf, 15)
+    buf = (ctypes.c_double * 16)()
+    k = load().mpl_get_phase_times(h, buf, 16)
     return [buf[i] for i in range(k)]
 
 
@@ -291,7 +293,7 @@ def mpl_get_launch_count(h) -> int:
 
 PHASES = ("total", "correlation", "selection", "gram", "finish", "master", "residual", "corr_columns",
           "finish_flops", "qroute_columns", "qroute", "apg_elems", "apg_global_elems", "residual_bytes",
-          "gram_bytes")
+          "gram_bytes", "finish_bytes")
 
 
 @dataclass
@@ -315,7 +317,7 @@ class Solver:
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
                     warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE,
                     omega=MPL_OPT_OMEGA, stop_rinf=MPL_OPT_STOP_RINF, stop_r2=MPL_OPT_STOP_R2,
-                    stop_eps=MPL_OPT_STOP_EPS, qgram=MPL_OPT_QGRAM)
+                    stop_eps=MPL_OPT_STOP_EPS, qgram=MPL_OPT_QGRAM, gemm_tile=MPL_OPT_GEMM_TILE)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 

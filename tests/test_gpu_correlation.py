@@ -168,3 +168,29 @@ def test_bf16_accumulator_assumption_adversarial(kind, n):
     err = np.abs(C - exact)
     ratio = (err / (n * 2.0 ** -22 * absdot)).max()
     assert ratio <= 1.25, ratio
+
+
+def _run_tile(At, R, bn):
+    import torch
+    s = mpl.Solver(torch.from_numpy(At).cuda(), precision=1, gemm_tile=bn)
+    C = torch.empty((R.shape[0], At.shape[0]), dtype=torch.float32, device="cuda")
+    s.correlate(torch.from_numpy(R).cuda(), C)
+    torch.cuda.synchronize()
+    s.close()
+    return C.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("bn", [64, 256])
+@pytest.mark.parametrize("n,m,p", [(4096, 65536, 300), (1000, 2050, 130), (256, 1000, 37)])
+def test_bf16_tile_widths(bn, n, m, p):
+    """The 64- and 256-signal tiles (their own TMA boxes, ring depths and TMEM accumulators)
+    give the same scores as the 128-signal tile, bit for bit (the accumulation order along n
+    does not depend on the tile), within the accumulation bound, on shapes with ragged tails
+    and more tiles than SMs."""
+    At, R = _data(n, m, p, 19 * n + p + bn)
+    C = _run_tile(At, R, bn)
+    C128 = _run_tile(At, R, 128)
+    np.testing.assert_array_equal(C, C128)
+    A16, R16 = _bf16(At).astype(np.float64), _bf16(R).astype(np.float64)
+    err16 = np.abs(C - R16 @ A16.T)
+    assert np.all(err16 <= 1.25 * n * 2.0 ** -22 * (np.abs(R16) @ np.abs(A16).T) + 1e-30)

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1302_5010_gb300 import synth
+from paper_1302_5010_gb300 import mpl, synth
 from parity import check_against_oracle
 from test_gpu_parity import assert_certified, oracle_solve, solve_gpu
 
@@ -42,3 +42,23 @@ def test_mixed_identical_to_plain_c2():
     np.testing.assert_array_equal(X64p, X64m)
     idx = np.arange(0, P.p, 8)
     check_against_oracle(P, X64m[idx], oracle_solve(P, idx), idx)
+
+
+@pytest.mark.parametrize("bn", [64, 256])
+def test_gemm_tile_does_not_change_the_solution(bn):
+    """The mixed path with another GEMM tile width solves to the same bits."""
+    import torch
+    P = synth.make_config("c5", p=24)
+    At = torch.from_numpy(P.At).cuda()
+    B, lam = torch.from_numpy(P.B).cuda(), torch.from_numpy(P.lam).cuda()
+    out = []
+    for tile in (128, bn):
+        s = mpl.Solver(At, rho=P.rho, precision=1, smax=512, gemm_tile=tile)
+        X = torch.empty((P.p, P.m), device="cuda")
+        r = s.solve(B, lam, X)
+        torch.cuda.synchronize()
+        assert r.status == mpl.MPL_OK
+        out.append((X.cpu().numpy(), r.stats["outer_iters"]))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
