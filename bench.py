@@ -36,10 +36,15 @@ UNIT = "signals/s"
 TOL = 1e-6
 FP32_LANES_PER_SM = 128
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the
-# roofline block can report, per workload, from one ncu capture of that kernel (None until a
-# capture of the current kernel exists).
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the roofline block
+# can report, per workload, from an ncu capture of the current kernel; absent until one exists.
+TRAFFIC = {
+    # all k_finish launches of one solve of the 4096 x 65536 batch: 619.9 MB read + 1.6 MB
+    # written over the 16 launches of a 64-signal solve (9.71 MB per signal), scaled to 1024
+    # signals (per-signal work is independent of the batch); per step, like the entry's
+    # bytes_per_step
+    ("c3", "k_finish"): 9.94e9,
+}
 
 # active-set capacity per workload (supports reach ~570 atoms on c3, ~290 on c5)
 SMAX = {"c1": None, "c2": None, "c3": 1024, "c4": 512, "c5": 512}
@@ -248,7 +253,8 @@ def correlation_microbench(args) -> None:
     A = torch.randn((m, n), device="cuda", generator=g)
     A /= A.norm(dim=1, keepdim=True)
     R = torch.randn((p, n), device="cuda", generator=g) * 0.3
-    s = mpl.Solver(A, precision=1 if args.path == "mixed" else 0)
+    s = mpl.Solver(A, precision=1 if args.path == "mixed" else 0,
+                   **({"gemm_tile": args.gemm_tile} if args.path == "mixed" else {}))
     C = torch.empty((p, m), device="cuda")
     for _ in range(max(args.warmup, 1)):
         s.correlate(R, C)
@@ -261,6 +267,7 @@ def correlation_microbench(args) -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"microbench": "correlation", "path": args.path, "n": n, "m": m, "p": p,
+                      "gemm_tile": args.gemm_tile if args.path == "mixed" else None,
                       "ms_per_call": ms, "tflops_incl_staging": 2.0 * n * m * p / ms / 1e9}))
     s.close()
 
@@ -450,7 +457,7 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
     roof = dict(kern[dom])
     tr = TRAFFIC.get((args.config, roof["kernel"]))
     roof["traffic"] = tr
-    roof["traffic_unit"] = "bytes per launch"
+    roof["traffic_unit"] = "bytes per step (all launches of the kernel in one solve)"
     # summed event times per phase (the finish runs on a second stream, so phases overlap)
     roof["phase_ms_per_step"] = {k: round(v, 4) for k, v in phase.items() if v > 0}
     roof["events_pass_ms_per_step"] = float(sum(prof_ms)) / args.steps
@@ -459,6 +466,37 @@ def timed_path(args, mpl, torch, P, dev, precision: int, world: int, dist, local
             "training": training, "X64": X64,
             "outer_iters_mean": float(np.mean(stats["outer_iters"])),
             "active_size_mean": float(np.mean(stats["active_size"]))}
+
+
+def solve_once(args):
+    """Profiling target: args.warmup solves (graph capture, Q build), then one solve of the
+    workload args.solve_once (first args.solve_p signals) with fixed options, printing the
+    kernel launches of each so that an ncu capture can skip the warm-up."""
+    import torch
+    from paper_1302_5010_gb300 import mpl, synth
+    P = synth.make_config(args.solve_once, p=args.solve_p)
+    dev = torch.device("cuda", 0)
+    At = torch.from_numpy(P.At).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    lam = torch.from_numpy(P.lam).to(dev)
+    opts = dict(qgram=args.solve_qgram, graph=args.solve_graph, sync_every=args.solve_sync)
+    if SMAX.get(args.solve_once):
+        opts["smax"] = SMAX[args.solve_once]
+    if args.path == "mixed":
+        opts["gemm_tile"] = args.gemm_tile
+    s = mpl.Solver(At, rho=P.rho, precision=1 if args.path == "mixed" else 0, **opts)
+    X = torch.empty((P.p, P.m), dtype=torch.float32, device=dev)
+    before = 0
+    for _ in range(args.warmup):
+        s.solve(B, lam, X, TOL)
+        torch.cuda.synchronize()
+        before += s.launches()
+    r = s.solve(B, lam, X, TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_once": args.solve_once, "p": P.p, "path": args.path, "options": opts,
+                      "launches_before": before, "launches": s.launches(),
+                      "certified": int(np.sum(r.stats["status"] == mpl.MPL_SIG_CERTIFIED))}), flush=True)
+    s.close()
 
 
 def omp_compare(args):
@@ -526,10 +564,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--corr-shape", type=int, nargs=3, metavar=("N", "M", "P"), default=None,
                     help="profile the correlation GEMM alone on this shape instead of the benchmark")
+    ap.add_argument("--gemm-tile", type=int, default=256, choices=[64, 128, 256],
+                    help="signals per tile of the BF16 GEMM in the correlation microbenchmark")
     ap.add_argument("--omp-compare", type=int, default=0, metavar="P",
                     help="lambda = 0 on the 4096 x 16384, k 400-600 shape for P signals: rho = 1 (batch "
                          "OMP) against multi-atom growth, instead of the benchmark")
+    ap.add_argument("--solve-once", default=None, metavar="CFG",
+                    help="profiling target: --warmup solves, then one solve of workload CFG")
+    ap.add_argument("--solve-p", type=int, default=None, help="signals of the --solve-once workload")
+    ap.add_argument("--solve-qgram", type=int, default=1)
+    ap.add_argument("--solve-graph", type=int, default=1)
+    ap.add_argument("--solve-sync", type=int, default=4)
     args = ap.parse_args()
+    if args.solve_once:
+        solve_once(args)
+        return
     if args.corr_shape:
         correlation_microbench(args)
         return

@@ -34,23 +34,23 @@ __device__ __forceinline__ float4 load4(const float* row, int k, int n) {
     return v;
 }
 
+// jtile0: first atom tile of this launch (grids cover at most 65535 atom tiles; larger
+// dictionaries take several launches).
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
+__global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur, int jtile0) {
     pdl_enter();
     const int act_n = d.cnt->act_n_of(cur);
     // signal tiles vary fastest, so the blocks in flight share their atom tile in L2
     // (the dictionary streams from HBM once per launch)
     const int k0 = blockIdx.x * BN;
     if (k0 >= act_n) return;
+    const int j0 = (jtile0 + (int)blockIdx.y) * BM;
     const int n = d.n, m = d.m;
     const int* act = d.act_of(cur);
 
     __shared__ __align__(16) float As[2][BK][BM + PAD];
     __shared__ __align__(16) float Bs[2][BK][BN + PAD];
 
-    // atom tiles beyond the grid's y extent (65535 tiles) are taken in further passes
-    for (int j0 = blockIdx.y * BM; j0 < m; j0 += gridDim.y * BM) {
-    if (j0 != blockIdx.y * BM) __syncthreads();  // the previous tile's last slice is consumed
     const int tid = threadIdx.x;
     const int lrow = tid >> 1;       // 0..127: row of the tile this thread loads
     const int lk = (tid & 1) * 4;    // 0 or 4: k offset within the slice
@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
             }
         }
     }
-    }  // atom tiles
 }
 
 }  // namespace
@@ -137,12 +136,14 @@ __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur) {
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
     const int tiles_m = (d.m + BM - 1) / BM;
-    dim3 grid((act_n_ub + BN - 1) / BN, tiles_m < 65535 ? tiles_m : 65535);
     const bool vec = (d.n % 4) == 0;
-    const cudaError_t e = vec ? launch_chain(k_corr_f32<true>, grid, dim3(256), 0, s, d, cur)
-                              : launch_chain(k_corr_f32<false>, grid, dim3(256), 0, s, d, cur);
-    if (e != cudaSuccess) return e;
-    ++*nl;
+    for (int t0 = 0; t0 < tiles_m; t0 += 65535) {  // grid.y is at most 65535
+        dim3 grid((act_n_ub + BN - 1) / BN, tiles_m - t0 < 65535 ? tiles_m - t0 : 65535);
+        const cudaError_t e = vec ? launch_chain(k_corr_f32<true>, grid, dim3(256), 0, s, d, cur, t0)
+                                  : launch_chain(k_corr_f32<false>, grid, dim3(256), 0, s, d, cur, t0);
+        if (e != cudaSuccess) return e;
+        ++*nl;
+    }
     return cudaGetLastError();
 }
 

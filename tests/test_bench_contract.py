@@ -41,8 +41,8 @@ def test_metric_matches_baseline_file():
 
 
 def test_traffic_entries_are_per_launch_byte_counts():
-    """The roofline block's `traffic` entries are DRAM bytes per launch of one kernel on one
-    workload: positive numbers, keyed by (workload, kernel), nothing else."""
+    """The roofline block's `traffic` entries are DRAM bytes of one kernel on one workload:
+    positive numbers, keyed by (workload, kernel), nothing else."""
     sys.path.insert(0, ROOT)
     import bench
     for key, v in bench.TRAFFIC.items():
