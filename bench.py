@@ -543,6 +543,139 @@ def omp_compare(args):
         s.close()
 
 
+def streaming_warm_vs_cold(args, mpl, torch, dev) -> dict:
+    """The streaming workload (2048 x 32768, 4096 signals arriving in batches of 512): every
+    batch solved to the KKT tolerance by the mixed path, cold and with the learned warm
+    start, the proposal trained on 50000 signals of the same generator (disjoint seed)
+    solved and certified by the same solver.  Each mode: one untimed pass over the batches
+    (graph capture), then one pass timed by device events per batch."""
+    cfg = "c5"
+    P = rank_problem(synth_mod(), cfg, 0)
+    ntrain = args.c5_train or TRAIN_SIGNALS[cfg]
+    Pt = rank_problem(synth_mod(), cfg, 0, p=ntrain, seed_shift=9000)
+    At = torch.from_numpy(P.At).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    lam = torch.from_numpy(P.lam).to(dev)
+    bs = 512
+    solver = mpl.Solver(At, rho=P.rho, precision=1, smax=SMAX[cfg])
+    stream = torch.cuda.current_stream()
+    X = torch.empty((bs, P.m), dtype=torch.float32, device=dev)
+    tune = solver.autotune(B[:bs], lam[:bs], TOL, stream)
+
+    def one_pass(timed: bool):
+        ms, outer, cert = [], [], True
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for c0 in range(0, P.p, bs):
+            ev0.record(stream)
+            res = solver.solve(B[c0:c0 + bs], lam[c0:c0 + bs], X, TOL, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            outer.append(res.stats["outer_iters"].astype(np.float64))
+            cert &= bool(res.status == mpl.MPL_OK and np.all(res.stats["status"] == mpl.MPL_SIG_CERTIFIED))
+        o = np.concatenate(outer)
+        return {"signals_per_s": P.p / (sum(ms) / 1e3), "ms_per_batch": float(np.mean(ms)),
+                "outer_iters_mean": float(o.mean()), "outer_iters_max": int(o.max()), "certified_all": cert}
+
+    one_pass(False)
+    cold = one_pass(True)
+    # training stream: solved cold in chunks, then the proposal trained on its supports
+    t0 = time.perf_counter()
+    Bt = torch.from_numpy(Pt.B).to(dev)
+    lt = torch.from_numpy(Pt.lam).to(dev)
+    Xt = torch.zeros((Pt.p, Pt.m), dtype=torch.float32, device=dev)
+    labels_ok = True
+    for c0 in range(0, Pt.p, 4096):
+        r = solver.solve(Bt[c0:c0 + 4096], lt[c0:c0 + 4096], Xt[c0:c0 + 4096], TOL, stream)
+        labels_ok &= bool(np.all(r.stats["status"] == mpl.MPL_SIG_CERTIFIED))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = solver.train_proposal(Bt, lt, Xt, epochs=args.train_epochs)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del Xt
+    solver.set(mpl.MPL_OPT_WARM_START, 2)
+    one_pass(False)
+    warm = one_pass(True)
+    warm["active"] = bool(solver.get(mpl.MPL_OPT_WARM_CANDIDATES) > P.rho)
+    solver.close()
+    return {"workload": "c5: A 2048x32768 Gaussian, 4096 signals in batches of 512, k~U[50,200], rho 50",
+            "cold": cold, "warm": warm, "speedup_warm_vs_cold": warm["signals_per_s"] / cold["signals_per_s"],
+            "autotune": tune,
+            "training": {"signals": Pt.p, "labels_certified": labels_ok, "solve_s": t1 - t0, "train_s": t2 - t1,
+                         "epochs": args.train_epochs, "loss_first": float(losses[0]) if len(losses) else None,
+                         "loss_last": float(losses[-1]) if len(losses) else None}}
+
+
+def synth_mod():
+    from paper_1302_5010_gb300 import synth
+    return synth
+
+
+def big_dictionary_run(args):
+    """Single-signal MPL and SMPL (omega = 3) on the big dictionary of the paper's Sec. 4.6:
+    A 2^12 x 2^20 Gaussian (16 GiB in FP32, drawn on the device), a k-sparse N(0, 1) code,
+    noise U[-0.01, 0.01], lambda = 0.005 ||A^T b||_inf and the stopping rule of eq. (stop_con)
+    at 1e-5, as in the paper's experiments (Sec. 4.1).  With one signal every correlation is
+    a matrix-vector product over the whole dictionary.  For each path (mixed BF16, plain
+    FP32) and omega: a warm-up solve, then args.steps solves timed by device events, then one
+    solve with event nodes around the phases.  One JSON line each (not a bench line)."""
+    import torch
+    from paper_1302_5010_gb300 import mpl, synth
+
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    dev = torch.device("cuda", 0)
+    n, m = args.big_shape
+    t0 = time.perf_counter()
+    At, b, lam, supp, vals = synth.big_dictionary_device(n, m, args.big_k, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    x_true = torch.zeros(m, dtype=torch.float64, device=dev)
+    x_true[supp] = vals
+    stream = torch.cuda.current_stream()
+    for precision in (1, 0):
+        for omega in (1, 3):
+            s = mpl.Solver(At, rho=args.big_rho, precision=precision, smax=1024, stop_eps=1e-5, omega=omega)
+            X = torch.empty((1, m), dtype=torch.float32, device=dev)
+            res = s.solve(b, lam, X, TOL, stream)  # warm-up: BF16 copy, graphs
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(max(args.steps, 1)):
+                ev0.record(stream)
+                res = s.solve(b, lam, X, TOL, stream)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+            s.set(mpl.MPL_OPT_PROFILE, 1)
+            s.solve(b, lam, X, TOL, stream)
+            torch.cuda.synchronize()
+            ph = s.phase_times()
+            s.set(mpl.MPL_OPT_PROFILE, 0)
+            X64 = torch.zeros((1, m), dtype=torch.float64, device=dev)
+            s.solution_f64(X64)
+            st = res.stats
+            err = float(torch.linalg.vector_norm(X64[0] - x_true) / torch.linalg.vector_norm(x_true))
+            found = torch.abs(X64[0]) > 1e-3 * torch.abs(X64[0]).max()
+            hit = int(found[supp].sum())
+            iters = int(st["outer_iters"][0])
+            # the correlation reads the whole dictionary once per outer iteration
+            corr_bytes = float(iters) * m * n * (2 if precision == 1 else 4)
+            print(json.dumps({
+                "big_dictionary": f"{n}x{m}", "k": args.big_k, "rho": args.big_rho, "omega": omega,
+                "path": "mixed" if precision == 1 else "plain", "lam": float(lam[0]),
+                "ms_per_solve": float(np.median(ms)), "ms_all": [round(v, 3) for v in ms],
+                "status": int(st["status"][0]), "outer_iters": iters,
+                "active_size": int(st["active_size"][0]), "nnz": int(st["nnz"][0]),
+                "rel_err_vs_planted": err, "planted_found": hit, "support_size": int(found.sum()),
+                "phase_ms": {k: round(float(ph[k]), 3) for k in ("correlation", "selection", "gram", "finish",
+                                                                 "master", "residual")},
+                "correlation_gbs": corr_bytes / (ph["correlation"] / 1e3) / 1e9 if ph["correlation"] > 0 else None,
+                "generate_s": gen_s}), flush=True)
+            s.close()
+            del X, X64
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,6 +702,14 @@ def main():
     ap.add_argument("--omp-compare", type=int, default=0, metavar="P",
                     help="lambda = 0 on the 4096 x 16384, k 400-600 shape for P signals: rho = 1 (batch "
                          "OMP) against multi-atom growth, instead of the benchmark")
+    ap.add_argument("--no-c5", action="store_true", help="skip the streaming warm-vs-cold measurement")
+    ap.add_argument("--c5-only", action="store_true", help="only the streaming warm-vs-cold measurement")
+    ap.add_argument("--c5-train", type=int, default=None, help="training signals of the streaming measurement")
+    ap.add_argument("--big-dict", action="store_true",
+                    help="single-signal MPL / SMPL on the paper's 2^12 x 2^20 big dictionary instead of the benchmark")
+    ap.add_argument("--big-shape", type=int, nargs=2, default=[4096, 1 << 20], metavar=("N", "M"))
+    ap.add_argument("--big-k", type=int, default=600)
+    ap.add_argument("--big-rho", type=int, default=50)
     ap.add_argument("--solve-once", default=None, metavar="CFG",
                     help="profiling target: --warmup solves, then one solve of workload CFG")
     ap.add_argument("--solve-p", type=int, default=None, help="signals of the --solve-once workload")
@@ -578,6 +719,14 @@ def main():
     args = ap.parse_args()
     if args.solve_once:
         solve_once(args)
+        return
+    if args.big_dict:
+        big_dictionary_run(args)
+        return
+    if args.c5_only:
+        import torch
+        from paper_1302_5010_gb300 import mpl
+        print(json.dumps(streaming_warm_vs_cold(args, mpl, torch, torch.device("cuda", 0))), flush=True)
         return
     if args.corr_shape:
         correlation_microbench(args)
@@ -639,6 +788,9 @@ def main():
             "kernels": other["kernels"], "clocks": other["clocks"], "autotune": other["autotune"],
             "warm_start": False}
         line["speedup_vs_" + names[1 - precision].replace("-", "_")] = main_run["value"] / other["value"]
+    if rank == 0 and not args.no_c5 and args.config != "c5":
+        # the streaming workload's warm start against the cold solve (extra keys, rank 0 only)
+        line["c5_streaming"] = streaming_warm_vs_cold(args, mpl, torch, dev)
     if n_err:
         cb, Xo = cpu_baseline(args.config, P, n_err)
         line["cpu_baseline"] = cb

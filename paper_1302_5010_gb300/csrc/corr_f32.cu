@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256) k_corr_f32(Dev d, int cur, int jtile0) {
 
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl) {
     if (act_n_ub <= 0) return cudaSuccess;
+    if (gemv_route(d, act_n_ub)) return launch_corr_gemv(d, cur, act_n_ub, false, s, nl);
     const int tiles_m = (d.m + BM - 1) / BM;
     const bool vec = (d.n % 4) == 0;
     for (int t0 = 0; t0 < tiles_m; t0 += 65535) {  // grid.y is at most 65535

@@ -395,6 +395,7 @@ cudaError_t prepare_corr_bf16() {
 cudaError_t launch_corr_bf16(const Dev& d, int cur, const void* tmap, int act_n_ub, int sms, cudaStream_t s,
                              int64_t* nl, int bn) {
     if (act_n_ub <= 0) return cudaSuccess;
+    if (gemv_route(d, act_n_ub)) return launch_corr_gemv(d, cur, act_n_ub, true, s, nl);
     cudaError_t ep = prepare_corr_bf16();
     if (ep != cudaSuccess) return ep;
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(tmap);

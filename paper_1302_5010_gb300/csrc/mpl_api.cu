@@ -126,12 +126,15 @@ mpl_status_t from_cuda(cudaError_t e) {
     return MPL_ERR_CUDA;
 }
 
+// A failed allocation is not sticky, but it stays the thread's last error: it is cleared
+// here so that the launch checks of a later call do not report it again.
 #define CK(x)                                               \
     do {                                                    \
         cudaError_t e_ = (x);                               \
         if (e_ != cudaSuccess) {                            \
             if (getenv("MPL_DEBUG"))                        \
                 fprintf(stderr, "mpl: %s failed: %s (%s:%d)\n", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            if (e_ == cudaErrorMemoryAllocation) (void)cudaGetLastError(); \
             return from_cuda(e_);                           \
         }                                                   \
     } while (0)
@@ -555,20 +558,29 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
 // Q = A^T A, once per handle (identity route, Gram gather).
 static mpl_status_t ensure_q(mpl_ctx* h, cudaStream_t st, int64_t* nl) {
     const int n = h->n, m = h->m;
-    if (!h->Q) {
-        CK(cudaMalloc(&h->Q, (size_t)m * m * sizeof(float)));
-        int* act = nullptr;
-        Counters* cnt = nullptr;
-        CK(cudaMalloc(&act, (size_t)m * sizeof(int)));
-        CK(cudaMalloc(&cnt, sizeof(Counters)));
-        const cudaError_t e = build_gram_q(h->A32, n, m, h->Q, act, cnt, st, nl);
-        const cudaError_t es = cudaStreamSynchronize(st);
-        cudaFree(act);
-        cudaFree(cnt);
+    if (h->Q) return MPL_OK;
+    // m^2 floats: 17 GB for 65536 atoms, 4 TB for 2^20 (refused before any allocation)
+    const size_t bytes = (size_t)m * m * sizeof(float);
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    if (bytes > free_b) return MPL_ERR_OOM;
+    float* Q = nullptr;
+    int* act = nullptr;
+    Counters* cnt = nullptr;
+    cudaError_t e = cudaMalloc(&Q, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&act, (size_t)m * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(Counters));
+    if (e == cudaSuccess) e = build_gram_q(h->A32, n, m, Q, act, cnt, st, nl);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    cudaFree(act);
+    cudaFree(cnt);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) {
+        cudaFree(Q);  // no half-built Q stays behind
         CK(e);
-        CK(es);
-        clear_graphs(h);
     }
+    h->Q = Q;
+    clear_graphs(h);
     return MPL_OK;
 }
 

@@ -175,6 +175,12 @@ struct PropArgs {
 // ---------------------------------------------------------------- launchers
 // Each returns the CUDA error of its launch and adds its launches to *nl.
 cudaError_t launch_corr_f32(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
+// Matrix-vector correlations for at most GEMV_P active signals (n >= GEMV_MIN_N): the FP32
+// and BF16 launchers take this route themselves when gemv_route holds.
+constexpr int GEMV_P = 8;
+constexpr int GEMV_MIN_N = 256;
+bool gemv_route(const Dev& d, int act_n_ub);
+cudaError_t launch_corr_gemv(const Dev& d, int cur, int act_n_ub, bool bf16, cudaStream_t s, int64_t* nl);
 // BF16 tensor-core correlation (tcgen05 + TMA).  prepare() encodes the TMA
 // descriptors for A16 (m x n) and R16c (pmax x n, one per tile width) into tmap
 // (TC_TMAP_BYTES).  bn: signals per output tile, 64, 128 or 256.

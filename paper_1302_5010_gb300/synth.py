@@ -110,21 +110,31 @@ def sparse_codes(m: int, p: int, kmin: int, kmax: int, values: str, rng) -> np.n
 
 def gaussian_problem(n: int, m: int, p: int, kmin: int, kmax: int, values: str, sigma: float,
                      lam_frac: float, rho: int, seed_A: int, seed_B: int, name: str = "gauss",
-                     At: Optional[np.ndarray] = None) -> Problem:
-    """Compressive-sensing batch: b_i = A x_i + e_i with e_i ~ N(0, sigma^2 I)."""
+                     At: Optional[np.ndarray] = None, noise: str = "gaussian") -> Problem:
+    """Compressive-sensing batch: b_i = A x_i + e_i with e_i ~ N(0, sigma^2 I), or with
+    noise="uniform" e_i ~ U[-sigma, sigma]^n (the noise of the paper's Sec. 4 experiments)."""
     if At is None:
         At = gaussian_dictionary(n, m, seed_A)
     rng = _rng(seed_B)
     X = sparse_codes(m, p, kmin, kmax, values, rng)
-    A64 = At.astype(np.float64)
     B = np.empty((p, n), dtype=np.float32)
     for i in range(p):
         nz = np.nonzero(X[i])[0]
-        b = A64[nz].T @ X[i, nz] + sigma * rng.standard_normal(n)
+        e = sigma * rng.standard_normal(n) if noise == "gaussian" else rng.uniform(-sigma, sigma, n)
+        b = At[nz].astype(np.float64).T @ X[i, nz] + e
         B[i] = b.astype(np.float32)
     lam = lambdas_from_fraction(At, B, lam_frac)
-    return Problem(name, At, B, lam, rho, X, dict(n=n, m=m, p=p, kmin=kmin, kmax=kmax,
-                                                 values=values, sigma=sigma, lam_frac=lam_frac))
+    return Problem(name, At, B, lam, rho, X, dict(n=n, m=m, p=p, kmin=kmin, kmax=kmax, values=values,
+                                                 sigma=sigma, noise=noise, lam_frac=lam_frac))
+
+
+def big_dictionary_problem(n: int = 1024, m: int = 1 << 18, k: int = 150, rho: int = 20,
+                           lam_frac: float = 0.005, seed: int = 0, p: int = 1) -> Problem:
+    """The big-dictionary single-signal setting of the paper's Sec. 4.6 (there 2^12 x 2^20,
+    k in 300..800), at the caller's size: Gaussian unit-norm atoms, a k-sparse code with
+    N(0, 1) entries, noise U[-0.01, 0.01] (Sec. 4.1) and lambda = 0.005 ||A^T b||_inf."""
+    return gaussian_problem(n, m, p, k, k, "gaussian", 0.01, lam_frac, rho, seed_A=30_000 + seed,
+                            seed_B=40_000 + seed, name=f"bigdict{n}x{m}", noise="uniform")
 
 
 def face_problem(n: int = 1024, classes: int = 100, per_class: int = 90, rank: int = 9,
@@ -207,3 +217,32 @@ def small_problem(n: int, m: int, p: int, kmin: int, kmax: int, rho: int, lam_fr
     """A reduced Gaussian workload for parity tests (sizes chosen by the caller)."""
     return gaussian_problem(n, m, p, kmin, kmax, values, sigma, lam_frac, rho,
                             seed_A=10_000 + seed, seed_B=20_000 + seed, name=name)
+
+
+def big_dictionary_device(n: int = 4096, m: int = 1 << 20, k: int = 600, lam_frac: float = 0.005,
+                          seed: int = 0, device: str = "cuda"):
+    """The Sec. 4.6 setting at the paper's full size (2^12 x 2^20 atoms: 16 GiB in FP32),
+    drawn on the device with torch's seeded Philox generator (a host draw of 4.3e9 normals
+    takes minutes): Gaussian atoms normalised to unit norm, a k-sparse N(0, 1) code, noise
+    U[-0.01, 0.01], lambda = lam_frac ||A^T b||_inf evaluated in float64 and rounded to
+    float32.  Returns (At (m, n) float32, b (1, n) float32, lam (1,) float32, support (k,)
+    int64, values (k,) float64) as device tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(50_000 + seed)
+    At = torch.empty((m, n), dtype=torch.float32, device=device)
+    step = max(1, (1 << 28) // n)
+    for j0 in range(0, m, step):
+        blk = At[j0:j0 + step]
+        blk.normal_(generator=g)
+        blk /= torch.linalg.vector_norm(blk.double(), dim=1, keepdim=True).float()
+    supp = torch.randperm(m, generator=g, device=device)[:k]
+    vals = torch.randn(k, generator=g, device=device, dtype=torch.float64)
+    e = (torch.rand(n, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0) * 0.01
+    b64 = At[supp].double().T @ vals + e
+    b = b64.float()
+    amax = torch.zeros((), dtype=torch.float64, device=device)
+    for j0 in range(0, m, step):
+        amax = torch.maximum(amax, (At[j0:j0 + step].double() @ b.double()).abs().max())
+    lam = (lam_frac * amax).float().reshape(1)
+    return At, b.reshape(1, n), lam, supp, vals

@@ -15,7 +15,9 @@ from paper_1302_5010_gb300 import mpl
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(256, 1000, 1), (256, 1000, 37), (1000, 2050, 130), (1024, 8192, 256), (4096, 4096, 300)]
+# (p <= 8 with n >= 256 takes the matrix-vector route, the others the GEMMs)
+SHAPES = [(256, 1000, 1), (256, 1000, 37), (1000, 2050, 130), (1024, 8192, 256), (4096, 4096, 300),
+          (1024, 40000, 3), (2048, 30000, 8), (1000, 20001, 5)]
 
 
 def _bf16(x):
