@@ -58,10 +58,15 @@ ERR_SIGNALS = 64
 
 def workload_desc(cfg: str, P, path: str) -> dict:
     meta = P.meta
+    if "classes" in meta:
+        what = (f"{cfg}: A = [D I] {P.n}x{P.m}, D {meta['classes']} classes x {meta['per_class']} atoms of "
+                f"rank-{meta['rank']} subspaces (pixel-like, unit norm), I for occlusion; p={P.p} queries with "
+                f"{int(100 * meta['corrupt'])}% of pixels corrupted")
+    else:
+        what = (f"{cfg}: A {P.n}x{P.m} Gaussian unit-norm atoms, p={P.p} signals, "
+                f"k~U[{meta.get('kmin')},{meta.get('kmax')}], sigma={meta.get('sigma')}")
     return {
-        "workload": (f"{cfg}: A {P.n}x{P.m} Gaussian unit-norm atoms, p={P.p} signals, "
-                     f"k~U[{meta.get('kmin')},{meta.get('kmax')}], sigma={meta.get('sigma')}, "
-                     f"lambda_i={meta.get('lam_frac')}*||A^T b_i||_inf, rho={P.rho}, tol={TOL}"),
+        "workload": f"{what}, lambda_i={meta.get('lam_frac')}*||A^T b_i||_inf, rho={P.rho}, tol={TOL}",
         "n": P.n, "m": P.m, "p": P.p, "rho": P.rho, "tol": TOL, "path": path,
         "l2": "flushed between timed steps (256 MiB write)",
     }

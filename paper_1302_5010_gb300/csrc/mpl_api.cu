@@ -864,11 +864,26 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
     double graph_phase[16] = {0};
     int t = 0;
+#ifdef MPL_TIMELINE
+    // diagnostic build: device timestamps of every iteration's parts and finish
+    struct Mark { int t, kind; cudaEvent_t e; };
+    std::vector<Mark> marks;
+    auto mark = [&](int kind, cudaStream_t s_) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s_);
+        marks.push_back({t, kind, e});
+    };
+    mark(-1, st);
+#endif
     for (; live > 0 && t < hard_cap; ++t) {
         const int par = t & 1;
         cudaStream_t fin_st = par ? h->side_odd : h->side;
         // the finish of iteration t - 2 (same parity) is done before its signals re-enter
         CK(cudaStreamWaitEvent(st, h->ev_fin[par], 0));
+#ifdef MPL_TIMELINE
+        mark(0, st);
+#endif
         for (int part = 0; part < 2; ++part) {
             if (graph) {
                 size_t gi = 0;
@@ -885,11 +900,21 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                 CK(cudaEventRecord(h->ev_sel, st));
                 CK(cudaStreamWaitEvent(fin_st, h->ev_sel, 0));
                 cudaEvent_t f0 = pt.begin(fin_st);
+#ifdef MPL_TIMELINE
+                mark(1, st);
+                mark(3, fin_st);
+#endif
                 CK(launch_finish(d, par, graph ? p : live, finish_scap(h, d, t), fin_st, &nl));
                 pt.end(4, f0, fin_st);
                 CK(cudaEventRecord(h->ev_fin[par], fin_st));
+#ifdef MPL_TIMELINE
+                mark(4, fin_st);
+#endif
             }
         }
+#ifdef MPL_TIMELINE
+        mark(2, st);
+#endif
         const bool last = t + 1 >= hard_cap;
         if ((t + 1) % h->sync_every == 0 || last) {
             CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
@@ -902,6 +927,10 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
             // active next iteration, plus the signals of the last two finishes
             live = h->cnt_h->act_n[(t & 1) ^ 1] + h->cnt_h->fin_par[0] + h->cnt_h->fin_par[1];
+#ifdef MPL_TIMELINE
+            fprintf(stderr, "TC %d %d %d %d\n", t, h->cnt_h->act_n[(t & 1) ^ 1], h->cnt_h->fin_par[t & 1],
+                    h->cnt_h->grow_n);
+#endif
             if (graph && h->profile) {
                 for (size_t gi : window)
                     for (auto& mk : h->graphs[gi].marks) {
@@ -937,6 +966,14 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     CK(cudaStreamSynchronize(st));
     if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
     pt.collect();
+#ifdef MPL_TIMELINE
+    for (auto& mk : marks) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, marks[0].e, mk.e);
+        fprintf(stderr, "TL %d %d %.4f\n", mk.t, mk.kind, ms);
+    }
+    for (auto& mk : marks) cudaEventDestroy(mk.e);
+#endif
     for (int k = 1; k < 7; ++k) h->phase_ms[k] += graph_phase[k];
     h->phase_ms[PH_QROUTE] += graph_phase[PH_QROUTE];
     h->phase_ms[7] = (double)h->cnt_h->cols;  // columns the correlation processed
