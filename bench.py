@@ -484,7 +484,8 @@ def solve_once(args):
     At = torch.from_numpy(P.At).to(dev)
     B = torch.from_numpy(P.B).to(dev)
     lam = torch.from_numpy(P.lam).to(dev)
-    opts = dict(qgram=args.solve_qgram, graph=args.solve_graph, sync_every=args.solve_sync)
+    opts = dict(qgram=args.solve_qgram, graph=args.solve_graph, sync_every=args.solve_sync,
+                qroute=args.solve_qroute)
     if SMAX.get(args.solve_once):
         opts["smax"] = SMAX[args.solve_once]
     if args.path == "mixed":
@@ -721,6 +722,7 @@ def main():
     ap.add_argument("--solve-qgram", type=int, default=1)
     ap.add_argument("--solve-graph", type=int, default=1)
     ap.add_argument("--solve-sync", type=int, default=4)
+    ap.add_argument("--solve-qroute", type=int, default=0, help="identity route bound of the --solve-once run")
     args = ap.parse_args()
     if args.solve_once:
         solve_once(args)

@@ -579,6 +579,7 @@ struct FinShared {
     float cs[2]; // rotation of the factor update
     float rot[2][2];  // rotations of the CTA-wide update, alternating slots
     int cg;      // 1: solves by conjugate gradients on the Gram block (no factor)
+    uint64_t cbar;  // cluster barrier of a clustered finish (C arrivals per phase)
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -976,10 +977,10 @@ __device__ double dot_ff(const float* __restrict__ a, const float* __restrict__ 
 // 4t + 4 nt c; the atom columns are read as float4, eight atoms per round so
 // that eight loads are in flight.  Each entry sums the atoms in order of P, as
 // residual_df does.
-__device__ void residual_df4(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
-                             const float* __restrict__ b, float* rh, float* rl) {
+__device__ void residual_df4_range(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
+                                   const float* __restrict__ b, float* rh, float* rl, int k_lo, int k_hi) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = tid * 4; k < n; k += nt * 4) {
+    for (int k = k_lo + tid * 4; k < k_hi; k += nt * 4) {
         const float4 bv = __ldg(reinterpret_cast<const float4*>(b + k));
         df c0{bv.x, 0.f}, c1{bv.y, 0.f}, c2{bv.z, 0.f}, c3{bv.w, 0.f};
         int a = 0;
@@ -1007,6 +1008,11 @@ __device__ void residual_df4(const float* __restrict__ A, int n, const int* Pi, 
         *reinterpret_cast<float4*>(rh + k) = make_float4(c0.hi, c1.hi, c2.hi, c3.hi);
         *reinterpret_cast<float4*>(rl + k) = make_float4(c0.lo, c1.lo, c2.lo, c3.lo);
     }
+}
+
+__device__ __forceinline__ void residual_df4(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
+                                             const float* __restrict__ b, float* rh, float* rl) {
+    residual_df4_range(A, n, Pi, xd, np, b, rh, rl, 0, n);
 }
 
 // out[a] = a_{idx[a]}^T r for a < cnt, in double-FP32, two atoms per warp at a
@@ -1260,12 +1266,130 @@ __device__ __noinline__ int cg_solve(FinShared& sh, const float* Gi, int smax, i
     return ok ? it : -1;
 }
 
+// ---------------------------------------------------------------- cluster finish
+// When few signals finish at once (the last outer iterations, where each finish sits on the
+// critical path), a signal's finish runs on a cluster of C CTAs (C SMs).  Every CTA runs the
+// whole finish on identical data, so their control flow is identical; only the column sweeps
+// are divided: the exact residual by row blocks of n / C entries, the correlations by blocks
+// of the atom list, after which every CTA reads the other blocks from its peers' shared
+// memory (distributed shared memory).  Before such reads, and before a CTA overwrites what
+// its peers may still read, the cluster meets at a barrier built on one mbarrier per CTA
+// (C arrivals, one remote arrive from each CTA), waited on with a bound: on expiry the CTA
+// records DERR_TIMEOUT and the finish returns without its result.
+constexpr uint64_t FIN_CLUSTER_WAIT_NS = 4000000000ull;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Generic address of the same shared-memory object in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T* peer_ptr(T* p, unsigned rank) {
+    uint64_t out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+    return reinterpret_cast<T*>(out);
+}
+
+struct ClusterSync {
+    uint64_t* bar;  // this CTA's barrier (count C)
+    int C;
+    unsigned phase;
+};
+
+// All threads of all C CTAs: returns false (uniformly within the CTA) when the wait expired.
+__device__ bool csync(const Dev& d, ClusterSync& cs) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(cs.bar));
+        for (int r = 0; r < cs.C; ++r) {
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+        }
+    }
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(cs.bar));
+    const uint32_t parity = cs.phase & 1u;
+    bool ok = false;
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) { ok = true; break; }
+        if ((it & 255u) == 0u) {
+            uint64_t now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            if (it == 0) t0 = now;
+            else if (now - t0 > FIN_CLUSTER_WAIT_NS) break;
+        }
+    }
+    ++cs.phase;
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && threadIdx.x == 0) atomicCAS(&d.cnt->err, 0, (int)DERR_TIMEOUT);
+    return ok;
+}
+
+// Block b of [0, len) split into C parts (multiples of `align`).
+__device__ __forceinline__ void part_of(int len, int C, int b, int align, int* lo, int* hi) {
+    const int per = (((len + C - 1) / C) + align - 1) / align * align;
+    *lo = min(len, b * per);
+    *hi = min(len, *lo + per);
+}
+
+// r = b - A_P x: this CTA's row block, then the other blocks from the peers.
+__device__ bool residual_cluster(const Dev& d, ClusterSync& cs, unsigned rank, const float* A, int n,
+                                 const int* Pi, const df* xd, int np, const float* b, float* rh, float* rl) {
+    int lo, hi;
+    part_of(n, cs.C, (int)rank, 4, &lo, &hi);
+    residual_df4_range(A, n, Pi, xd, np, b, rh, rl, lo, hi);
+    if (!csync(d, cs)) return false;
+    for (int q = 1; q < cs.C; ++q) {
+        const unsigned pr = (rank + q) % cs.C;
+        int plo, phi;
+        part_of(n, cs.C, (int)pr, 4, &plo, &phi);
+        const float4* sh4 = reinterpret_cast<const float4*>(peer_ptr(rh, pr));
+        const float4* sl4 = reinterpret_cast<const float4*>(peer_ptr(rl, pr));
+        for (int k = plo + 4 * (int)threadIdx.x; k < phi; k += 4 * (int)blockDim.x) {
+            reinterpret_cast<float4*>(rh)[k >> 2] = sh4[k >> 2];
+            reinterpret_cast<float4*>(rl)[k >> 2] = sl4[k >> 2];
+        }
+    }
+    return csync(d, cs);  // no peer overwrites its block before every CTA has read it
+}
+
+// out[a] = a_{idx[a]}^T r for a < cnt: this CTA's block of atoms, then the others' results.
+__device__ bool dots_cluster(const Dev& d, ClusterSync& cs, unsigned rank, const float* A, int n, const int* idx,
+                             int cnt, const float* rh, const float* rl, double* out) {
+    int lo, hi;
+    part_of(cnt, cs.C, (int)rank, 2, &lo, &hi);
+    if (hi > lo) dots_df_warp(A, n, idx + lo, hi - lo, rh, rl, out + lo);
+    if (!csync(d, cs)) return false;
+    for (int q = 1; q < cs.C; ++q) {
+        const unsigned pr = (rank + q) % cs.C;
+        int plo, phi;
+        part_of(cnt, cs.C, (int)pr, 2, &plo, &phi);
+        const double* po = peer_ptr(out, pr);
+        for (int a = plo + (int)threadIdx.x; a < phi; a += (int)blockDim.x) out[a] = po[a];
+    }
+    return csync(d, cs);
+}
+
 // NT = FIN_THREADS (two CTAs per SM) or FIN_THREADS_WIDE (one CTA per SM, taken when the
 // shared-memory layout allows only one anyway: the wider CTA shortens the latency-bound
 // sweeps over the support's columns).
+// C > 1: a cluster of C CTAs per signal (C consecutive blocks), see csync.
 template <int NT>
-__global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int cur, int scap, int msm, int rsm) {
-    const int g = blockIdx.x;
+__global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int cur, int scap, int msm, int rsm,
+                                                                      int C) {
+    const int g = blockIdx.x / C;
     if (g >= d.cnt->fin_par[cur]) return;
     const int i = d.list_fin[cur][g];
     extern __shared__ __align__(16) double fsm[];
@@ -1290,7 +1414,10 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         // an odd stride spreads a column over the banks
         const bool fsm = s <= msm;
         sh.F.ldf = fsm ? ((msm + 1) | 1) : ((scap + 1) | 1);
-        sh.F.Mf = fsm ? q : reinterpret_cast<float*>(d.chol + (size_t)i * smax * smax);
+        // the factor workspace: the signal's own, or in a clustered finish this CTA's slot of
+        // the pool (the CTAs of a cluster factor the same block side by side)
+        double* wk = C > 1 ? d.fin_pool + (size_t)blockIdx.x * smax * smax : d.chol + (size_t)i * smax * smax;
+        sh.F.Mf = fsm ? q : reinterpret_cast<float*>(wk);
         if (msm) q += (size_t)msm * ((msm + 1) | 1);
         sh.F.stage = msm ? nullptr : q;  // panel staging for a factor in global memory
         sh.F.stage_n = msm ? 0 : fac_stage_floats(scap);
@@ -1304,15 +1431,30 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         float* rbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sh.adds + scap) + 15) & ~(uintptr_t)15);
         sh.rh = rsm ? rbase : d.R32 + (size_t)i * d.n;
         sh.rl = rsm ? rbase + d.n : d.R32lo + (size_t)i * d.n;
-        sh.F.Md = d.chol + (size_t)i * smax * smax;  // shares the workspace with a global FP32 factor
+        sh.F.Md = wk;  // shares the workspace with a global FP32 factor
         sh.F.ldd = smax;
         sh.F.fp64 = 0;
         // supports too large for a shared-memory factor are solved by conjugate gradients on
         // the Gram block (their vectors in the staging area); a factor in global memory is the
         // fallback when CG does not converge
         sh.cg = (msm == 0 && s > FIN_CG_MIN_S) ? 1 : 0;
+        if (C > 1) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                             static_cast<uint32_t>(__cvta_generic_to_shared(&sh.cbar))),
+                         "r"(C)
+                         : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     __syncthreads();
+    // every CTA's barrier is initialised before any remote arrive (reached by all CTAs of the
+    // cluster: the returns above depend only on the signal, which they share)
+    if (C > 1) {
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+    const unsigned rank = C > 1 ? cluster_rank() : 0u;
+    ClusterSync cs{&sh.cbar, C, 0u};
     float* cgv = msm ? nullptr
                      : reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sh.F.stage) + 15) & ~(uintptr_t)15);
     const double lam = (double)d.lam[i];
@@ -1337,6 +1479,8 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         sh.sg[a] = lam0 ? 1 : (v > 0.f ? 1 : (v < 0.f ? -1 : 0));
     }
     __syncthreads();
+    // every CTA of a cluster has read the signal's point before the first one can write it back
+    if (C > 1 && !csync(d, cs)) return;
 
     FT_BEGIN
     bool ok = false;
@@ -1490,7 +1634,11 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             FX_BEGIN
             FT_CNT(11);
             if (vec4) {
-                residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+                if (C > 1) {
+                    if (!residual_cluster(d, cs, rank, d.A32, n, sh.Pi, xd, np, b, rh, rl)) return;
+                } else {
+                    residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
+                }
             } else {
                 residual_df(d.A32, n, sh.Pi, xd, np, b, rh, rl);
             }
@@ -1499,7 +1647,11 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             bytes += 8ull * n * np + 4ull * n;  // the support's columns twice, and b
             double lmax = 0.0;
             if (vec4) {
-                dots_df_warp(d.A32, n, sh.Pi, np, rh, rl, sh.w);
+                if (C > 1) {
+                    if (!dots_cluster(d, cs, rank, d.A32, n, sh.Pi, np, rh, rl, sh.w)) return;
+                } else {
+                    dots_df_warp(d.A32, n, sh.Pi, np, rh, rl, sh.w);
+                }
                 __syncthreads();
                 for (int a = tid; a < np; a += nt) {
                     const double dv = sh.w[a] - lam * (double)sh.sg[sh.P[a]];
@@ -1608,7 +1760,11 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             }
             __syncthreads();
             const int nz = sh.ival[2];
-            dots_df_warp(d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np);
+            if (C > 1) {
+                if (!dots_cluster(d, cs, rank, d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np)) return;
+            } else {
+                dots_df_warp(d.A32, n, sh.Pi + np, nz, rh, rl, sh.w + np);
+            }
             __syncthreads();
             for (int k = tid; k < nz; k += nt) {
                 const double ca = sh.w[np + k];
@@ -1658,9 +1814,14 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         break;
     }
 
-    if (tid == 0) {
+    // (the CTAs of a cluster hold the same result: the first one writes it)
+    if (tid == 0 && rank == 0) {
         atomicAdd(&d.cnt->fin_flops, flops);
         atomicAdd(&d.cnt->fin_bytes, bytes);
+    }
+    if (rank != 0) {
+        csync(d, cs);  // the peers' reads of this CTA's shared memory are over
+        return;
     }
     if (ok) {
         double* x64 = d.xS64 + (size_t)i * smax;
@@ -1741,6 +1902,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             }
         }
     }
+    if (C > 1) csync(d, cs);
 }
 
 }  // namespace
@@ -1757,7 +1919,7 @@ cudaError_t prepare_finish() {
     return e;
 }
 
-cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl) {
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl, int sms) {
     if (ub <= 0) return cudaSuccess;
     scap = ((scap + 31) / 32) * 32;
     if (scap > d.smax) scap = d.smax;
@@ -1774,8 +1936,31 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t 
     const size_t dyn = dyn_of(msm, rsm);
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
-    if (dyn > FIN_SMEM_TWO_CTAS) k_finish<FIN_THREADS_WIDE><<<ub, FIN_THREADS_WIDE, dyn, s>>>(d, cur, scap, msm, rsm);
-    else k_finish<FIN_THREADS><<<ub, FIN_THREADS, dyn, s>>>(d, cur, scap, msm, rsm);
+    // a cluster per signal when the finishing signals leave most SMs idle (at most ub of them;
+    // clusters of C so that C ub stays within two CTAs per SM); the row-block exchange needs
+    // the residual pair in shared memory and float4 rows
+    // (-DMPL_NO_FIN_CLUSTER builds one CTA per signal only, for comparisons)
+    int C = 1;
+#if !defined(MPL_NO_FIN_CLUSTER)
+    if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
+        while (C < FIN_CLUSTER_MAX && 2 * C * ub <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
+#endif
+    const bool wide = dyn > FIN_SMEM_TWO_CTAS;
+    cudaLaunchConfig_t c{};
+    c.gridDim = dim3((unsigned)(ub * C));
+    c.blockDim = dim3(wide ? FIN_THREADS_WIDE : FIN_THREADS);
+    c.dynamicSmemBytes = dyn;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    c.attrs = at;
+    c.numAttrs = C > 1 ? 1 : 0;
+    const cudaError_t e = wide ? cudaLaunchKernelEx(&c, k_finish<FIN_THREADS_WIDE>, d, cur, scap, msm, rsm, C)
+                               : cudaLaunchKernelEx(&c, k_finish<FIN_THREADS>, d, cur, scap, msm, rsm, C);
+    if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
 }

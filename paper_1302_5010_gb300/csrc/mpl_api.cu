@@ -214,6 +214,10 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.h, ps));
     CK(alloc(h, &d.ritz, ps));
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
+    // the CTAs of a clustered finish each factor in a workspace of their own (at most
+    // FIN_CLUSTER_MAX per signal and two CTAs per SM in one launch)
+    d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
+    CK(alloc(h, &d.fin_pool, (size_t)d.fin_slots * smax * smax));
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],
                     &d.list_fin[1], &d.reent[0], &d.reent[1], &d.list_apg, &d.explore, &d.early};
@@ -904,7 +908,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                 mark(1, st);
                 mark(3, fin_st);
 #endif
-                CK(launch_finish(d, par, graph ? p : live, finish_scap(h, d, t), fin_st, &nl));
+                CK(launch_finish(d, par, std::min(p, live), finish_scap(h, d, t), fin_st, &nl, h->sms));
                 pt.end(4, f0, fin_st);
                 CK(cudaEventRecord(h->ev_fin[par], fin_st));
 #ifdef MPL_TIMELINE

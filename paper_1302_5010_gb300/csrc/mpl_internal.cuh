@@ -118,6 +118,8 @@ struct Dev {
     float* h;                    // p x smax A_S^T b
     float* ritz;                 // p x smax power-iteration vector (warm start of L)
     double* chol;                // p x smax x smax FP64 workspace (large supports)
+    double* fin_pool;            // fin_slots more such workspaces: one per CTA of a clustered finish
+    int fin_slots;
     int* state;                  // p SigState
     int* ssize;                  // p |S_i|
     int* snew;                   // p atoms appended this iteration
@@ -207,8 +209,11 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
 // Gram growth gathered from Q (MPL_OPT_QGRAM): same outputs, bit for bit, as launch_gram.
 cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 // The exact finish of the signals the selection of an iteration with parity cur sent to it
-// (list_fin[cur]); each finished signal that is not done joins reent[cur].
-cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl);
+// (list_fin[cur]); each finished signal that is not done joins reent[cur].  ub bounds the
+// number of finishing signals; when ub is small against the sms SMs a signal's finish runs on
+// a cluster of up to FIN_CLUSTER_MAX CTAs.
+constexpr int FIN_CLUSTER_MAX = 8;
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl, int sms);
 // Append reent[cur] to the active list of an iteration with parity cur (rows for the GEMM
 // included); the finishes that filled it must be complete.
 cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl);
