@@ -39,11 +39,11 @@ namespace mpl {
 //  of the factor: support + right-hand side, Gram gather]
 __device__ long long g_fin_trace[8192][16];
 #define FT_BEGIN long long ft0_ = clock64(), fx_ = 0;
-#define FT_SPLIT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; } while (0)
-#define FT_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
-#define FT_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
+#define FT_SPLIT(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; } while (0)
+#define FT_ADD(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
+#define FT_CNT(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
 #define FX_BEGIN fx_ = clock64();
-#define FX_END(slot) do { if (threadIdx.x == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - fx_; } while (0)
+#define FX_END(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - fx_; } while (0)
 #else
 #define FX_BEGIN
 #define FX_END(slot) do {} while (0)
@@ -1015,6 +1015,68 @@ __device__ __forceinline__ void residual_df4(const float* __restrict__ A, int n,
     residual_df4_range(A, n, Pi, xd, np, b, rh, rl, 0, n);
 }
 
+// The same rows [k_lo, k_hi) when they are fewer than the CTA's threads (a cluster's block
+// of a short residual): thread g nv + v takes float4 slot v and the atoms g, g + G, ... of P
+// (G groups), group 0 starting from b; the groups' double-FP32 partial sums meet in scratch
+// (blockDim.x x 8 floats) and are added in group order.  Ends with the CTA synchronised.
+__device__ void residual_df4_groups(const float* __restrict__ A, int n, const int* Pi, const df* xd, int np,
+                                    const float* __restrict__ b, float* rh, float* rl, int k_lo, int k_hi, int G,
+                                    float* scratch) {
+    const int tid = threadIdx.x;
+    const int nv = (k_hi - k_lo) >> 2;
+    const int g = tid / nv, v = tid - g * nv;
+    if (g < G) {
+        const int k = k_lo + 4 * v;
+        df c0{0.f, 0.f}, c1 = c0, c2 = c0, c3 = c0;
+        if (g == 0) {
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(b + k));
+            c0.hi = bv.x; c1.hi = bv.y; c2.hi = bv.z; c3.hi = bv.w;
+        }
+        int a = g;
+        for (; a + 7 * G < np; a += 8 * G) {
+            float4 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                w[u] = __ldg(reinterpret_cast<const float4*>(A + (size_t)Pi[a + u * G] * n + k));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const df x = xd[a + u * G];
+                c0 = df_fma(c0, -w[u].x, x);
+                c1 = df_fma(c1, -w[u].y, x);
+                c2 = df_fma(c2, -w[u].z, x);
+                c3 = df_fma(c3, -w[u].w, x);
+            }
+        }
+        for (; a < np; a += G) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(A + (size_t)Pi[a] * n + k));
+            const df x = xd[a];
+            c0 = df_fma(c0, -w.x, x);
+            c1 = df_fma(c1, -w.y, x);
+            c2 = df_fma(c2, -w.z, x);
+            c3 = df_fma(c3, -w.w, x);
+        }
+        float4* sp = reinterpret_cast<float4*>(scratch + (size_t)tid * 8);
+        sp[0] = make_float4(c0.hi, c0.lo, c1.hi, c1.lo);
+        sp[1] = make_float4(c2.hi, c2.lo, c3.hi, c3.lo);
+    }
+    __syncthreads();
+    if (tid < nv) {
+        const float4* s0 = reinterpret_cast<const float4*>(scratch + (size_t)tid * 8);
+        df c0{s0[0].x, s0[0].y}, c1{s0[0].z, s0[0].w}, c2{s0[1].x, s0[1].y}, c3{s0[1].z, s0[1].w};
+        for (int q = 1; q < G; ++q) {
+            const float4* sq = reinterpret_cast<const float4*>(scratch + (size_t)(q * nv + tid) * 8);
+            c0 = df_add(c0, df{sq[0].x, sq[0].y});
+            c1 = df_add(c1, df{sq[0].z, sq[0].w});
+            c2 = df_add(c2, df{sq[1].x, sq[1].y});
+            c3 = df_add(c3, df{sq[1].z, sq[1].w});
+        }
+        const int k = k_lo + 4 * tid;
+        *reinterpret_cast<float4*>(rh + k) = make_float4(c0.hi, c1.hi, c2.hi, c3.hi);
+        *reinterpret_cast<float4*>(rl + k) = make_float4(c0.lo, c1.lo, c2.lo, c3.lo);
+    }
+    __syncthreads();
+}
+
 // out[a] = a_{idx[a]}^T r for a < cnt, in double-FP32, two atoms per warp at a
 // time (n % 4 == 0): lane l takes the float4 slices k = 4l + 128q, up to eight
 // slices of both atoms in flight per round, the residual pair from shared
@@ -1141,131 +1203,6 @@ __device__ __forceinline__ float bsumf(float v, double* red) {
     return t;
 }
 
-// q_a = (G_SS v)_a for the support positions a = P[k] (v is zero outside P, so this is
-// G_PP v_P): a warp per pair of rows, the row's first s entries as float4 slices when the
-// block's leading dimension allows (else scalar), fixed butterfly per row.
-__device__ __noinline__ void gram_rows_mv(const float* __restrict__ Gi, int smax, int s, const int* P, int np,
-                             const float* v, float* q) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bool vec = (smax & 3) == 0;
-    for (int k = 2 * warp; k < np; k += 2 * nw) {
-        const int ra = P[k], rb = k + 1 < np ? P[k + 1] : P[k];
-        const float* ga = Gi + (size_t)ra * smax;
-        const float* gb = Gi + (size_t)rb * smax;
-        float sa = 0.f, sb = 0.f;
-        for (int c0 = 4 * lane; c0 < s; c0 += 512) {
-            float4 a4[4], b4[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + 128 * u;
-                if (c < s) {
-                    if (vec) {
-                        a4[u] = __ldg(reinterpret_cast<const float4*>(ga + c));
-                        b4[u] = __ldg(reinterpret_cast<const float4*>(gb + c));
-                    } else {
-                        a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
-                                            c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
-                        b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
-                                            c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
-                    }
-                } else {
-                    a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + 128 * u;
-                if (c < s) {
-                    // v has zeros from s up to the next multiple of 4 (and outside P)
-                    const float4 x = *reinterpret_cast<const float4*>(v + c);
-                    sa = fmaf(a4[u].x, x.x, sa); sa = fmaf(a4[u].y, x.y, sa);
-                    sa = fmaf(a4[u].z, x.z, sa); sa = fmaf(a4[u].w, x.w, sa);
-                    sb = fmaf(b4[u].x, x.x, sb); sb = fmaf(b4[u].y, x.y, sb);
-                    sb = fmaf(b4[u].z, x.z, sb); sb = fmaf(b4[u].w, x.w, sb);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            sa += __shfl_xor_sync(0xffffffffu, sa, o);
-            sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        }
-        if (lane == 0) {
-            q[ra] = sa;
-            if (k + 1 < np) q[rb] = sb;
-        }
-    }
-}
-
-// Conjugate gradients for G_PP z = rhs in FP32 (supports whose FP32 factor would not fit
-// shared memory; the Gram blocks of these workloads are well conditioned).  io holds the
-// right-hand side on entry and the solution on exit, both indexed by support slot k < np;
-// x0 (indexed by S position, may be null) is the warm start on P.  The four vectors are
-// kept by S position in `vec` (4 x ld floats, 16-byte aligned, ld >= s rounded up to 4):
-// z, r, p (zero outside P, the product's operand) and q = G p.  Stops when the recurred
-// residual is at most rtol ||rhs||; returns the iterations taken, or -1 when maxit is
-// reached or the curvature p^T G p is not positive (the caller falls back to a factor).
-__device__ __noinline__ int cg_solve(FinShared& sh, const float* Gi, int smax, int s, int np, double* io, const double* x0,
-                        float rtol, int maxit, float* vec, int ld) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    float* z = vec;
-    float* r = vec + ld;
-    float* p = vec + 2 * ld;
-    float* q = vec + 3 * ld;
-    const int sp = (s + 3) & ~3;
-    for (int a = tid; a < sp; a += nt) { p[a] = 0.f; z[a] = 0.f; }
-    __syncthreads();
-    float bb = 0.f;
-    for (int k = tid; k < np; k += nt) {
-        const int a = sh.P[k];
-        const float rhs = (float)io[k];
-        bb = fmaf(rhs, rhs, bb);
-        r[a] = rhs;
-        if (x0) { z[a] = (float)x0[a]; p[a] = z[a]; }
-    }
-    bb = bsumf(bb, sh.red);
-    if (x0) {  // r = rhs - G z0
-        gram_rows_mv(Gi, smax, s, sh.P, np, p, q);
-        __syncthreads();
-        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; r[a] -= q[a]; }
-        __syncthreads();
-    }
-    float rr = 0.f;
-    for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; rr = fmaf(r[a], r[a], rr); p[a] = r[a]; }
-    rr = bsumf(rr, sh.red);
-    const float stop2 = rtol * rtol * bb;
-    int it = 0;
-    int ok = 0;
-    for (;;) {
-        if (rr <= stop2) { ok = 1; break; }
-        if (it >= maxit) break;
-        gram_rows_mv(Gi, smax, s, sh.P, np, p, q);
-        __syncthreads();
-        float pq = 0.f;
-        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; pq = fmaf(p[a], q[a], pq); }
-        pq = bsumf(pq, sh.red);
-        if (!(pq > 0.f)) break;
-        const float alpha = rr / pq;
-        float rn = 0.f;
-        for (int k = tid; k < np; k += nt) {
-            const int a = sh.P[k];
-            z[a] = fmaf(alpha, p[a], z[a]);
-            const float ra = fmaf(-alpha, q[a], r[a]);
-            r[a] = ra;
-            rn = fmaf(ra, ra, rn);
-        }
-        rn = bsumf(rn, sh.red);
-        const float beta = rn / rr;
-        rr = rn;
-        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; p[a] = fmaf(beta, p[a], r[a]); }
-        __syncthreads();
-        ++it;
-    }
-    for (int k = tid; k < np; k += nt) io[k] = (double)z[sh.P[k]];
-    __syncthreads();
-    return ok ? it : -1;
-}
-
 // ---------------------------------------------------------------- cluster finish
 // When few signals finish at once (the last outer iterations, where each finish sits on the
 // critical path), a signal's finish runs on a cluster of C CTAs (C SMs).  Every CTA runs the
@@ -1344,12 +1281,20 @@ __device__ __forceinline__ void part_of(int len, int C, int b, int align, int* l
     *hi = min(len, *lo + per);
 }
 
-// r = b - A_P x: this CTA's row block, then the other blocks from the peers.
+// r = b - A_P x: this CTA's row block (with the atoms spread over thread groups when the block
+// has fewer float4 slots than the CTA has threads, given scratch of blockDim.x x 8 floats),
+// then the other blocks from the peers.
 __device__ bool residual_cluster(const Dev& d, ClusterSync& cs, unsigned rank, const float* A, int n,
-                                 const int* Pi, const df* xd, int np, const float* b, float* rh, float* rl) {
+                                 const int* Pi, const df* xd, int np, const float* b, float* rh, float* rl,
+                                 float* scratch, int scratch_n) {
     int lo, hi;
     part_of(n, cs.C, (int)rank, 4, &lo, &hi);
-    residual_df4_range(A, n, Pi, xd, np, b, rh, rl, lo, hi);
+    const int nv = (hi - lo) >> 2, nt = (int)blockDim.x;
+    const int G = nv > 0 ? min(8, nt / nv) : 1;
+    if (G >= 2 && scratch && scratch_n >= nt * 8)
+        residual_df4_groups(A, n, Pi, xd, np, b, rh, rl, lo, hi, G, scratch);
+    else
+        residual_df4_range(A, n, Pi, xd, np, b, rh, rl, lo, hi);
     if (!csync(d, cs)) return false;
     for (int q = 1; q < cs.C; ++q) {
         const unsigned pr = (rank + q) % cs.C;
@@ -1380,6 +1325,157 @@ __device__ bool dots_cluster(const Dev& d, ClusterSync& cs, unsigned rank, const
         for (int a = plo + (int)threadIdx.x; a < phi; a += (int)blockDim.x) out[a] = po[a];
     }
     return csync(d, cs);
+}
+
+// q_a = (G_SS v)_a for the support positions a = P[k] (v is zero outside P, so this is
+// G_PP v_P): a warp per pair of rows, the row's first s entries as float4 slices when the
+// block's leading dimension allows (else scalar), fixed butterfly per row.
+__device__ __noinline__ void gram_rows_mv(const float* __restrict__ Gi, int smax, int s, const int* P, int np,
+                             const float* v, float* q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool vec = (smax & 3) == 0;
+    for (int k = 2 * warp; k < np; k += 2 * nw) {
+        const int ra = P[k], rb = k + 1 < np ? P[k + 1] : P[k];
+        const float* ga = Gi + (size_t)ra * smax;
+        const float* gb = Gi + (size_t)rb * smax;
+        float sa = 0.f, sb = 0.f;
+        for (int c0 = 4 * lane; c0 < s; c0 += 512) {
+            float4 a4[4], b4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    if (vec) {
+                        a4[u] = __ldg(reinterpret_cast<const float4*>(ga + c));
+                        b4[u] = __ldg(reinterpret_cast<const float4*>(gb + c));
+                    } else {
+                        a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
+                        b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
+                                            c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
+                    }
+                } else {
+                    a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 128 * u;
+                if (c < s) {
+                    // v has zeros from s up to the next multiple of 4 (and outside P)
+                    const float4 x = *reinterpret_cast<const float4*>(v + c);
+                    sa = fmaf(a4[u].x, x.x, sa); sa = fmaf(a4[u].y, x.y, sa);
+                    sa = fmaf(a4[u].z, x.z, sa); sa = fmaf(a4[u].w, x.w, sa);
+                    sb = fmaf(b4[u].x, x.x, sb); sb = fmaf(b4[u].y, x.y, sb);
+                    sb = fmaf(b4[u].z, x.z, sb); sb = fmaf(b4[u].w, x.w, sb);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (lane == 0) {
+            q[ra] = sa;
+            if (k + 1 < np) q[rb] = sb;
+        }
+    }
+}
+
+// Conjugate gradients for G_PP z = rhs in FP32 (supports whose FP32 factor would not fit
+// shared memory; the Gram blocks of these workloads are well conditioned).  io holds the
+// right-hand side on entry and the solution on exit, both indexed by support slot k < np;
+// x0 (indexed by S position, may be null) is the warm start on P.  The four vectors are
+// kept by S position in `vec` (4 x ld floats, 16-byte aligned, ld >= s rounded up to 4):
+// z, r, p (zero outside P, the product's operand) and q = G p.  Stops when the recurred
+// residual is at most rtol ||rhs||; returns the iterations taken, or -1 when maxit is
+// reached or the curvature p^T G p is not positive (the caller falls back to a factor).
+// G_PP v for the CG: the whole block by this CTA, or in a clustered finish this CTA's block
+// of rows followed by the other rows' products from the peers (each row by one CTA, with
+// the same arithmetic, so the product does not depend on the cluster size).  false: a
+// cluster barrier timed out.
+__device__ bool cg_product(const Dev& d, ClusterSync* cs, unsigned rank, const float* Gi, int smax, int s,
+                           const int* P, int np, const float* v, float* q) {
+    if (!cs || cs->C <= 1) {
+        gram_rows_mv(Gi, smax, s, P, np, v, q);
+        return true;
+    }
+    int lo, hi;
+    part_of(np, cs->C, (int)rank, 2, &lo, &hi);
+    if (hi > lo) gram_rows_mv(Gi, smax, s, P + lo, hi - lo, v, q);
+    if (!csync(d, *cs)) return false;
+    for (int r = 1; r < cs->C; ++r) {
+        const unsigned pr = (rank + r) % cs->C;
+        int plo, phi;
+        part_of(np, cs->C, (int)pr, 2, &plo, &phi);
+        const float* pq = peer_ptr(q, pr);
+        for (int k = plo + (int)threadIdx.x; k < phi; k += (int)blockDim.x) q[P[k]] = pq[P[k]];
+    }
+    return csync(d, *cs);
+}
+
+// Returns the iterations taken, -1 when it does not converge, -2 when a cluster barrier
+// timed out (the finish must return).
+__device__ __noinline__ int cg_solve(FinShared& sh, const float* Gi, int smax, int s, int np, double* io, const double* x0,
+                        float rtol, int maxit, float* vec, int ld, const Dev& d, ClusterSync* cs, unsigned rank) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* z = vec;
+    float* r = vec + ld;
+    float* p = vec + 2 * ld;
+    float* q = vec + 3 * ld;
+    const int sp = (s + 3) & ~3;
+    for (int a = tid; a < sp; a += nt) { p[a] = 0.f; z[a] = 0.f; }
+    __syncthreads();
+    float bb = 0.f;
+    for (int k = tid; k < np; k += nt) {
+        const int a = sh.P[k];
+        const float rhs = (float)io[k];
+        bb = fmaf(rhs, rhs, bb);
+        r[a] = rhs;
+        if (x0) { z[a] = (float)x0[a]; p[a] = z[a]; }
+    }
+    bb = bsumf(bb, sh.red);
+    if (x0) {  // r = rhs - G z0
+        if (!cg_product(d, cs, rank, Gi, smax, s, sh.P, np, p, q)) return -2;
+        __syncthreads();
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; r[a] -= q[a]; }
+        __syncthreads();
+    }
+    float rr = 0.f;
+    for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; rr = fmaf(r[a], r[a], rr); p[a] = r[a]; }
+    rr = bsumf(rr, sh.red);
+    const float stop2 = rtol * rtol * bb;
+    int it = 0;
+    int ok = 0;
+    for (;;) {
+        if (rr <= stop2) { ok = 1; break; }
+        if (it >= maxit) break;
+        if (!cg_product(d, cs, rank, Gi, smax, s, sh.P, np, p, q)) return -2;
+        __syncthreads();
+        float pq = 0.f;
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; pq = fmaf(p[a], q[a], pq); }
+        pq = bsumf(pq, sh.red);
+        if (!(pq > 0.f)) break;
+        const float alpha = rr / pq;
+        float rn = 0.f;
+        for (int k = tid; k < np; k += nt) {
+            const int a = sh.P[k];
+            z[a] = fmaf(alpha, p[a], z[a]);
+            const float ra = fmaf(-alpha, q[a], r[a]);
+            r[a] = ra;
+            rn = fmaf(ra, ra, rn);
+        }
+        rn = bsumf(rn, sh.red);
+        const float beta = rn / rr;
+        rr = rn;
+        for (int k = tid; k < np; k += nt) { const int a = sh.P[k]; p[a] = fmaf(beta, p[a], r[a]); }
+        __syncthreads();
+        ++it;
+    }
+    for (int k = tid; k < np; k += nt) io[k] = (double)z[sh.P[k]];
+    __syncthreads();
+    return ok ? it : -1;
 }
 
 // NT = FIN_THREADS (two CTAs per SM) or FIN_THREADS_WIDE (one CTA per SM, taken when the
@@ -1504,8 +1600,10 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             FT_CNT(6);
             if (sh.cg) {
                 // the sign-fixed system from the current point (the master problem's solution)
-                const int it = cg_solve(sh, Gi, smax, s, np, sh.z, sh.x, 1e-6f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3);
+                const int it = cg_solve(sh, Gi, smax, s, np, sh.z, sh.x, 1e-6f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3,
+                                        d, &cs, rank);
                 FT_ADD(1);
+                if (it == -2) return;
                 if (it < 0) {  // not converging: factor this signal's blocks from now on
                     __syncthreads();
                     if (tid == 0) sh.cg = 0;
@@ -1635,7 +1733,9 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             FT_CNT(11);
             if (vec4) {
                 if (C > 1) {
-                    if (!residual_cluster(d, cs, rank, d.A32, n, sh.Pi, xd, np, b, rh, rl)) return;
+                    if (!residual_cluster(d, cs, rank, d.A32, n, sh.Pi, xd, np, b, rh, rl, cgv,
+                                          msm ? 0 : sh.F.stage_n - 4))
+                        return;
                 } else {
                     residual_df4(d.A32, n, sh.Pi, xd, np, b, rh, rl);
                 }
@@ -1701,7 +1801,9 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             FT_CNT(7);
             FX_BEGIN
             if (sh.cg) {
-                const int it = cg_solve(sh, Gi, smax, s, np, sh.w, nullptr, 1e-4f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3);
+                const int it = cg_solve(sh, Gi, smax, s, np, sh.w, nullptr, 1e-4f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3,
+                                        d, &cs, rank);
+                if (it == -2) return;
                 if (it < 0) {
                     // not converging: factor the block and evaluate the correction again
                     __syncthreads();
@@ -1919,7 +2021,7 @@ cudaError_t prepare_finish() {
     return e;
 }
 
-cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl, int sms) {
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cudaStream_t s, int64_t* nl, int sms) {
     if (ub <= 0) return cudaSuccess;
     scap = ((scap + 31) / 32) * 32;
     if (scap > d.smax) scap = d.smax;
@@ -1936,14 +2038,16 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t 
     const size_t dyn = dyn_of(msm, rsm);
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
-    // a cluster per signal when the finishing signals leave most SMs idle (at most ub of them;
-    // clusters of C so that C ub stays within two CTAs per SM); the row-block exchange needs
-    // the residual pair in shared memory and float4 rows
+    // a cluster per signal when the finishing signals leave most SMs idle: about est of them
+    // (at most ub), clusters of C so that C est stays within four CTAs per SM (the launch
+    // time is that of its longest finishes, which the clusters shorten) and every CTA of
+    // the grid has a workspace slot; the row-block exchange needs the residual pair in shared
+    // memory and float4 rows.  (The solve passes the exact count as both.)
     // (-DMPL_NO_FIN_CLUSTER builds one CTA per signal only, for comparisons)
     int C = 1;
 #if !defined(MPL_NO_FIN_CLUSTER)
     if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
-        while (C < FIN_CLUSTER_MAX && 2 * C * ub <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
+        while (C < FIN_CLUSTER_MAX && 2 * C * est <= 4 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
 #endif
     const bool wide = dyn > FIN_SMEM_TWO_CTAS;
     cudaLaunchConfig_t c{};

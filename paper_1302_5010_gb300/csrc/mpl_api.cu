@@ -58,6 +58,8 @@ struct mpl_ctx {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
     cudaEvent_t ev_sel = nullptr;                 // the selection of the current iteration is done
+    cudaEvent_t ev_fcnt = nullptr;                // ... and its finish count copied to fin_h
+    int* fin_h = nullptr;                         // pinned
     cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // the exact finish of the last iteration of each parity
     int use_graph = 1;
     struct GraphEntry {
@@ -216,7 +218,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     // the CTAs of a clustered finish each factor in a workspace of their own (at most
     // FIN_CLUSTER_MAX per signal and two CTAs per SM in one launch)
-    d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
+    d.fin_slots = FIN_CLUSTER_MAX * std::min(std::max(h->sms, 1), P);
     CK(alloc(h, &d.fin_pool, (size_t)d.fin_slots * smax * smax));
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],
@@ -413,6 +415,7 @@ mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
     if (cudaMalloc(&h->colnorm, (size_t)m * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMalloc(&h->scal, 16 * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMallocHost(&h->cnt_h, sizeof(Counters)) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMallocHost(&h->fin_h, sizeof(int)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMemcpy(h->A32, A, bytes, cudaMemcpyDefault) != cudaSuccess) return fail(MPL_ERR_CUDA);
     int64_t nl = 0;
     if (launch_colnorm(h->A32, n, m, h->colnorm, nullptr, 0, &nl) != cudaSuccess) return fail(MPL_ERR_CUDA);
@@ -438,6 +441,7 @@ void mpl_destroy(mpl_handle_t h) {
     cudaFree(h->Xst);
     for (float* q : {h->pw, h->pwb, h->pm1, h->pm2, h->pgrad, h->pacc, h->rn}) cudaFree(q);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
+    if (h->fin_h) cudaFreeHost(h->fin_h);
     clear_graphs(h);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->main) cudaStreamDestroy(h->main);
@@ -447,7 +451,7 @@ void mpl_destroy(mpl_handle_t h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->side_odd) cudaStreamDestroy(h->side_odd);
-    for (cudaEvent_t e : {h->ev_sel, h->ev_fin[0], h->ev_fin[1]})
+    for (cudaEvent_t e : {h->ev_sel, h->ev_fcnt, h->ev_fin[0], h->ev_fin[1]})
         if (e) cudaEventDestroy(e);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
@@ -776,7 +780,8 @@ static mpl_status_t ensure_streams(mpl_ctx* h) {
     CK(cudaStreamCreateWithPriority(&h->side_odd, cudaStreamNonBlocking, prio_lo));
     CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
     CK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, prio_hi));
-    cudaEvent_t* evs[] = {&h->ev_fork2, &h->ev_join2, &h->ev_in, &h->ev_out, &h->ev_sel, &h->ev_fin[0], &h->ev_fin[1]};
+    cudaEvent_t* evs[] = {&h->ev_fork2, &h->ev_join2, &h->ev_in,  &h->ev_out,
+                          &h->ev_sel,   &h->ev_fcnt,  &h->ev_fin[0], &h->ev_fin[1]};
     for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return MPL_OK;
 }
@@ -899,22 +904,32 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                 CK(launch_part(h, d, t, part, live, st, &pt, &nl));
             }
             if (part == 0) {
-                // the exact finish of the signals without violators, beside part 1 and the
-                // next iteration
+                // the selection is done: its count of signals without violators comes back
+                // while part 1 runs
                 CK(cudaEventRecord(h->ev_sel, st));
-                CK(cudaStreamWaitEvent(fin_st, h->ev_sel, 0));
-                cudaEvent_t f0 = pt.begin(fin_st);
+                CK(cudaMemcpyAsync(h->fin_h, &d.cnt->fin_par[par], sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaEventRecord(h->ev_fcnt, st));
 #ifdef MPL_TIMELINE
                 mark(1, st);
-                mark(3, fin_st);
-#endif
-                CK(launch_finish(d, par, std::min(p, live), finish_scap(h, d, t), fin_st, &nl, h->sms));
-                pt.end(4, f0, fin_st);
-                CK(cudaEventRecord(h->ev_fin[par], fin_st));
-#ifdef MPL_TIMELINE
-                mark(4, fin_st);
 #endif
             }
+        }
+        {
+            // the exact finish of the signals without violators, beside part 1 and the next
+            // iteration, its grid and cluster size from their count
+            CK(cudaEventSynchronize(h->ev_fcnt));
+            const int nf = *h->fin_h;
+            CK(cudaStreamWaitEvent(fin_st, h->ev_sel, 0));
+            cudaEvent_t f0 = pt.begin(fin_st);
+#ifdef MPL_TIMELINE
+            mark(3, fin_st);
+#endif
+            if (nf > 0) CK(launch_finish(d, par, nf, nf, finish_scap(h, d, t), fin_st, &nl, h->sms));
+            pt.end(4, f0, fin_st);
+            CK(cudaEventRecord(h->ev_fin[par], fin_st));
+#ifdef MPL_TIMELINE
+            mark(4, fin_st);
+#endif
         }
 #ifdef MPL_TIMELINE
         mark(2, st);
@@ -931,6 +946,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
             // active next iteration, plus the signals of the last two finishes
             live = h->cnt_h->act_n[(t & 1) ^ 1] + h->cnt_h->fin_par[0] + h->cnt_h->fin_par[1];
+
 #ifdef MPL_TIMELINE
             fprintf(stderr, "TC %d %d %d %d\n", t, h->cnt_h->act_n[(t & 1) ^ 1], h->cnt_h->fin_par[t & 1],
                     h->cnt_h->grow_n);

@@ -210,10 +210,10 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
 cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
 // The exact finish of the signals the selection of an iteration with parity cur sent to it
 // (list_fin[cur]); each finished signal that is not done joins reent[cur].  ub bounds the
-// number of finishing signals; when ub is small against the sms SMs a signal's finish runs on
-// a cluster of up to FIN_CLUSTER_MAX CTAs.
+// number of finishing signals, est estimates it; when est is small against the sms SMs a
+// signal's finish runs on a cluster of up to FIN_CLUSTER_MAX CTAs.
 constexpr int FIN_CLUSTER_MAX = 8;
-cudaError_t launch_finish(const Dev& d, int cur, int ub, int scap, cudaStream_t s, int64_t* nl, int sms);
+cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cudaStream_t s, int64_t* nl, int sms);
 // Append reent[cur] to the active list of an iteration with parity cur (rows for the GEMM
 // included); the finishes that filled it must be complete.
 cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl);
