@@ -2039,15 +2039,15 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cuda
     cudaError_t ep = prepare_finish();
     if (ep != cudaSuccess) return ep;
     // a cluster per signal when the finishing signals leave most SMs idle: about est of them
-    // (at most ub), clusters of C so that C est stays within four CTAs per SM (the launch
-    // time is that of its longest finishes, which the clusters shorten) and every CTA of
+    // (at most ub), clusters of C so that C est stays within two CTAs per SM (four per SM
+    // measured slower: the clusters then crowd out the concurrent iteration) and every CTA of
     // the grid has a workspace slot; the row-block exchange needs the residual pair in shared
     // memory and float4 rows.  (The solve passes the exact count as both.)
     // (-DMPL_NO_FIN_CLUSTER builds one CTA per signal only, for comparisons)
     int C = 1;
 #if !defined(MPL_NO_FIN_CLUSTER)
     if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
-        while (C < FIN_CLUSTER_MAX && 2 * C * est <= 4 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
+        while (C < FIN_CLUSTER_MAX && 2 * C * est <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
 #endif
     const bool wide = dyn > FIN_SMEM_TWO_CTAS;
     cudaLaunchConfig_t c{};
