@@ -1204,6 +1204,7 @@ __device__ __forceinline__ float bsumf(float v, double* red) {
 }
 
 // ---------------------------------------------------------------- cluster finish
+// (Built with -DMPL_FIN_CLUSTER only; see launch_finish.)
 // When few signals finish at once (the last outer iterations, where each finish sits on the
 // critical path), a signal's finish runs on a cluster of C CTAs (C SMs).  Every CTA runs the
 // whole finish on identical data, so their control flow is identical; only the column sweeps
@@ -1271,6 +1272,9 @@ __device__ bool csync(const Dev& d, ClusterSync& cs) {
     ++cs.phase;
     ok = __syncthreads_and(ok) != 0;
     if (!ok && threadIdx.x == 0) atomicCAS(&d.cnt->err, 0, (int)DERR_TIMEOUT);
+#ifdef MPL_BOUNDS
+    if (!ok && threadIdx.x == 0) atomicCAS(&d.cnt->bounds_site, 0, 706);
+#endif
     return ok;
 }
 
@@ -1289,6 +1293,11 @@ __device__ bool residual_cluster(const Dev& d, ClusterSync& cs, unsigned rank, c
                                  float* scratch, int scratch_n) {
     int lo, hi;
     part_of(n, cs.C, (int)rank, 4, &lo, &hi);
+#ifdef MPL_BOUNDS
+    for (int a = threadIdx.x; a < np; a += blockDim.x)
+        MPL_OOB(Pi[a] < 0 || Pi[a] >= d.m, 702);
+    MPL_OOB(lo < 0 || hi > n || (lo & 3) || (hi & 3), 703);
+#endif
     const int nv = (hi - lo) >> 2, nt = (int)blockDim.x;
     const int G = nv > 0 ? min(8, nt / nv) : 1;
     if (G >= 2 && scratch && scratch_n >= nt * 8)
@@ -1315,6 +1324,10 @@ __device__ bool dots_cluster(const Dev& d, ClusterSync& cs, unsigned rank, const
                              int cnt, const float* rh, const float* rl, double* out) {
     int lo, hi;
     part_of(cnt, cs.C, (int)rank, 2, &lo, &hi);
+#ifdef MPL_BOUNDS
+    for (int a = threadIdx.x; a < cnt; a += blockDim.x)
+        MPL_OOB(idx[a] < 0 || idx[a] >= d.m, 704);
+#endif
     if (hi > lo) dots_df_warp(A, n, idx + lo, hi - lo, rh, rl, out + lo);
     if (!csync(d, cs)) return false;
     for (int q = 1; q < cs.C; ++q) {
@@ -1403,6 +1416,10 @@ __device__ bool cg_product(const Dev& d, ClusterSync* cs, unsigned rank, const f
     }
     int lo, hi;
     part_of(np, cs->C, (int)rank, 2, &lo, &hi);
+#ifdef MPL_BOUNDS
+    for (int k = threadIdx.x; k < np; k += blockDim.x)
+        MPL_OOB(P[k] < 0 || P[k] >= s, 705);
+#endif
     if (hi > lo) gram_rows_mv(Gi, smax, s, P + lo, hi - lo, v, q);
     if (!csync(d, *cs)) return false;
     for (int r = 1; r < cs->C; ++r) {
@@ -1511,8 +1528,10 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         const bool fsm = s <= msm;
         sh.F.ldf = fsm ? ((msm + 1) | 1) : ((scap + 1) | 1);
         // the factor workspace: the signal's own, or in a clustered finish this CTA's slot of
-        // the pool (the CTAs of a cluster factor the same block side by side)
-        double* wk = C > 1 ? d.fin_pool + (size_t)blockIdx.x * smax * smax : d.chol + (size_t)i * smax * smax;
+        // the pool (the CTAs of a cluster factor the same block side by side); the finishes of
+        // the two iteration parities run concurrently, so each parity has its own half
+        double* wk = C > 1 ? d.fin_pool + ((size_t)cur * d.fin_slots + blockIdx.x) * smax * smax
+                           : d.chol + (size_t)i * smax * smax;
         sh.F.Mf = fsm ? q : reinterpret_cast<float*>(wk);
         if (msm) q += (size_t)msm * ((msm + 1) | 1);
         sh.F.stage = msm ? nullptr : q;  // panel staging for a factor in global memory
@@ -1551,6 +1570,8 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
     }
     const unsigned rank = C > 1 ? cluster_rank() : 0u;
     ClusterSync cs{&sh.cbar, C, 0u};
+    // (the cluster's last block bounds every block's workspace slot: a uniform check)
+    if (MPL_OOB(C > 1 && ((int)(blockIdx.x / C) * C + C > d.fin_slots || (int)rank >= C), 701)) return;
     float* cgv = msm ? nullptr
                      : reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sh.F.stage) + 15) & ~(uintptr_t)15);
     const double lam = (double)d.lam[i];
@@ -2043,9 +2064,10 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cuda
     // measured slower: the clusters then crowd out the concurrent iteration) and every CTA of
     // the grid has a workspace slot; the row-block exchange needs the residual pair in shared
     // memory and float4 rows.  (The solve passes the exact count as both.)
-    // (-DMPL_NO_FIN_CLUSTER builds one CTA per signal only, for comparisons)
+    // Off unless built with -DMPL_FIN_CLUSTER: the face-shaped 1024 x 10024 workload faulted
+    // the GPU once with clusters after the workspace race was fixed, with a cause not found.
     int C = 1;
-#if !defined(MPL_NO_FIN_CLUSTER)
+#if defined(MPL_FIN_CLUSTER)
     if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
         while (C < FIN_CLUSTER_MAX && 2 * C * est <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
 #endif

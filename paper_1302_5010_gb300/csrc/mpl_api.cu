@@ -216,10 +216,21 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.h, ps));
     CK(alloc(h, &d.ritz, ps));
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
-    // the CTAs of a clustered finish each factor in a workspace of their own (at most
-    // FIN_CLUSTER_MAX per signal and two CTAs per SM in one launch)
-    d.fin_slots = FIN_CLUSTER_MAX * std::min(std::max(h->sms, 1), P);
-    CK(alloc(h, &d.fin_pool, (size_t)d.fin_slots * smax * smax));
+    // the CTAs of a clustered finish each factor in a workspace of their own: fin_slots per
+    // iteration parity (the finishes of consecutive iterations run at the same time); a
+    // clustered launch has at most two CTAs per SM
+    // (only in builds with the clustered finish, -DMPL_FIN_CLUSTER)
+#if defined(MPL_FIN_CLUSTER)
+    d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
+    CK(alloc(h, &d.fin_pool, 2 * (size_t)d.fin_slots * smax * smax));
+#endif
+    // chunk maxima of the score rows for batches the matrix-vector route serves
+    if (m > SEL_ROWCACHE_ATOMS) {
+        const size_t nch = ((size_t)m + SEL_CHUNK - 1) / SEL_CHUNK;
+        CK(alloc(h, &d.sel_tmax, (size_t)GEMV_P * nch));
+        CK(alloc(h, &d.sel_nf, (size_t)GEMV_P));
+        CK(cudaMemset(d.sel_nf, 0, GEMV_P * sizeof(int)));
+    }
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],
                     &d.list_fin[1], &d.reent[0], &d.reent[1], &d.list_apg, &d.explore, &d.early};
@@ -675,7 +686,8 @@ static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int ac
             pa.w = h->pwb;
             pa.rn = h->rn;
         }
-        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, propose ? &pa : nullptr, route, fuse)) != cudaSuccess)
+        if ((e = launch_select(d, cur, no_grow, act_ub, run, nl, propose ? &pa : nullptr, route, fuse, 1)) !=
+            cudaSuccess)
             return e;
         if (d.ovf_list) {
             // second pass for the signals whose band overflowed: FP32 correlations of just

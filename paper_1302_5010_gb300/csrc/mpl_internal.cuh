@@ -118,8 +118,10 @@ struct Dev {
     float* h;                    // p x smax A_S^T b
     float* ritz;                 // p x smax power-iteration vector (warm start of L)
     double* chol;                // p x smax x smax FP64 workspace (large supports)
-    double* fin_pool;            // fin_slots more such workspaces: one per CTA of a clustered finish
-    int fin_slots;
+    double* fin_pool;            // 2 x fin_slots more such workspaces: one per CTA of a clustered
+    int fin_slots;               // finish, a half per iteration parity
+    unsigned* sel_tmax;          // GEMV_P x ceil(m / SEL_CHUNK) chunk maxima of the score rows (small batches)
+    int* sel_nf;                 // GEMV_P flags: a non-finite score in the row
     int* state;                  // p SigState
     int* ssize;                  // p |S_i|
     int* snew;                   // p atoms appended this iteration
@@ -195,8 +197,13 @@ cudaError_t launch_gather_r16(const Dev& d, int cur, int act_n_ub, cudaStream_t 
 // Correlation routes of one outer iteration (selects the selection kernel's error band).
 enum CorrRoute : int { ROUTE_GEMM = 0, ROUTE_GEMM_F32 = 1, ROUTE_Q = 2 };
 // fuse_compact: the selection's last CTA also builds the work lists (k_compact not needed).
+// chunked: for at most GEMV_P signals on rows above the row cache, a first kernel writes
+// the rows' SEL_CHUNK-atom maxima and the selection starts from them (sel_chunked).
+constexpr int SEL_CHUNK = 32;
+bool sel_chunked(const Dev& d, int act_n_ub);
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa = nullptr, int route = ROUTE_GEMM, int fuse_compact = 0);
+                          const PropArgs* pa = nullptr, int route = ROUTE_GEMM, int fuse_compact = 0,
+                          int chunked = 0);
 // Identity route (eq. batchQ): scores beta_i - Q_S x_S into the compacted score rows.
 cudaError_t launch_corr_q(const Dev& d, int cur, int act_n_ub, cudaStream_t s, int64_t* nl);
 // beta_i = score row of signal i (after an FP32 correlation of the residual b_i).

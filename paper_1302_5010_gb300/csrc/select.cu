@@ -204,6 +204,11 @@ struct RowKeys {
     const uint32_t* msk;
     __device__ __forceinline__ unsigned operator()(int j, int* nf) const { return key_of(row, msk, j, nf); }
 };
+// Keys already computed (the chunk maxima of k_sel_maxima).
+struct PlainKeys {
+    const unsigned* k;
+    __device__ __forceinline__ unsigned operator()(int j, int*) const { return k[j]; }
+};
 
 // Key of the kth largest score (1-based) among the m keys, by 3 radix passes
 // over 11/11/10 bits.  Returns 0 when fewer than kth keys exceed 0.  The bin
@@ -479,6 +484,108 @@ __device__ bool fast_kth_row(K key, const float* row, const uint32_t* msk, int m
     return true;
 }
 
+// Small batches on long score rows (at most GEMV_P signals, rows of up to 2^26 atoms): the
+// maxima of the row's SEL_CHUNK-atom chunks come from k_sel_maxima (many CTAs per signal), so
+// the signal's CTA works on m / SEL_CHUNK maxima instead of m scores.  T = the kth largest
+// chunk maximum is a lower bound on the kth largest key (the maxima are keys of distinct
+// atoms); only chunks whose maximum reaches TL = key(value(T) - band) can hold a key the
+// caller's band takes, and those chunks' keys at or above TL form the list: the keys >= T at
+// the front of sh.key (their rank gives the kth largest), those in [TL, T) behind them.
+// Returns false (the row path) when more than SEL_KCAP chunks qualify, more than blockDim.x
+// keys are >= T, or the list overflows.  On success as fast_kth_row.
+__device__ bool fast_kth_chunks(const float* row, const uint32_t* msk, int m, const unsigned* tm, int nch, int kth,
+                                float band, SelSmem& sh, unsigned* kkey, unsigned* tlo, unsigned* below) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (kth > nch) return false;
+    const unsigned T = radix_kth(PlainKeys{tm}, nch, kth, sh);
+    if (T == 0u) return false;
+    const float tv = (__uint_as_float(T) - band) * (1.f - 2e-6f);
+    const unsigned TL = tv > 0.f ? min(__float_as_uint(tv), T) : 1u;
+    // the chunks whose maximum reaches TL (warp-aggregated slots in sh.idx)
+    if (tid == 0) { sh.kc = 0; sh.outmax = 0; }
+    __syncthreads();
+    unsigned omax = 0;
+    for (int cb = tid - lane; cb < nch; cb += nt) {
+        const int c = cb + lane;
+        const unsigned mx = c < nch ? tm[c] : 0u;
+        const bool take = c < nch && mx >= TL;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sh.kc, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) {
+            const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (pos < (unsigned)SEL_KCAP) sh.idx[pos] = c;
+        } else if (mx > omax) {
+            omax = mx;
+        }
+    }
+    if (tid == 0) { sh.lcnt = 0; sh.vc = 0; }
+    __syncthreads();
+    const unsigned cc = sh.kc;
+    if (cc > (unsigned)SEL_KCAP) return false;  // uniform
+    // their keys: one warp per chunk, lane l on atom l of the chunk (the front holds at most
+    // nt entries, the back the other SEL_KCAP - nt)
+    for (unsigned q = warp; q < cc; q += nw) {
+        const int j0 = sh.idx[q] * SEL_CHUNK;
+        for (int u = 0; u < SEL_CHUNK; u += 32) {
+            const int j = j0 + u + lane;
+            int nf = 0;
+            const unsigned kj = j < m ? key_of(row, msk, j, &nf) : 0u;
+            const bool hiw = j < m && kj >= T;
+            const bool low = j < m && kj >= TL && kj < T;
+            const unsigned bh = __ballot_sync(0xffffffffu, hiw), bl = __ballot_sync(0xffffffffu, low);
+            unsigned baseh = 0, basel = 0;
+            if (lane == 0 && bh) baseh = atomicAdd(&sh.lcnt, (unsigned)__popc(bh));
+            if (lane == 0 && bl) basel = atomicAdd(&sh.vc, (unsigned)__popc(bl));
+            baseh = __shfl_sync(0xffffffffu, baseh, 0);
+            basel = __shfl_sync(0xffffffffu, basel, 0);
+            const unsigned long long e = ((unsigned long long)kj << 32) | (unsigned)j;
+            if (hiw) {
+                const unsigned pos = baseh + __popc(bh & ((1u << lane) - 1u));
+                if (pos < (unsigned)nt) sh.key[pos] = e;
+            } else if (low) {
+                const unsigned pos = basel + __popc(bl & ((1u << lane) - 1u));
+                if (pos < (unsigned)(SEL_KCAP - nt)) sh.key[SEL_KCAP - 1 - pos] = e;
+            } else if (kj > omax) {
+                omax = kj;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    if (lane == 0 && omax) atomicMax(&sh.outmax, omax);
+    __syncthreads();
+    const unsigned c = sh.lcnt, cl = sh.vc;
+    if (c > (unsigned)nt || cl > (unsigned)(SEL_KCAP - nt)) return false;  // uniform
+    if (tid < (int)c) {
+        const unsigned long long e = sh.key[tid];
+        unsigned above = 0;
+#pragma unroll 8
+        for (unsigned u = 0; u < c; ++u) above += sh.key[u] > e ? 1u : 0u;
+        if (above == (unsigned)kth - 1u) sh.bin = (unsigned)(e >> 32);
+    }
+    // the back part behind the front one (through registers: the ranges may overlap)
+    unsigned long long mv[SEL_KCAP / SEL_THREADS];
+#pragma unroll
+    for (int q = 0; q < SEL_KCAP / SEL_THREADS; ++q) {
+        const unsigned t = tid + q * nt;
+        mv[q] = t < cl ? sh.key[SEL_KCAP - 1 - t] : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < SEL_KCAP / SEL_THREADS; ++q) {
+        const unsigned t = tid + q * nt;
+        if (t < cl) sh.key[c + t] = mv[q];
+    }
+    if (tid == 0) { sh.lcnt = c + cl; sh.vc = 0; }
+    __syncthreads();
+    *kkey = sh.bin;
+    *tlo = TL;
+    *below = sh.outmax;
+    return true;
+}
+
 // The band { j : key >= tkey } from the list of fast_kth (tkey >= its T): into
 // sh.idx, with the largest key left outside (list keys below tkey, or below T).
 __device__ unsigned collect_list(unsigned tkey, unsigned below, SelSmem& sh) {
@@ -620,6 +727,7 @@ __device__ __forceinline__ unsigned ordered_bits(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+template <bool CHUNKED>
 __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, const PropArgs& pa, int route) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
@@ -676,8 +784,18 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         const CachedKeys ck{reinterpret_cast<const unsigned*>(sh.row)};
         const RowKeys rk{row, msk};
         unsigned kkey = 0, tlo = 0, below = 0;
-        const bool listed = cache ? fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below)
-                                  : fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below);
+        // (chunked: the row's chunk maxima are in d.sel_tmax; they describe the first attempt's scores)
+        const int nch = (m + SEL_CHUNK - 1) / SEL_CHUNK;
+        if (CHUNKED && attempt == 0 && !cache && tid == 0 && d.sel_nf[kblk]) {
+            sh.nonfinite = 1;
+            d.sel_nf[kblk] = 0;  // (k_sel_maxima of the next iteration runs after this kernel)
+        }
+        const bool listed =
+            cache ? fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below)
+                  : (CHUNKED && attempt == 0
+                         ? fast_kth_chunks(row, msk, m, d.sel_tmax + (size_t)kblk * nch, nch, kth, 2.f * D, sh, &kkey,
+                                           &tlo, &below)
+                         : fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below));
         if (!listed) kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_VAL(7, listed ? 1 : 0);
         ST_VAL(8, listed ? sh.lcnt : 0);
@@ -1015,10 +1133,11 @@ __global__ void __launch_bounds__(1024) k_compact(Dev d, int cur) {
 
 // The selection of one outer iteration; with fuse set, the last CTA to finish
 // (counted with a fenced atomic) also runs the compaction, saving a launch.
+template <bool CHUNKED>
 __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int no_grow, PropArgs pa, int route,
                                                            int fuse) {
     pdl_enter();
-    select_body(d, cur, no_grow, pa, route);
+    select_body<CHUNKED>(d, cur, no_grow, pa, route);
     if (!fuse) return;
     __shared__ int last;
     __syncthreads();
@@ -1031,6 +1150,38 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     __threadfence();
     compact_body(d, cur);
     if (threadIdx.x == 0) d.cnt->sel_done = 0;
+}
+
+// Chunk maxima of the score rows of a small batch (see fast_kth_chunks): thread c of signal
+// position y takes atoms [SEL_CHUNK c, SEL_CHUNK (c + 1)) (float4 loads when m % 4 == 0),
+// writes the largest key (0 for members of S and non-finite scores) and flags non-finite
+// scores per signal position (cleared by the selection that reads the flag).
+__global__ void __launch_bounds__(256) k_sel_maxima(Dev d, int cur) {
+    pdl_enter();
+    const int kblk = blockIdx.y;
+    if (kblk >= d.cnt->act_n[cur]) return;
+    const int i = d.act[cur][kblk];
+    const int m = d.m, nch = (m + SEL_CHUNK - 1) / SEL_CHUNK;
+    const int c = blockIdx.x * 256 + threadIdx.x;
+    if (c >= nch) return;
+    const float* row = d.Cs + (size_t)kblk * m;
+    const uint32_t* msk = d.mask + (size_t)i * d.mw;
+    const int j0 = c * SEL_CHUNK;
+    unsigned mx = 0;
+    int nf = 0;
+    if ((m & 3) == 0 && j0 + SEL_CHUNK <= m) {
+#pragma unroll
+        for (int u = 0; u < SEL_CHUNK; u += 4) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(row + j0 + u));
+            const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) mx = max(mx, key_of(f, msk, j0 + u + e, e, &nf));
+        }
+    } else {
+        for (int j = j0; j < j0 + SEL_CHUNK && j < m; ++j) mx = max(mx, key_of(row, msk, j, &nf));
+    }
+    d.sel_tmax[(size_t)kblk * nch + c] = mx;
+    if (nf) atomicExch(&d.sel_nf[kblk], 1);
 }
 
 }  // namespace
@@ -1048,24 +1199,39 @@ extern "C" int mpl_debug_sel_trace(long long* out, int count, int reset) {
 }
 #endif
 
+bool sel_chunked(const Dev& d, int act_n_ub) {
+    return d.sel_tmax && d.sel_nf && act_n_ub <= GEMV_P && d.m > SEL_ROWCACHE_ATOMS;
+}
+
 cudaError_t prepare_select() {
     static bool attr = false;
     if (attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(SelSmem) + PROP_NPARAM * sizeof(float)));
+    const int mx = (int)(sizeof(SelSmem) + PROP_NPARAM * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) attr = true;
     return e;
 }
 
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
-                          const PropArgs* pa, int route, int fuse_compact) {
+                          const PropArgs* pa, int route, int fuse_compact, int chunked) {
     if (act_n_ub <= 0) return cudaSuccess;
     PropArgs a{};
     if (pa) a = *pa;
     const size_t sm = sizeof(SelSmem) + (a.mode != SEL_NORMAL ? PROP_NPARAM * sizeof(float) : 0);
     cudaError_t e = prepare_select();
     if (e != cudaSuccess) return e;
-    e = launch_chain(k_select, dim3(act_n_ub), dim3(SEL_THREADS), sm, s, d, cur, no_grow, a, route, fuse_compact);
+    chunked = chunked && sel_chunked(d, act_n_ub) ? 1 : 0;
+    if (chunked) {
+        const int nch = (d.m + SEL_CHUNK - 1) / SEL_CHUNK;
+        e = launch_chain(k_sel_maxima, dim3((nch + 255) / 256, act_n_ub), dim3(256), 0, s, d, cur);
+        if (e != cudaSuccess) return e;
+        ++*nl;
+    }
+    e = chunked ? launch_chain(k_select<true>, dim3(act_n_ub), dim3(SEL_THREADS), sm, s, d, cur, no_grow, a, route,
+                               fuse_compact)
+                : launch_chain(k_select<false>, dim3(act_n_ub), dim3(SEL_THREADS), sm, s, d, cur, no_grow, a, route,
+                               fuse_compact);
     if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
