@@ -224,12 +224,12 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
     CK(alloc(h, &d.fin_pool, 2 * (size_t)d.fin_slots * smax * smax));
 #endif
-    // chunk maxima of the score rows for batches the matrix-vector route serves
+    // chunk maxima of the score rows above the shared-memory row cache (1/8 of the score matrix)
     if (m > SEL_ROWCACHE_ATOMS) {
         const size_t nch = ((size_t)m + SEL_CHUNK - 1) / SEL_CHUNK;
-        CK(alloc(h, &d.sel_tmax, (size_t)GEMV_P * nch));
-        CK(alloc(h, &d.sel_nf, (size_t)GEMV_P));
-        CK(cudaMemset(d.sel_nf, 0, GEMV_P * sizeof(int)));
+        CK(alloc(h, &d.sel_tmax, (size_t)P * nch));
+        CK(alloc(h, &d.sel_nf, (size_t)P));
+        CK(cudaMemset(d.sel_nf, 0, (size_t)P * sizeof(int)));
     }
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
                     &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],

@@ -120,8 +120,8 @@ struct Dev {
     double* chol;                // p x smax x smax FP64 workspace (large supports)
     double* fin_pool;            // 2 x fin_slots more such workspaces: one per CTA of a clustered
     int fin_slots;               // finish, a half per iteration parity
-    unsigned* sel_tmax;          // GEMV_P x ceil(m / SEL_CHUNK) chunk maxima of the score rows (small batches)
-    int* sel_nf;                 // GEMV_P flags: a non-finite score in the row
+    unsigned* sel_tmax;          // P x ceil(m / SEL_CHUNK) chunk maxima of the score rows (m above the row cache)
+    int* sel_nf;                 // P flags: a non-finite score in the row
     int* state;                  // p SigState
     int* ssize;                  // p |S_i|
     int* snew;                   // p atoms appended this iteration

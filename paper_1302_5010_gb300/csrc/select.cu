@@ -790,12 +790,17 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             sh.nonfinite = 1;
             d.sel_nf[kblk] = 0;  // (k_sel_maxima of the next iteration runs after this kernel)
         }
-        const bool listed =
-            cache ? fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below)
-                  : (CHUNKED && attempt == 0
-                         ? fast_kth_chunks(row, msk, m, d.sel_tmax + (size_t)kblk * nch, nch, kth, 2.f * D, sh, &kkey,
-                                           &tlo, &below)
-                         : fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below));
+        bool listed = false;
+        if (cache) {
+            listed = fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);
+        } else {
+            if (CHUNKED && attempt == 0) {
+                listed = fast_kth_chunks(row, msk, m, d.sel_tmax + (size_t)kblk * nch, nch, kth, 2.f * D, sh, &kkey,
+                                         &tlo, &below);
+                __syncthreads();  // (a failed chunk route's shared state is read before it is reused)
+            }
+            if (!listed) listed = fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below);
+        }
         if (!listed) kkey = cache ? radix_kth(ck, m, kth, sh) : radix_kth(rk, m, kth, sh);
         ST_VAL(7, listed ? 1 : 0);
         ST_VAL(8, listed ? sh.lcnt : 0);
@@ -1152,35 +1157,52 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_select(Dev d, int cur, int n
     if (threadIdx.x == 0) d.cnt->sel_done = 0;
 }
 
-// Chunk maxima of the score rows of a small batch (see fast_kth_chunks): thread c of signal
-// position y takes atoms [SEL_CHUNK c, SEL_CHUNK (c + 1)) (float4 loads when m % 4 == 0),
-// writes the largest key (0 for members of S and non-finite scores) and flags non-finite
-// scores per signal position (cleared by the selection that reads the flag).
+// Chunk maxima of the score rows (see fast_kth_chunks): warp w of signal position blockIdx.x
+// takes the 32 chunks [32 w', 32 w' + 32) (w' = 8 blockIdx.y + w), i.e. 1024 consecutive atoms.  Each of
+// its eight float4 loads covers four chunks (eight lanes per chunk, coalesced across the warp);
+// the eight lanes of a chunk combine by shuffles.  Ragged ends (a partial last warp, or
+// m % 4 != 0) take one chunk per lane with scalar loads.  Writes the largest key of each chunk
+// (0 for members of S and non-finite scores) and flags non-finite scores per signal position
+// (cleared by the selection that reads the flag).
 __global__ void __launch_bounds__(256) k_sel_maxima(Dev d, int cur) {
+    static_assert(SEL_CHUNK == 32, "k_sel_maxima: a warp covers 32 chunks of 32 atoms");
     pdl_enter();
-    const int kblk = blockIdx.y;
+    const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
     const int i = d.act[cur][kblk];
     const int m = d.m, nch = (m + SEL_CHUNK - 1) / SEL_CHUNK;
-    const int c = blockIdx.x * 256 + threadIdx.x;
-    if (c >= nch) return;
+    const int lane = threadIdx.x & 31;
+    const int cw = (blockIdx.y * 8 + (threadIdx.x >> 5)) * 32;  // first chunk of this warp
+    if (cw >= nch) return;
     const float* row = d.Cs + (size_t)kblk * m;
     const uint32_t* msk = d.mask + (size_t)i * d.mw;
-    const int j0 = c * SEL_CHUNK;
-    unsigned mx = 0;
+    unsigned* tm = d.sel_tmax + (size_t)kblk * nch;
+    const int j0 = cw * SEL_CHUNK;
     int nf = 0;
-    if ((m & 3) == 0 && j0 + SEL_CHUNK <= m) {
+    if ((m & 3) == 0 && j0 + 32 * SEL_CHUNK <= m) {
+        float4 v[8];
 #pragma unroll
-        for (int u = 0; u < SEL_CHUNK; u += 4) {
-            const float4 v = __ldcs(reinterpret_cast<const float4*>(row + j0 + u));
-            const float f[4] = {v.x, v.y, v.z, v.w};
+        for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(row + j0 + 128 * u + 4 * lane));
 #pragma unroll
-            for (int e = 0; e < 4; ++e) mx = max(mx, key_of(f, msk, j0 + u + e, e, &nf));
+        for (int u = 0; u < 8; ++u) {
+            const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            const int j = j0 + 128 * u + 4 * lane;
+            unsigned mx = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) mx = max(mx, key_of(f, msk, j + e, e, &nf));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+            if ((lane & 7) == 0) tm[cw + 4 * u + (lane >> 3)] = mx;
         }
     } else {
-        for (int j = j0; j < j0 + SEL_CHUNK && j < m; ++j) mx = max(mx, key_of(row, msk, j, &nf));
+        const int c = cw + lane;
+        if (c < nch) {
+            unsigned mx = 0;
+            for (int j = c * SEL_CHUNK; j < (c + 1) * SEL_CHUNK && j < m; ++j) mx = max(mx, key_of(row, msk, j, &nf));
+            tm[c] = mx;
+        }
     }
-    d.sel_tmax[(size_t)kblk * nch + c] = mx;
     if (nf) atomicExch(&d.sel_nf[kblk], 1);
 }
 
@@ -1200,7 +1222,7 @@ extern "C" int mpl_debug_sel_trace(long long* out, int count, int reset) {
 #endif
 
 bool sel_chunked(const Dev& d, int act_n_ub) {
-    return d.sel_tmax && d.sel_nf && act_n_ub <= GEMV_P && d.m > SEL_ROWCACHE_ATOMS;
+    return d.sel_tmax && d.sel_nf && act_n_ub > 0 && d.m > SEL_ROWCACHE_ATOMS;
 }
 
 cudaError_t prepare_select() {
@@ -1224,7 +1246,7 @@ cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cuda
     chunked = chunked && sel_chunked(d, act_n_ub) ? 1 : 0;
     if (chunked) {
         const int nch = (d.m + SEL_CHUNK - 1) / SEL_CHUNK;
-        e = launch_chain(k_sel_maxima, dim3((nch + 255) / 256, act_n_ub), dim3(256), 0, s, d, cur);
+        e = launch_chain(k_sel_maxima, dim3(act_n_ub, (nch + 255) / 256), dim3(256), 0, s, d, cur);
         if (e != cudaSuccess) return e;
         ++*nl;
     }
