@@ -36,12 +36,15 @@ namespace mpl {
 #ifdef MPL_FIN_TRACE
 // Per-signal phase cycle counters of the exact finish (diagnostic builds only):
 // [factor, solve, crossing, gram-zero-check, verify, exact-zero-check, steps, refinements,
-//  of the factor: support + right-hand side, Gram gather]
-__device__ long long g_fin_trace[8192][16];
+//  of the factor: support + right-hand side, Gram gather, evaluation cycles, evaluations,
+//  refinement-solve cycles, FP64 refactors, their cycles, exact Gram rebuilds, CG iterations
+//  of the steps' solves, CG solves of the steps, CG iterations of the refinements, finishes]
+__device__ long long g_fin_trace[8192][20];
 #define FT_BEGIN long long ft0_ = clock64(), fx_ = 0;
 #define FT_SPLIT(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; } while (0)
 #define FT_ADD(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - ft0_; ft0_ = clock64(); } while (0)
 #define FT_CNT(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += 1; } while (0)
+#define FT_VAL(slot, v) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += (v); } while (0)
 #define FX_BEGIN fx_ = clock64();
 #define FX_END(slot) do { if (threadIdx.x == 0 && rank == 0 && i < 8192) g_fin_trace[i][slot] += clock64() - fx_; } while (0)
 #else
@@ -50,6 +53,7 @@ __device__ long long g_fin_trace[8192][16];
 #define FT_BEGIN
 #define FT_ADD(slot) do {} while (0)
 #define FT_CNT(slot) do {} while (0)
+#define FT_VAL(slot, v) do {} while (0)
 #define FT_SPLIT(slot) do {} while (0)
 #endif
 
@@ -1600,6 +1604,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
     if (C > 1 && !csync(d, cs)) return;
 
     FT_BEGIN
+    FT_CNT(19);
     bool ok = false;
     double kkt_on = 0.0, cmax_s = 0.0;
     int np = 0;
@@ -1624,6 +1629,8 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
                 const int it = cg_solve(sh, Gi, smax, s, np, sh.z, sh.x, 1e-6f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3,
                                         d, &cs, rank);
                 FT_ADD(1);
+                FT_VAL(16, it);
+                FT_CNT(17);
                 if (it == -2) return;
                 if (it < 0) {  // not converging: factor this signal's blocks from now on
                     __syncthreads();
@@ -1824,6 +1831,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
             if (sh.cg) {
                 const int it = cg_solve(sh, Gi, smax, s, np, sh.w, nullptr, 1e-4f, FIN_CG_MAXIT, cgv, (scap + 3) & ~3,
                                         d, &cs, rank);
+                FT_VAL(18, it);
                 if (it == -2) return;
                 if (it < 0) {
                     // not converging: factor the block and evaluate the correction again
@@ -2097,9 +2105,9 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cuda
 extern "C" int mpl_debug_fin_trace(long long* out, int count, int reset) {
     if (count > 8192) count = 8192;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 16 * (size_t)count) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, mpl::g_fin_trace, sizeof(long long) * 20 * (size_t)count) != cudaSuccess) return -1;
     if (reset) {
-        static long long zero[8192][16];
+        static long long zero[8192][20];
         if (cudaMemcpyToSymbol(mpl::g_fin_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
     }
     return count;

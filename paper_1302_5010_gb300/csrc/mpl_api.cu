@@ -236,6 +236,9 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
                     &d.list_fin[1], &d.reent[0], &d.reent[1], &d.list_apg, &d.explore, &d.early};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
     CK(alloc(h, &d.rnorm, (size_t)P));
+    CK(alloc(h, &d.res_part, (size_t)P * res_blocks(n) * 3));
+    CK(alloc(h, &d.res_tick, (size_t)P));
+    CK(cudaMemset(d.res_tick, 0, (size_t)P * sizeof(int)));
     CK(alloc(h, &d.r16e, (size_t)P));
     CK(alloc(h, &d.r16t, (size_t)P));
     CK(alloc(h, &d.bnorm, (size_t)P));

@@ -136,6 +136,8 @@ struct Dev {
     float* f0;                   // p f(x^0) = ||b||^2 / 2
     int* nnz;                    // p
     float* rnorm;                // p ||r|| upper bound
+    float* res_part;             // p x RES_BLOCKS(n) x 3 partial sums of the residual's row blocks
+    int* res_tick;               // p row blocks of the residual update done (reset by the last one)
     float* eps;                  // p current eq. (inner) tolerance
     double* obj;                 // p FP64 objective
     double* kkt_in;              // p KKT violation / lambda on S (from the finish)
@@ -200,6 +202,10 @@ enum CorrRoute : int { ROUTE_GEMM = 0, ROUTE_GEMM_F32 = 1, ROUTE_Q = 2 };
 // chunked: for at most GEMV_P signals on rows above the row cache, a first kernel writes
 // the rows' SEL_CHUNK-atom maxima and the selection starts from them (sel_chunked).
 constexpr int SEL_CHUNK = 32;
+// rows of the residual update per CTA (256 threads x float4): a signal's residual is split
+// into ceil(n / RES_ROWS) row blocks, one CTA each
+constexpr int RES_ROWS = 1024;
+inline int res_blocks(int n) { return (n + RES_ROWS - 1) / RES_ROWS; }
 bool sel_chunked(const Dev& d, int act_n_ub);
 cudaError_t launch_select(const Dev& d, int cur, int no_grow, int act_n_ub, cudaStream_t s, int64_t* nl,
                           const PropArgs* pa = nullptr, int route = ROUTE_GEMM, int fuse_compact = 0,

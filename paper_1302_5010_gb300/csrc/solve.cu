@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
         d.finishes[i] = 0;
         d.fails[i] = 0;
         d.nnz[i] = 0;
+        d.res_tick[i] = 0;  // (a solve that stopped on an error may have left a count)
         d.rnorm[i] = __double2float_ru(sqrt(bb)) * (1.f + 1e-6f);
         if (d.pos) d.pos[i] = i;
         if (d.bnorm) { d.bnorm[i] = d.rnorm[i]; d.xl1[i] = 0.f; }
@@ -453,14 +454,67 @@ __device__ __forceinline__ float gram_mv(const float* __restrict__ G, int ld, in
 }
 
 // y = G x for a block in global memory (leading dimension ld, row r = column r by
-// symmetry): a warp per pair of rows, each row's s entries read as float4 slices (four per
-// lane in flight for each of the two rows) when ld allows, fixed butterfly per row.  x is
-// zero from s up to the next multiple of 4.  With h != nullptr lane 0 also returns its
-// rows' share of the restricted objective, lambda |x_r| + x_r (y_r / 2 - h_r).
-__device__ __forceinline__ float gram_mv_stream(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
-                                                float* __restrict__ y, const float* h = nullptr, float lam = 0.f) {
+// symmetry).  Lane l of a warp owns the float4 slices c = 4 l + 128 u (u < U = ceil(s / 128))
+// of a row and sums them in order of u, then a fixed butterfly combines the lanes; a warp
+// takes RW rows per round and issues all RW x U slice loads before the first product (up to
+// 16 per lane in flight: the streamed products are latency-bound).  x is zero from s up to
+// the next multiple of 4.  With h != nullptr lane 0 also returns its rows' share of the
+// restricted objective, lambda |x_r| + x_r (y_r / 2 - h_r).
+template <int U, int RW>
+__device__ __forceinline__ float gram_mv_stream_vec(const float* __restrict__ G, int ld, int s,
+                                                    const float* __restrict__ x, float* __restrict__ y,
+                                                    const float* h, float lam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bool vec = (ld & 3) == 0;
+    float part = 0.f;
+    for (int r = RW * warp; r < s; r += RW * nw) {
+        float4 g[RW][U];
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            const float* gr = G + (size_t)min(r + w, s - 1) * ld;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = 4 * lane + 128 * u;
+                g[w][u] = c < s ? __ldg(reinterpret_cast<const float4*>(gr + c)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        float acc[RW];
+#pragma unroll
+        for (int w = 0; w < RW; ++w) acc[w] = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = 4 * lane + 128 * u;
+            if (c < s) {
+                const float4 xv = *reinterpret_cast<const float4*>(x + c);
+#pragma unroll
+                for (int w = 0; w < RW; ++w) {
+                    acc[w] = fmaf(g[w][u].x, xv.x, acc[w]); acc[w] = fmaf(g[w][u].y, xv.y, acc[w]);
+                    acc[w] = fmaf(g[w][u].z, xv.z, acc[w]); acc[w] = fmaf(g[w][u].w, xv.w, acc[w]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int w = 0; w < RW; ++w) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int w = 0; w < RW; ++w) {
+                if (r + w < s) {
+                    y[r + w] = acc[w];
+                    if (h) part += lam * fabsf(x[r + w]) + x[r + w] * (0.5f * acc[w] - h[r + w]);
+                }
+            }
+        }
+    }
+    return part;
+}
+
+// The same product with scalar loads (ld not a multiple of 4): a warp per pair of rows.
+__device__ __forceinline__ float gram_mv_stream_scalar(const float* __restrict__ G, int ld, int s,
+                                                       const float* __restrict__ x, float* __restrict__ y,
+                                                       const float* h, float lam) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float part = 0.f;
     for (int r = 2 * warp; r < s; r += 2 * nw) {
         const int rb = r + 1 < s ? r + 1 : r;
@@ -473,15 +527,10 @@ __device__ __forceinline__ float gram_mv_stream(const float* __restrict__ G, int
             for (int u = 0; u < 4; ++u) {
                 const int c = c0 + 128 * u;
                 if (c < s) {
-                    if (vec) {
-                        a4[u] = __ldg(reinterpret_cast<const float4*>(ga + c));
-                        b4[u] = __ldg(reinterpret_cast<const float4*>(gb + c));
-                    } else {
-                        a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
-                                            c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
-                        b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
-                                            c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
-                    }
+                    a4[u] = make_float4(__ldg(ga + c), c + 1 < s ? __ldg(ga + c + 1) : 0.f,
+                                        c + 2 < s ? __ldg(ga + c + 2) : 0.f, c + 3 < s ? __ldg(ga + c + 3) : 0.f);
+                    b4[u] = make_float4(__ldg(gb + c), c + 1 < s ? __ldg(gb + c + 1) : 0.f,
+                                        c + 2 < s ? __ldg(gb + c + 2) : 0.f, c + 3 < s ? __ldg(gb + c + 3) : 0.f);
                 } else {
                     a4[u] = b4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -513,6 +562,22 @@ __device__ __forceinline__ float gram_mv_stream(const float* __restrict__ G, int
         }
     }
     return part;
+}
+
+__device__ __noinline__ float gram_mv_stream(const float* __restrict__ G, int ld, int s, const float* __restrict__ x,
+                                             float* __restrict__ y, const float* h = nullptr, float lam = 0.f) {
+    if ((ld & 3) != 0) return gram_mv_stream_scalar(G, ld, s, x, y, h, lam);
+    switch ((s + 127) >> 7) {
+        case 0:
+        case 1: return gram_mv_stream_vec<1, 8>(G, ld, s, x, y, h, lam);
+        case 2: return gram_mv_stream_vec<2, 8>(G, ld, s, x, y, h, lam);
+        case 3: return gram_mv_stream_vec<3, 4>(G, ld, s, x, y, h, lam);
+        case 4: return gram_mv_stream_vec<4, 4>(G, ld, s, x, y, h, lam);
+        case 5: return gram_mv_stream_vec<5, 2>(G, ld, s, x, y, h, lam);
+        case 6: return gram_mv_stream_vec<6, 2>(G, ld, s, x, y, h, lam);
+        case 7: return gram_mv_stream_vec<7, 2>(G, ld, s, x, y, h, lam);
+        default: return gram_mv_stream_vec<8, 2>(G, ld, s, x, y, h, lam);
+    }
 }
 
 struct ApgVec {
@@ -787,11 +852,16 @@ __global__ void __launch_bounds__(APG_THREADS) k_apg(Dev d, int vcap, int gcap, 
 }
 
 // ------------------------------------------------------------------ residual
+// Row block y = blockIdx.y of signal position blockIdx.x: rows [RES_ROWS y, RES_ROWS (y + 1)).
+// Each entry sums the atoms in order of the support, whatever the split.  The three norms
+// are block sums per row block, combined in order of y by the block that finishes last (a
+// ticket per signal, no waiting), so they do not depend on the order the blocks run in.
 __global__ void __launch_bounds__(256) k_residual(Dev d) {
     pdl_enter();
     const int g = blockIdx.x;
     if (g >= d.cnt->apg_n) return;
     const int i = d.list_apg[g];
+    const int yb = blockIdx.y, nb = gridDim.y;
     const int n = d.n, smax = d.smax, s = d.ssize[i];
     __shared__ int nzi[1024];
     __shared__ float nzv[1024];
@@ -817,7 +887,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
     __syncthreads();
     const int nz = cntnz;
     if (MPL_OOB(s > 1024 || nz > 1024, 301)) return;
-    if (d.Q) {  // ||x_S||_1 for the identity route's error band (FP32 sum, rounded up by gamma_1024)
+    if (d.Q && yb == 0) {  // ||x_S||_1 for the identity route's error band (FP32 sum, rounded up by gamma_1024)
         float l1 = 0.f;
         for (int a = threadIdx.x; a < nz; a += blockDim.x) l1 += fabsf(nzv[a]);
         const float t1 = block_sum(l1, red);
@@ -834,9 +904,10 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
         es = fmaf(e, e, es);
         ts = fmaf(fq, fq, ts);
     };
+    const int k_lo = yb * RES_ROWS, k_hi = min(n, k_lo + RES_ROWS);
     if ((n & 3) == 0) {
         // float4 columns, four atoms per pass with their loads issued first
-        for (int k = threadIdx.x * 4; k < n; k += blockDim.x * 4) {
+        for (int k = k_lo + threadIdx.x * 4; k < k_hi; k += blockDim.x * 4) {
             float4 acc = *reinterpret_cast<const float4*>(b + k);
             int a = 0;
             for (; a + 7 < nz; a += 8) {  // eight atom columns' loads in flight, then in order
@@ -888,7 +959,7 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
             if (r16) { bf_terms(acc.x); bf_terms(acc.y); bf_terms(acc.z); bf_terms(acc.w); }
         }
     } else {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = k_lo + threadIdx.x; k < k_hi; k += blockDim.x) {
             float acc = b[k];
             for (int a = 0; a < nz; ++a) acc = fmaf(-nzv[a], __ldg(d.A32 + (size_t)nzi[a] * n + k), acc);
             r32[k] = acc;
@@ -898,16 +969,35 @@ __global__ void __launch_bounds__(256) k_residual(Dev d) {
             if (r16) bf_terms(acc);
         }
     }
-    // FP32 sums: a few roundings per term and a 256-way tree, far inside the 1e-5 margin
+    // FP32 sums: a few roundings per term, a 256-way tree and at most 64 row blocks, far
+    // inside the 1e-5 margin
     block_sum3(ss, es, ts, red);
     if (threadIdx.x == 0) {
-        d.rnorm[i] = sqrtf(ss) * (1.f + 1e-5f);
-        d.r16e[i] = sqrtf(es) * (1.f + 1e-5f);
-        d.r16t[i] = sqrtf(ts) * (1.f + 1e-5f);
-        d.nnz[i] = nz;
-        // atom columns and b read, the FP32 residual (and its BF16 copies) written
-        atomicAdd(&d.cnt->res_bytes, (unsigned long long)n * (4ull * (nz + 2) + (d.R16 ? 2ull : 0ull) +
-                                                              (d.pos ? 2ull : 0ull)));
+        if (yb == 0) {
+            d.nnz[i] = nz;
+            // atom columns and b read, the FP32 residual (and its BF16 copies) written
+            atomicAdd(&d.cnt->res_bytes, (unsigned long long)n * (4ull * (nz + 2) + (d.R16 ? 2ull : 0ull) +
+                                                                  (d.pos ? 2ull : 0ull)));
+        }
+        bool last = nb == 1;
+        if (!last) {
+            float* part = d.res_part + ((size_t)i * nb + yb) * 3;
+            part[0] = ss; part[1] = es; part[2] = ts;
+            __threadfence();
+            last = atomicAdd(&d.res_tick[i], 1) == nb - 1;
+            if (last) {
+                __threadfence();
+                const volatile float* all = d.res_part + (size_t)i * nb * 3;
+                ss = es = ts = 0.f;
+                for (int y = 0; y < nb; ++y) { ss += all[3 * y]; es += all[3 * y + 1]; ts += all[3 * y + 2]; }
+                d.res_tick[i] = 0;
+            }
+        }
+        if (last) {
+            d.rnorm[i] = sqrtf(ss) * (1.f + 1e-5f);
+            d.r16e[i] = sqrtf(es) * (1.f + 1e-5f);
+            d.r16t[i] = sqrtf(ts) * (1.f + 1e-5f);
+        }
     }
 }
 
@@ -1213,7 +1303,7 @@ cudaError_t launch_apg(const Dev& d, int ub, int sms, int vcap, cudaStream_t s, 
 
 cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
     if (ub <= 0) return cudaSuccess;
-    const cudaError_t e = launch_chain(k_residual, dim3(ub), dim3(256), 0, s, d);
+    const cudaError_t e = launch_chain(k_residual, dim3(ub, res_blocks(d.n)), dim3(256), 0, s, d);
     if (e != cudaSuccess) return e;
     ++*nl;
     return cudaGetLastError();
