@@ -583,7 +583,7 @@ struct FinShared {
     float cs[2]; // rotation of the factor update
     float rot[2][2];  // rotations of the CTA-wide update, alternating slots
     int cg;      // 1: solves by conjugate gradients on the Gram block (no factor)
-    uint64_t cbar;  // cluster barrier of a clustered finish (C arrivals per phase)
+    uint64_t cbar[2];  // cluster barriers of a clustered finish (C arrivals per phase; phases alternate)
 };
 
 // Ordered support of the sign pattern (one warp writes sh.P, count in ival[1]).
@@ -1208,16 +1208,15 @@ __device__ __forceinline__ float bsumf(float v, double* red) {
 }
 
 // ---------------------------------------------------------------- cluster finish
-// (Built with -DMPL_FIN_CLUSTER only; see launch_finish.)
 // When few signals finish at once (the last outer iterations, where each finish sits on the
 // critical path), a signal's finish runs on a cluster of C CTAs (C SMs).  Every CTA runs the
 // whole finish on identical data, so their control flow is identical; only the column sweeps
 // are divided: the exact residual by row blocks of n / C entries, the correlations by blocks
 // of the atom list, after which every CTA reads the other blocks from its peers' shared
 // memory (distributed shared memory).  Before such reads, and before a CTA overwrites what
-// its peers may still read, the cluster meets at a barrier built on one mbarrier per CTA
-// (C arrivals, one remote arrive from each CTA), waited on with a bound: on expiry the CTA
-// records DERR_TIMEOUT and the finish returns without its result.
+// its peers may still read, the cluster meets at a barrier built on two mbarriers per CTA used
+// in turn (C arrivals, one remote arrive from each CTA), waited on with a bound: on expiry the
+// CTA records DERR_TIMEOUT and the finish returns without its result.
 constexpr uint64_t FIN_CLUSTER_WAIT_NS = 4000000000ull;
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -1235,25 +1234,32 @@ __device__ __forceinline__ T* peer_ptr(T* p, unsigned rank) {
 }
 
 struct ClusterSync {
-    uint64_t* bar;  // this CTA's barrier (count C)
+    uint64_t* bar;  // this CTA's two barriers (count C each)
     int C;
     unsigned phase;
 };
 
 // All threads of all C CTAs: returns false (uniformly within the CTA) when the wait expired.
+// Each CTA arrives once on the barrier of every CTA of the cluster and waits on its own.
+// Consecutive phases use the two barriers in turn: an arrival for phase k + 1 cannot land on
+// a barrier that is still in phase k (with one barrier, a CTA that has passed phase k could
+// complete a slower CTA's phase k before a third CTA's arrival for k), and an arrival for
+// phase k + 2 comes only after every CTA has passed phase k + 1, so after the barrier of
+// phase k has completed it.  The n-th phase of barrier b has parity n & 1.
 __device__ bool csync(const Dev& d, ClusterSync& cs) {
     __syncthreads();
+    uint64_t* bar = cs.bar + (cs.phase & 1u);
     if (threadIdx.x == 0) {
         asm volatile("fence.acq_rel.cluster;" ::: "memory");
-        const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(cs.bar));
+        const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
         for (int r = 0; r < cs.C; ++r) {
             uint32_t remote;
             asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
             asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
         }
     }
-    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(cs.bar));
-    const uint32_t parity = cs.phase & 1u;
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+    const uint32_t parity = (cs.phase >> 1) & 1u;
     bool ok = false;
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
@@ -1558,10 +1564,11 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         // fallback when CG does not converge
         sh.cg = (msm == 0 && s > FIN_CG_MIN_S) ? 1 : 0;
         if (C > 1) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
-                             static_cast<uint32_t>(__cvta_generic_to_shared(&sh.cbar))),
-                         "r"(C)
-                         : "memory");
+            for (int q = 0; q < 2; ++q)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                                 static_cast<uint32_t>(__cvta_generic_to_shared(&sh.cbar[q]))),
+                             "r"(C)
+                             : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
@@ -1573,7 +1580,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     const unsigned rank = C > 1 ? cluster_rank() : 0u;
-    ClusterSync cs{&sh.cbar, C, 0u};
+    ClusterSync cs{sh.cbar, C, 0u};
     // (the cluster's last block bounds every block's workspace slot: a uniform check)
     if (MPL_OOB(C > 1 && ((int)(blockIdx.x / C) * C + C > d.fin_slots || (int)rank >= C), 701)) return;
     float* cgv = msm ? nullptr
@@ -2071,11 +2078,10 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cuda
     // (at most ub), clusters of C so that C est stays within two CTAs per SM (four per SM
     // measured slower: the clusters then crowd out the concurrent iteration) and every CTA of
     // the grid has a workspace slot; the row-block exchange needs the residual pair in shared
-    // memory and float4 rows.  (The solve passes the exact count as both.)
-    // Off unless built with -DMPL_FIN_CLUSTER: the face-shaped 1024 x 10024 workload faulted
-    // the GPU once with clusters after the workspace race was fixed, with a cause not found.
+    // memory and float4 rows.  (The solve passes the exact count as both.)  Builds with
+    // -DMPL_NO_FIN_CLUSTER keep one CTA per signal.
     int C = 1;
-#if defined(MPL_FIN_CLUSTER)
+#if !defined(MPL_NO_FIN_CLUSTER)
     if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
         while (C < FIN_CLUSTER_MAX && 2 * C * est <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
 #endif

@@ -219,8 +219,7 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     // the CTAs of a clustered finish each factor in a workspace of their own: fin_slots per
     // iteration parity (the finishes of consecutive iterations run at the same time); a
     // clustered launch has at most two CTAs per SM
-    // (only in builds with the clustered finish, -DMPL_FIN_CLUSTER)
-#if defined(MPL_FIN_CLUSTER)
+#if !defined(MPL_NO_FIN_CLUSTER)
     d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
     CK(alloc(h, &d.fin_pool, 2 * (size_t)d.fin_slots * smax * smax));
 #endif
