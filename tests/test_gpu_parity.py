@@ -76,6 +76,17 @@ def test_ragged_shapes(n, m, p, rho):
     check_against_oracle(P, X64, oracle_solve(P))
 
 
+def test_long_signals_residual_in_global_memory():
+    """n > 4096: the exact finish keeps its double-FP32 residual in the signal's global rows
+    instead of shared memory (the layout it also takes when more signals finish at once than
+    there are SMs and the shared-memory one fits a single CTA per SM)."""
+    P = synth.small_problem(4104, 3000, 12, 20, 60, rho=10, seed=4104, lam_frac=0.02)
+    for precision in (0, 1):
+        X, X64, res = solve_gpu(P, precision=precision)
+        assert_certified(res)
+        check_against_oracle(P, X64, oracle_solve(P))
+
+
 def test_c2_subset_all_signals():
     P = synth.make_config("c2", p=48)
     X, X64, res = solve_gpu(P)
