@@ -39,11 +39,11 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels the roofline block
 # can report, per workload, from an ncu capture of the current kernel; absent until one exists.
 TRAFFIC = {
-    # all k_finish launches of one solve of the 4096 x 65536 batch: 619.9 MB read + 1.6 MB
-    # written over the 16 launches of a 64-signal solve (9.71 MB per signal), scaled to 1024
+    # all k_finish launches of one solve of the 4096 x 65536 batch: 534.6 MB read + 5.3 MB
+    # written over the 9 launches of a 64-signal solve (8.44 MB per signal), scaled to 1024
     # signals (per-signal work is independent of the batch); per step, like the entry's
     # bytes_per_step
-    ("c3", "k_finish"): 9.94e9,
+    ("c3", "k_finish"): 8.64e9,
 }
 
 # active-set capacity per workload (supports reach ~570 atoms on c3, ~290 on c5)
