@@ -169,27 +169,42 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     if (MPL_OOB(s > smax || s > 1024 || q > s, 401)) return;
     for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
     __syncthreads();
-    // new columns (and, by symmetry, rows) of G_SS: eight independent loads per thread
-    // in flight before their stores (the stores could alias them as far as the compiler knows)
-    const int total = s * q;
-    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * blockDim.x) {
-        float v[8];
+    // new columns (and, by symmetry, rows) of G_SS in tiles of GT_A positions of S by GT_C new
+    // atoms: eight independent Q reads per thread in flight (scattered either way), the new
+    // rows G[s0 + c][a] written along a, then through a shared-memory tile the new columns
+    // G[a][s0 + c] written along c, so that both halves are stored in whole sectors
+    constexpr int GT_A = 32, GT_C = 64;
+    static_assert(GT_C * (GT_A + 1) <= GQ_BUF, "the tile lives in the staging buffer of h");
+    float (*gt)[GT_A + 1] = reinterpret_cast<float (*)[GT_A + 1]>(hbuf);  // (h's staging comes after)
+    const int ta = threadIdx.x & (GT_A - 1), tc = threadIdx.x >> 5;  // 256 threads: tc < 8
+    for (int a0 = 0; a0 < s; a0 += GT_A) {
+        for (int c0 = 0; c0 < q; c0 += GT_C) {
+            const int a = a0 + ta;
+            float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < total) {
-                const int a = e / q, c = e - a * q;
-                v[u] = __ldg(d.Q + (size_t)sidx[a] * m + sidx[s0 + c]);
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + tc + 8 * u;
+                v[u] = (a < s && c < q) ? __ldg(d.Q + (size_t)sidx[a] * m + sidx[s0 + c]) : 0.f;
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < total) {
-                const int a = e / q, c = e - a * q;
-                Gi[(size_t)a * smax + s0 + c] = v[u];
-                Gi[(size_t)(s0 + c) * smax + a] = v[u];
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + tc + 8 * u;
+                if (a < s && c < q) Gi[(size_t)(s0 + c) * smax + a] = v[u];
+                gt[tc + 8 * u][ta] = v[u];
             }
+            __syncthreads();
+            // the transposed tile: thread (row, lane) writes G[a0 + row][s0 + c0 + lane (+ 32)]
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ar = tc + 8 * u;  // 0..31
+                const int at = a0 + ar;
+#pragma unroll
+                for (int h2 = 0; h2 < GT_C; h2 += 32) {
+                    const int c = c0 + h2 + ta;
+                    if (at < s && c < q) Gi[(size_t)at * smax + s0 + c] = gt[h2 + ta][ar];
+                }
+            }
+            __syncthreads();
         }
     }
     // h of the new atoms, one FMA chain per atom (thread), over k ascending.  The
