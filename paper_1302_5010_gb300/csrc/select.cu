@@ -25,10 +25,12 @@ namespace mpl {
 #ifdef MPL_SEL_TRACE
 // Per-signal phase cycle counters of the selection (diagnostic builds only):
 // [row cache, k-th key, collect, re-score, sort + state, calls, band size, list-path
-//  k-th keys, list size]
-__device__ long long g_sel_trace[8192][10];
+//  k-th keys, list size, -, the last call's row cache, k-th key, collect, re-score,
+//  sort + state, band size, and of its chunk route: the check that failed (0: none), the
+//  keys >= T, the keys in [TL, T), the chunks that qualified]
+__device__ long long g_sel_trace[8192][20];
 #define ST_BEGIN long long st0_ = clock64();
-#define ST_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += clock64() - st0_; st0_ = clock64(); } while (0)
+#define ST_ADD(slot) do { if (threadIdx.x == 0 && i < 8192) { const long long dt_ = clock64() - st0_; g_sel_trace[i][slot] += dt_; g_sel_trace[i][10 + (slot)] = dt_; } st0_ = clock64(); } while (0)
 #define ST_CNT(slot) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += 1; } while (0)
 #define ST_VAL(slot, v) do { if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][slot] += (v); } while (0)
 #else
@@ -484,22 +486,30 @@ __device__ bool fast_kth_row(K key, const float* row, const uint32_t* msk, int m
     return true;
 }
 
-// Small batches on long score rows (at most GEMV_P signals, rows of up to 2^26 atoms): the
-// maxima of the row's SEL_CHUNK-atom chunks come from k_sel_maxima (many CTAs per signal), so
-// the signal's CTA works on m / SEL_CHUNK maxima instead of m scores.  T = the kth largest
-// chunk maximum is a lower bound on the kth largest key (the maxima are keys of distinct
-// atoms); only chunks whose maximum reaches TL = key(value(T) - band) can hold a key the
-// caller's band takes, and those chunks' keys at or above TL form the list: the keys >= T at
-// the front of sh.key (their rank gives the kth largest), those in [TL, T) behind them.
+// Score rows above the shared-memory row cache: the maxima of the row's SEL_CHUNK-atom chunks
+// come from k_sel_maxima (many CTAs per signal), so the signal's CTA works on m / SEL_CHUNK
+// maxima instead of m scores.  T = the kth largest chunk maximum is a lower bound on the kth
+// largest key (the maxima are keys of distinct atoms); the caller's band starts at or above
+// both value(T) - band and lo (a lower bound it knows in advance: the threshold side of the
+// band), so only chunks whose maximum reaches TL = key(max(value(T) - band, lo)), at most T,
+// can hold a key the band takes, and those chunks' keys at or above TL form the list: the
+// keys >= T at the front of sh.key (their rank gives the kth largest), those in [TL, T)
+// behind them.
 // Returns false (the row path) when more than SEL_KCAP chunks qualify, more than blockDim.x
 // keys are >= T, or the list overflows.  On success as fast_kth_row.
+#ifdef MPL_SEL_TRACE
+#define CK_TRACE(sig, w, a, b, c) do { if (threadIdx.x == 0 && (sig) < 8192) { g_sel_trace[sig][16] = (w); g_sel_trace[sig][17] = (a); g_sel_trace[sig][18] = (b); g_sel_trace[sig][19] = (c); } } while (0)
+#else
+#define CK_TRACE(sig, w, a, b, c) do {} while (0)
+#endif
 __device__ bool fast_kth_chunks(const float* row, const uint32_t* msk, int m, const unsigned* tm, int nch, int kth,
-                                float band, SelSmem& sh, unsigned* kkey, unsigned* tlo, unsigned* below) {
+                                float band, float lo, SelSmem& sh, unsigned* kkey, unsigned* tlo, unsigned* below,
+                                int sig) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    if (kth > nch) return false;
+    if (kth > nch) { CK_TRACE(sig, 1, 0, 0, 0); return false; }
     const unsigned T = radix_kth(PlainKeys{tm}, nch, kth, sh);
-    if (T == 0u) return false;
-    const float tv = (__uint_as_float(T) - band) * (1.f - 2e-6f);
+    if (T == 0u) { CK_TRACE(sig, 2, 0, 0, 0); return false; }
+    const float tv = fmaxf((__uint_as_float(T) - band) * (1.f - 2e-6f), lo);
     const unsigned TL = tv > 0.f ? min(__float_as_uint(tv), T) : 1u;
     // the chunks whose maximum reaches TL (warp-aggregated slots in sh.idx)
     if (tid == 0) { sh.kc = 0; sh.outmax = 0; }
@@ -523,7 +533,7 @@ __device__ bool fast_kth_chunks(const float* row, const uint32_t* msk, int m, co
     if (tid == 0) { sh.lcnt = 0; sh.vc = 0; }
     __syncthreads();
     const unsigned cc = sh.kc;
-    if (cc > (unsigned)SEL_KCAP) return false;  // uniform
+    if (cc > (unsigned)SEL_KCAP) { CK_TRACE(sig, 3, 0, 0, cc); return false; }  // uniform
     // their keys: one warp per chunk, lane l on atom l of the chunk (the front holds at most
     // nt entries, the back the other SEL_KCAP - nt)
     for (unsigned q = warp; q < cc; q += nw) {
@@ -557,7 +567,8 @@ __device__ bool fast_kth_chunks(const float* row, const uint32_t* msk, int m, co
     if (lane == 0 && omax) atomicMax(&sh.outmax, omax);
     __syncthreads();
     const unsigned c = sh.lcnt, cl = sh.vc;
-    if (c > (unsigned)nt || cl > (unsigned)(SEL_KCAP - nt)) return false;  // uniform
+    if (c > (unsigned)nt || cl > (unsigned)(SEL_KCAP - nt)) { CK_TRACE(sig, 4, c, cl, cc); return false; }  // uniform
+    CK_TRACE(sig, 0, c, cl, cc);
     if (tid < (int)c) {
         const unsigned long long e = sh.key[tid];
         unsigned above = 0;
@@ -795,8 +806,11 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             listed = fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);
         } else {
             if (CHUNKED && attempt == 0) {
-                listed = fast_kth_chunks(row, msk, m, d.sel_tmax + (size_t)kblk * nch, nch, kth, 2.f * D, sh, &kkey,
-                                         &tlo, &below);
+                // (the band below starts at or above lam_sel - D outside the warm start's pass;
+                // the list's floor sits a little lower, below any rounding of that bound)
+                const float lo = prop ? 0.f : (lam_sel - D) * (1.f - 2e-6f);
+                listed = fast_kth_chunks(row, msk, m, d.sel_tmax + (size_t)kblk * nch, nch, kth, 2.f * D, lo, sh,
+                                         &kkey, &tlo, &below, i);
                 __syncthreads();  // (a failed chunk route's shared state is read before it is reused)
             }
             if (!listed) listed = fast_kth_row(rk, row, msk, m, kth, sh, &kkey, &tlo, &below);
@@ -834,6 +848,9 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     }
     kc = min(kc, (unsigned)SEL_KCAP);
     ST_VAL(6, kc);
+#ifdef MPL_SEL_TRACE
+    if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][15] = kc;
+#endif
 
     // Re-score the candidates (one warp each) and mark the violators.
     if (tid == 0) { sh.vc = 0; sh.offmax = 0.f; }
@@ -1212,9 +1229,9 @@ __global__ void __launch_bounds__(256) k_sel_maxima(Dev d, int cur) {
 extern "C" int mpl_debug_sel_trace(long long* out, int count, int reset) {
     if (count > 8192) count = 8192;
     if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-    if (cudaMemcpyFromSymbol(out, g_sel_trace, sizeof(long long) * 10 * (size_t)count) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(out, g_sel_trace, sizeof(long long) * 20 * (size_t)count) != cudaSuccess) return -1;
     if (reset) {
-        static long long zero[8192][10];
+        static long long zero[8192][20];
         if (cudaMemcpyToSymbol(g_sel_trace, zero, sizeof(zero)) != cudaSuccess) return -1;
     }
     return count;
