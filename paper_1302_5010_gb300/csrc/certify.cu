@@ -1539,7 +1539,7 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
         sh.F.ldf = fsm ? ((msm + 1) | 1) : ((scap + 1) | 1);
         // the factor workspace: the signal's own, or in a clustered finish this CTA's slot of
         // the pool (the CTAs of a cluster factor the same block side by side); the finishes of
-        // the two iteration parities run concurrently, so each parity has its own half
+        // the FIN_SLOTS list slots run concurrently, so each slot has its own part
         double* wk = C > 1 ? d.fin_pool + ((size_t)cur * d.fin_slots + blockIdx.x) * smax * smax
                            : d.chol + (size_t)i * smax * smax;
         sh.F.Mf = fsm ? q : reinterpret_cast<float*>(wk);
@@ -2017,8 +2017,8 @@ __global__ void __launch_bounds__(NT, 2 * FIN_THREADS / NT) k_finish(Dev d, int 
                 d.state[i] = ST_DONE;
                 d.sstatus[i] = MPL_SIG_EARLY_STOP;
             } else {
-                // back into the active list two iterations on: the worst-case analysis of
-                // its exact residual certifies the atoms outside S (eq. 8)
+                // back into the active list once this finish is done: the worst-case
+                // analysis of its exact residual certifies the atoms outside S (eq. 8)
                 d.reent[cur][atomicAdd(&d.cnt->reent_n[cur], 1)] = i;
             }
         }

@@ -51,8 +51,8 @@ struct mpl_ctx {
     // options
     int rho = 1, precision = 0, max_outer = 200, smax = 0, inner_max = 400, warm = 0;
     int sync_every = 2, profile = 0;
-    cudaStream_t side = nullptr;  // the exact finish of even iterations runs here (and of odd ones on side_odd),
-    cudaStream_t side_odd = nullptr;  // overlapping the master problems and the next iteration
+    cudaStream_t fin_st[FIN_SLOTS] = {};  // the exact finish of iteration t runs on fin_st[t % FIN_SLOTS],
+                                          // overlapping the master problems and the next iterations
     cudaStream_t main = nullptr;  // graph-mode solves run here (captured streams cannot be the legacy one)
     cudaStream_t side2 = nullptr; // master problems with blocks outside shared memory, beside the others
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -60,7 +60,8 @@ struct mpl_ctx {
     cudaEvent_t ev_sel = nullptr;                 // the selection of the current iteration is done
     cudaEvent_t ev_fcnt = nullptr;                // ... and its finish count copied to fin_h
     int* fin_h = nullptr;                         // pinned
-    cudaEvent_t ev_fin[2] = {nullptr, nullptr};   // the exact finish of the last iteration of each parity
+    cudaEvent_t ev_fin[FIN_SLOTS] = {};           // the exact finish of the last iteration of each slot
+    int* ctl_h = nullptr;                         // pinned: per slot {fslot, mslots} copied to the counters
     int use_graph = 1;
     struct GraphEntry {
         int p, tk, par, nog, prof, route, part;
@@ -217,11 +218,11 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     CK(alloc(h, &d.ritz, ps));
     CK(alloc(h, &d.chol, pss));  // FP64 factor fallback (and FP32 factors beyond shared memory)
     // the CTAs of a clustered finish each factor in a workspace of their own: fin_slots per
-    // iteration parity (the finishes of consecutive iterations run at the same time); a
+    // finish list slot (the finishes of consecutive iterations run at the same time); a
     // clustered launch has at most two CTAs per SM
 #if !defined(MPL_NO_FIN_CLUSTER)
     d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
-    CK(alloc(h, &d.fin_pool, 2 * (size_t)d.fin_slots * smax * smax));
+    CK(alloc(h, &d.fin_pool, (size_t)FIN_SLOTS * d.fin_slots * smax * smax));
 #endif
     // chunk maxima of the score rows above the shared-memory row cache (1/8 of the score matrix)
     if (m > SEL_ROWCACHE_ATOMS) {
@@ -231,9 +232,13 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
         CK(cudaMemset(d.sel_nf, 0, (size_t)P * sizeof(int)));
     }
     int** ints[] = {&d.state, &d.ssize, &d.snew, &d.finalized, &d.outer, &d.inner, &d.finishes,
-                    &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_fin[0],
-                    &d.list_fin[1], &d.reent[0], &d.reent[1], &d.list_apg, &d.explore, &d.early};
+                    &d.fails, &d.sstatus, &d.nnz, &d.act[0], &d.act[1], &d.list_grow, &d.list_apg,
+                    &d.explore, &d.early};
     for (int** q : ints) CK(alloc(h, q, (size_t)P));
+    for (int q = 0; q < FIN_SLOTS; ++q) {
+        CK(alloc(h, &d.list_fin[q], (size_t)P));
+        CK(alloc(h, &d.reent[q], (size_t)P));
+    }
     CK(alloc(h, &d.rnorm, (size_t)P));
     CK(alloc(h, &d.res_part, (size_t)P * res_blocks(n) * 3));
     CK(alloc(h, &d.res_tick, (size_t)P));
@@ -429,6 +434,7 @@ mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
     if (cudaMalloc(&h->scal, 16 * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMallocHost(&h->cnt_h, sizeof(Counters)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMallocHost(&h->fin_h, sizeof(int)) != cudaSuccess) return fail(MPL_ERR_OOM);
+    if (cudaMallocHost(&h->ctl_h, 2 * FIN_SLOTS * sizeof(int)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMemcpy(h->A32, A, bytes, cudaMemcpyDefault) != cudaSuccess) return fail(MPL_ERR_CUDA);
     int64_t nl = 0;
     if (launch_colnorm(h->A32, n, m, h->colnorm, nullptr, 0, &nl) != cudaSuccess) return fail(MPL_ERR_CUDA);
@@ -455,16 +461,19 @@ void mpl_destroy(mpl_handle_t h) {
     for (float* q : {h->pw, h->pwb, h->pm1, h->pm2, h->pgrad, h->pacc, h->rn}) cudaFree(q);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
     if (h->fin_h) cudaFreeHost(h->fin_h);
+    if (h->ctl_h) cudaFreeHost(h->ctl_h);
     clear_graphs(h);
-    if (h->side) cudaStreamDestroy(h->side);
+    for (cudaStream_t q : h->fin_st)
+        if (q) cudaStreamDestroy(q);
     if (h->main) cudaStreamDestroy(h->main);
     if (h->side2) cudaStreamDestroy(h->side2);
     if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
-    if (h->side_odd) cudaStreamDestroy(h->side_odd);
-    for (cudaEvent_t e : {h->ev_sel, h->ev_fcnt, h->ev_fin[0], h->ev_fin[1]})
+    for (cudaEvent_t e : {h->ev_sel, h->ev_fcnt})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_fin)
         if (e) cudaEventDestroy(e);
     for (auto e : h->evpool) cudaEventDestroy(e);
     delete h;
@@ -644,12 +653,13 @@ static int iteration_route(const mpl_ctx* h, const Dev& d, int t) {
 }
 
 // One outer iteration of Algorithm 1 for every active signal, in two parts (kernels only):
-//   part 0  re-entry of the signals whose exact finish two iterations ago is done, the
-//           worst-case analysis (correlation) and the selection, which ends by building the
-//           work lists;
+//   part 0  re-entry of the signals whose exact finish of an earlier iteration is done (the
+//           slots the host put in the device counter mslots), the worst-case analysis
+//           (correlation) and the selection, which ends by building the work lists;
 //   part 1  Gram growth, master problems and residual update of the signals that took atoms.
 // Between the parts the host launches the exact finish of the signals without violators
-// (list_fin[t & 1]) on its own stream, where it overlaps part 1 and the whole next iteration.
+// (list_fin[t % FIN_SLOTS]) on its own stream, where it overlaps part 1 and the next
+// iterations.
 // pt == nullptr: no timing events (graph capture).
 static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int act_ub, cudaStream_t run,
                                PhaseTimer* pt, int64_t* nl) {
@@ -658,7 +668,7 @@ static cudaError_t launch_part(mpl_ctx* h, const Dev& d, int t, int part, int ac
     if (part == 0) {
         const int no_grow = t >= h->max_outer;
         const int route = iteration_route(h, d, t);
-        if (t >= 2 && (e = launch_merge(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
+        if (t >= 1 && (e = launch_merge(d, cur, act_ub, run, nl)) != cudaSuccess) return e;
         const int ph_corr = route == ROUTE_Q ? PH_QROUTE : 1;
         cudaEvent_t e0 = pt ? pt->begin_if(ph_corr, run) : nullptr;
         if (route == ROUTE_Q) {
@@ -785,18 +795,17 @@ static cudaError_t iteration_graph(mpl_ctx* h, const Dev& d, int t, int part, in
 
 // The library's streams and events, once per handle.  The outer-iteration chain is the
 // critical path: its blocks go first when an SM frees up; the exact finishes of converged
-// signals (two streams, by iteration parity) fill in behind it.
+// signals (FIN_SLOTS streams, by list slot) fill in behind it.
 static mpl_status_t ensure_streams(mpl_ctx* h) {
-    if (h->side) return MPL_OK;
+    if (h->main) return MPL_OK;
     int prio_lo = 0, prio_hi = 0;
     CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-    CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
-    CK(cudaStreamCreateWithPriority(&h->side_odd, cudaStreamNonBlocking, prio_lo));
-    CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
+    for (cudaStream_t& q : h->fin_st) CK(cudaStreamCreateWithPriority(&q, cudaStreamNonBlocking, prio_lo));
     CK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, prio_hi));
-    cudaEvent_t* evs[] = {&h->ev_fork2, &h->ev_join2, &h->ev_in,  &h->ev_out,
-                          &h->ev_sel,   &h->ev_fcnt,  &h->ev_fin[0], &h->ev_fin[1]};
+    cudaEvent_t* evs[] = {&h->ev_fork2, &h->ev_join2, &h->ev_in, &h->ev_out, &h->ev_sel, &h->ev_fcnt};
     for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (cudaEvent_t& e : h->ev_fin) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithPriority(&h->main, cudaStreamNonBlocking, prio_hi));
     return MPL_OK;
 }
 
@@ -877,13 +886,16 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     PhaseTimer pt{h, st, {}, 0};
     cudaEvent_t t_all = pt.begin();
     CK(launch_init(d, st, &nl));
-    // live: an upper bound on the signals not yet done (active, or in a finish of one of the
-    // last two iterations, whose re-entry is still to come); grids are sized by it outside
-    // graph mode (captured graphs are sized for p)
+    // live: an upper bound on the signals not yet done (active, or in a finish whose signals
+    // have not come back yet); grids are sized by it outside graph mode (captured graphs are
+    // sized for p)
     int live = p;
-    // every finish hands its work back through reent[], and each waits for the finish of the
-    // iteration before last (same parity), so a retry takes three iterations
-    const int hard_cap = h->max_outer + 3 * FIN_MAX_FAILS + 10;
+    // every finish hands its work back through reent[] of its list slot; an iteration merges
+    // the finishes that are done by its start and waits only for the one whose slot it reuses
+    // (FIN_SLOTS iterations on), so a retry takes at least two iterations
+    const int hard_cap = h->max_outer + (FIN_SLOTS + 1) * FIN_MAX_FAILS + 10;
+    bool pend[FIN_SLOTS] = {};  // finish launched, its signals not merged yet
+    int pend_n[FIN_SLOTS] = {};  // and how many signals it took
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
     double graph_phase[16] = {0};
     int t = 0;
@@ -901,9 +913,35 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
 #endif
     for (; live > 0 && t < hard_cap; ++t) {
         const int par = t & 1;
-        cudaStream_t fin_st = par ? h->side_odd : h->side;
-        // the finish of iteration t - 2 (same parity) is done before its signals re-enter
-        CK(cudaStreamWaitEvent(st, h->ev_fin[par], 0));
+        const int fs = t % FIN_SLOTS;
+        cudaStream_t fin_st = h->fin_st[fs];
+        // re-entry: the finishes that are done by now, and the one whose slot this iteration's
+        // selection fills (launched FIN_SLOTS iterations ago), waited for
+        int mask = 0;
+        for (int q = 0; q < FIN_SLOTS; ++q) {
+            if (!pend[q]) continue;
+            bool ready = q == fs;
+            if (!ready) {
+                const cudaError_t eq = cudaEventQuery(h->ev_fin[q]);
+                if (eq == cudaSuccess) {
+                    ready = true;
+                } else if (eq == cudaErrorNotReady) {
+                    const cudaError_t le = cudaGetLastError();  // (not an error: still running)
+                    if (le != cudaSuccess && le != cudaErrorNotReady) return MPL_ERR_CUDA;
+                } else {
+                    return MPL_ERR_CUDA;
+                }
+            }
+            if (ready) {
+                CK(cudaStreamWaitEvent(st, h->ev_fin[q], 0));
+                mask |= 1 << q;
+                pend[q] = false;
+            }
+        }
+        int* ctl = h->ctl_h + 2 * fs;  // (the copy has run before the next use of this entry)
+        ctl[0] = fs;
+        ctl[1] = mask;
+        CK(cudaMemcpyAsync(&d.cnt->fslot, ctl, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
 #ifdef MPL_TIMELINE
         mark(0, st);
 #endif
@@ -921,7 +959,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                 // the selection is done: its count of signals without violators comes back
                 // while part 1 runs
                 CK(cudaEventRecord(h->ev_sel, st));
-                CK(cudaMemcpyAsync(h->fin_h, &d.cnt->fin_par[par], sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(h->fin_h, &d.cnt->fin_par[fs], sizeof(int), cudaMemcpyDeviceToHost, st));
                 CK(cudaEventRecord(h->ev_fcnt, st));
 #ifdef MPL_TIMELINE
                 mark(1, st);
@@ -930,7 +968,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         }
         {
             // the exact finish of the signals without violators, beside part 1 and the next
-            // iteration, its grid and cluster size from their count
+            // iterations, its grid and cluster size from their count
             CK(cudaEventSynchronize(h->ev_fcnt));
             const int nf = *h->fin_h;
             CK(cudaStreamWaitEvent(fin_st, h->ev_sel, 0));
@@ -938,9 +976,11 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
 #ifdef MPL_TIMELINE
             mark(3, fin_st);
 #endif
-            if (nf > 0) CK(launch_finish(d, par, nf, nf, finish_scap(h, d, t), fin_st, &nl, h->sms));
+            if (nf > 0) CK(launch_finish(d, fs, nf, nf, finish_scap(h, d, t), fin_st, &nl, h->sms));
             pt.end(4, f0, fin_st);
-            CK(cudaEventRecord(h->ev_fin[par], fin_st));
+            CK(cudaEventRecord(h->ev_fin[fs], fin_st));
+            pend[fs] = nf > 0;
+            pend_n[fs] = nf;
 #ifdef MPL_TIMELINE
             mark(4, fin_st);
 #endif
@@ -958,12 +998,28 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                         h->cnt_h->bounds_site);
 #endif
             if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
-            // active next iteration, plus the signals of the last two finishes
-            live = h->cnt_h->act_n[(t & 1) ^ 1] + h->cnt_h->fin_par[0] + h->cnt_h->fin_par[1];
+            // active next iteration, plus the signals of the finishes not merged yet
+            const int act_next = h->cnt_h->act_n[par ^ 1];
+            int in_fin = 0;
+            for (int q = 0; q < FIN_SLOTS; ++q) in_fin += pend[q] ? pend_n[q] : 0;
+            live = act_next + in_fin;
+            if (act_next == 0 && in_fin > 0) {
+                // nothing left to iterate on but finishes in flight: wait for them, and go on
+                // only for the signals they send back
+                for (int q = 0; q < FIN_SLOTS; ++q)
+                    if (pend[q]) CK(cudaEventSynchronize(h->ev_fin[q]));
+                CK(cudaMemcpyAsync(h->cnt_h, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (h->cnt_h->err != 0) return h->cnt_h->err == DERR_TIMEOUT ? MPL_ERR_TIMEOUT : MPL_ERR_CUDA;
+                int back = 0;
+                for (int q = 0; q < FIN_SLOTS; ++q) back += pend[q] ? h->cnt_h->reent_n[q] : 0;
+                if (back == 0)
+                    for (bool& q : pend) q = false;
+                live = back;
+            }
 
 #ifdef MPL_TIMELINE
-            fprintf(stderr, "TC %d %d %d %d\n", t, h->cnt_h->act_n[(t & 1) ^ 1], h->cnt_h->fin_par[t & 1],
-                    h->cnt_h->grow_n);
+            fprintf(stderr, "TC %d %d %d %d\n", t, act_next, h->cnt_h->fin_par[fs], h->cnt_h->grow_n);
 #endif
             if (graph && h->profile) {
                 for (size_t gi : window)
@@ -977,8 +1033,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         }
     }
     // the last finishes, then the results
-    CK(cudaStreamWaitEvent(st, h->ev_fin[0], 0));
-    CK(cudaStreamWaitEvent(st, h->ev_fin[1], 0));
+    for (cudaEvent_t e : h->ev_fin) CK(cudaStreamWaitEvent(st, e, 0));
     CK(cudaMemsetAsync(Xd, 0, (size_t)m * p * sizeof(float), st));
     CK(launch_scatter(d, Xd, nullptr, st, &nl));
     pt.end(0, t_all);

@@ -48,14 +48,20 @@ enum SigState : int {
     ST_REFINE = 4,    // the exact finish failed: one more master-problem pass next iteration
 };
 
+// The exact finishes of outer iteration t use list slot t % FIN_SLOTS: a finish runs beside
+// the following iterations, and an iteration waits only for the finish whose slot it reuses.
+constexpr int FIN_SLOTS = 4;
+
 // Device-side counters and work-list lengths (one instance per solve).
 struct Counters {
     int act_n[2];    // active-list lengths (double-buffered by outer-iteration parity)
     int grow_n;      // signals that took new atoms
     int fin_n;       // signals sent to the exact finish (this iteration)
-    int fin_par[2];  // ... by outer-iteration parity (a finish runs while the next iteration does)
-    int reent_n[2];  // finished signals waiting to re-enter the active list, by the parity of
-                     // the iteration whose finish they left (merged two iterations later)
+    int fin_par[FIN_SLOTS];  // ... by list slot (a finish runs while the next iterations do)
+    int reent_n[FIN_SLOTS];  // finished signals waiting to re-enter the active list, by the
+                             // slot of the finish they left
+    int fslot;       // the slot this iteration's selection fills (set by the host per iteration)
+    int mslots;      // bit s: the finish of slot s is done, merge its signals this iteration
     int apg_n;       // signals in the master-problem list (grow + failed finishes)
     int apg_head;    // work-queue head of the persistent master-problem kernel
     int apg_head2;   // head of its second queue (blocks streamed from global memory)
@@ -118,8 +124,8 @@ struct Dev {
     float* h;                    // p x smax A_S^T b
     float* ritz;                 // p x smax power-iteration vector (warm start of L)
     double* chol;                // p x smax x smax FP64 workspace (large supports)
-    double* fin_pool;            // 2 x fin_slots more such workspaces: one per CTA of a clustered
-    int fin_slots;               // finish, a half per iteration parity
+    double* fin_pool;            // FIN_SLOTS x fin_slots more such workspaces: one per CTA of a
+    int fin_slots;               // clustered finish, a part per finish list slot
     unsigned* sel_tmax;          // P x ceil(m / SEL_CHUNK) chunk maxima of the score rows (m above the row cache)
     int* sel_nf;                 // P flags: a non-finite score in the row
     int* state;                  // p SigState
@@ -149,8 +155,8 @@ struct Dev {
     int* ovf_list;               // signals whose candidate band overflowed (second pass), or null
     Counters* ovf_cnt;           // its length in act_n[parity]
     int* list_grow;              // signals with new atoms
-    int* list_fin[2];            // signals sent to the exact finish, by outer-iteration parity
-    int* reent[2];               // finished signals to merge back into the active list, by parity
+    int* list_fin[FIN_SLOTS];    // signals sent to the exact finish, by list slot
+    int* reent[FIN_SLOTS];       // finished signals to merge back into the active list, by slot
     int* list_apg;               // master-problem work list
     Counters* cnt;
     __device__ const int* act_of(int c) const { return act[c]; }
@@ -221,14 +227,15 @@ cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
 cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl);
 // Gram growth gathered from Q (MPL_OPT_QGRAM): same outputs, bit for bit, as launch_gram.
 cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl);
-// The exact finish of the signals the selection of an iteration with parity cur sent to it
-// (list_fin[cur]); each finished signal that is not done joins reent[cur].  ub bounds the
+// The exact finish of the signals the selection of an iteration sent to list slot `slot`
+// (list_fin[slot]); each finished signal that is not done joins reent[slot].  ub bounds the
 // number of finishing signals, est estimates it; when est is small against the sms SMs a
 // signal's finish runs on a cluster of up to FIN_CLUSTER_MAX CTAs.
 constexpr int FIN_CLUSTER_MAX = 8;
-cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cudaStream_t s, int64_t* nl, int sms);
-// Append reent[cur] to the active list of an iteration with parity cur (rows for the GEMM
-// included); the finishes that filled it must be complete.
+cudaError_t launch_finish(const Dev& d, int slot, int ub, int est, int scap, cudaStream_t s, int64_t* nl, int sms);
+// Append reent[s] of every slot s in the device counter mslots to the active list of an
+// iteration with parity cur (rows for the GEMM included); the finishes that filled those
+// slots must be complete.
 cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl);
 // Master-problem launches: every signal of the work list, or only those whose Gram block fits
 // shared memory, or only those streamed from global memory.

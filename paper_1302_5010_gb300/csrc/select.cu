@@ -1124,7 +1124,7 @@ __device__ void compact_body(const Dev& d, int cur) {
             if (f[q]) {
                 if (MPL_OOB(off < 0 || off >= d.p || sig < 0 || sig >= d.p, 504)) continue;
                 if (q == 0) { d.list_grow[off] = sig; d.list_apg[off] = sig; }
-                else if (q == 1) d.list_fin[cur][off] = sig;
+                else if (q == 1) d.list_fin[d.cnt->fslot][off] = sig;
                 else {
                     nxt[off] = sig;
                     if (d.pos) d.pos[sig] = off;  // its GEMM row next iteration
@@ -1141,7 +1141,7 @@ __device__ void compact_body(const Dev& d, int cur) {
         d.cnt->grow_n = base[0];
         d.cnt->apg_n = base[0];
         d.cnt->fin_n = base[1];
-        d.cnt->fin_par[cur] = base[1];
+        d.cnt->fin_par[d.cnt->fslot] = base[1];
         d.cnt->act_n[cur ^ 1] = base[2];
         d.cnt->apg_head = 0;
         d.cnt->apg_head2 = 0;

@@ -162,8 +162,9 @@ __global__ void __launch_bounds__(256) k_init(Dev d) {
             d.cnt->sel_done = 0;
             d.cnt->bounds_site = 0;
             d.cnt->apg_elems = d.cnt->apg_gl_elems = 0ull;
-            d.cnt->fin_par[0] = d.cnt->fin_par[1] = 0;
-            d.cnt->reent_n[0] = d.cnt->reent_n[1] = 0;
+            for (int q = 0; q < FIN_SLOTS; ++q) d.cnt->fin_par[q] = d.cnt->reent_n[q] = 0;
+            d.cnt->fslot = 0;
+            d.cnt->mslots = 0;
             d.cnt->res_bytes = d.cnt->gram_bytes = d.cnt->fin_bytes = 0ull;
         }
     }
@@ -1311,33 +1312,44 @@ cudaError_t launch_residual(const Dev& d, int ub, cudaStream_t s, int64_t* nl) {
 
 // Per-signal statistics packed on the device into the host struct layout (one copy back).
 // ------------------------------------------------------------------ re-entry
-// Finished signals (reent[cur]) go back to the end of the active list of this iteration,
-// with their rows in the GEMM's compacted BF16 residual (the finish wrote the per-signal
-// copy); the counters are updated by k_merge_count once every row is in place.
+// Finished signals (reent[s] of the slots s in mslots, in slot order) go back to the end of
+// the active list of this iteration, with their rows in the GEMM's compacted BF16 residual
+// (the finish wrote the per-signal copy); the counters are updated by k_merge_count once
+// every row is in place.
 __global__ void __launch_bounds__(256) k_merge(Dev d, int cur) {
     pdl_enter();
-    const int base = d.cnt->act_n[cur], cnt = d.cnt->reent_n[cur], n = d.n;
-    for (int b = blockIdx.x; b < cnt; b += gridDim.x) {
-        const int i = d.reent[cur][b];
-        const int row = base + b;
-        if (MPL_OOB(row >= d.p || i < 0 || i >= d.p, 101)) continue;
-        if (threadIdx.x == 0) {
-            d.act[cur][row] = i;
-            if (d.pos) d.pos[i] = row;
+    const int mask = d.cnt->mslots, n = d.n;
+    int base = d.cnt->act_n[cur];
+    for (int q = 0; q < FIN_SLOTS; ++q) {
+        if (!((mask >> q) & 1)) continue;
+        const int cnt = d.cnt->reent_n[q];
+        for (int b = blockIdx.x; b < cnt; b += gridDim.x) {
+            const int i = d.reent[q][b];
+            const int row = base + b;
+            if (MPL_OOB(row >= d.p || i < 0 || i >= d.p, 101)) continue;
+            if (threadIdx.x == 0) {
+                d.act[cur][row] = i;
+                if (d.pos) d.pos[i] = row;
+            }
+            if (d.pos) {
+                const __nv_bfloat16* src = d.R16 + (size_t)i * n;
+                __nv_bfloat16* dst = d.R16c + (size_t)row * n;
+                for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+            }
         }
-        if (d.pos) {
-            const __nv_bfloat16* src = d.R16 + (size_t)i * n;
-            __nv_bfloat16* dst = d.R16c + (size_t)row * n;
-            for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
-        }
+        base += cnt;
     }
 }
 
 __global__ void k_merge_count(Dev d, int cur) {
     pdl_enter();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        d.cnt->act_n[cur] += d.cnt->reent_n[cur];
-        d.cnt->reent_n[cur] = 0;
+        const int mask = d.cnt->mslots;
+        for (int q = 0; q < FIN_SLOTS; ++q) {
+            if (!((mask >> q) & 1)) continue;
+            d.cnt->act_n[cur] += d.cnt->reent_n[q];
+            d.cnt->reent_n[q] = 0;
+        }
     }
 }
 
