@@ -485,7 +485,7 @@ def solve_once(args):
     B = torch.from_numpy(P.B).to(dev)
     lam = torch.from_numpy(P.lam).to(dev)
     opts = dict(qgram=args.solve_qgram, graph=args.solve_graph, sync_every=args.solve_sync,
-                qroute=args.solve_qroute)
+                qroute=args.solve_qroute, reentry=args.solve_reentry)
     if SMAX.get(args.solve_once):
         opts["smax"] = SMAX[args.solve_once]
     if args.path == "mixed":
@@ -723,6 +723,9 @@ def main():
     ap.add_argument("--solve-graph", type=int, default=1)
     ap.add_argument("--solve-sync", type=int, default=4)
     ap.add_argument("--solve-qroute", type=int, default=0, help="identity route bound of the --solve-once run")
+    ap.add_argument("--solve-reentry", type=int, default=0, choices=[0, 1],
+                    help="MPL_OPT_REENTRY of the --solve-once run (1: the same launches on every run, e.g. "
+                         "for a launch list whose skip count comes from a run without the profiler)")
     args = ap.parse_args()
     if args.solve_once:
         solve_once(args)

@@ -109,10 +109,21 @@ typedef enum {
                                      MPL_OPT_QROUTE, by one FMA chain per entry in the order
                                      the computed Gram block uses, so the solution is
                                      bit-identical either way.  0 = compute (default). */
-    MPL_OPT_GEMM_TILE = 19        /* signals per output tile of the BF16 tensor-core GEMM
+    MPL_OPT_GEMM_TILE = 19,       /* signals per output tile of the BF16 tensor-core GEMM
                                      (MPL_OPT_PRECISION = 1): 64, 128 (default) or 256; every
                                      score is accumulated in the same order whatever the
                                      tile, so the solution does not depend on it. */
+    MPL_OPT_REENTRY = 20          /* when a signal whose exact finish certified its active set
+                                     rejoins the loop for the worst-case analysis of eq. (8):
+                                     0 (default): at the first outer iteration that starts after
+                                     its finish is done (an iteration waits only for the finish
+                                     of four iterations back).  The outer iteration a signal's
+                                     next finish falls in, and so that finish's launch shape,
+                                     then depends on timing, and the certified solution may
+                                     differ between runs in its last bits.  1: exactly two
+                                     outer iterations later (each iteration waits for the
+                                     finish of two iterations back): the same bits on every
+                                     run, whatever the timing.  Both certify every signal. */
 } mpl_option_t;
 
 /* Per-signal outcome (host struct filled by mpl_get_stats). */

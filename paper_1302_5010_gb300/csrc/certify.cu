@@ -2078,11 +2078,12 @@ cudaError_t launch_finish(const Dev& d, int cur, int ub, int est, int scap, cuda
     // (at most ub), clusters of C so that C est stays within two CTAs per SM (four per SM
     // measured slower: the clusters then crowd out the concurrent iteration) and every CTA of
     // the grid has a workspace slot; the row-block exchange needs the residual pair in shared
-    // memory and float4 rows.  (The solve passes the exact count as both.)  Builds with
-    // -DMPL_NO_FIN_CLUSTER keep one CTA per signal.
+    // memory and float4 rows, and signals of at least FIN_CLUSTER_MIN_N entries (shorter
+    // sweeps gain less than the cluster barriers cost).  (The solve passes the exact count
+    // as both.)  Builds with -DMPL_NO_FIN_CLUSTER keep one CTA per signal.
     int C = 1;
 #if !defined(MPL_NO_FIN_CLUSTER)
-    if (rsm && (d.n & 3) == 0 && sms > 0 && d.fin_pool)
+    if (rsm && (d.n & 3) == 0 && d.n >= FIN_CLUSTER_MIN_N && sms > 0 && d.fin_pool)
         while (C < FIN_CLUSTER_MAX && 2 * C * est <= 2 * sms && 2 * C * ub <= d.fin_slots) C *= 2;
 #endif
     const bool wide = dyn > FIN_SMEM_TWO_CTAS;

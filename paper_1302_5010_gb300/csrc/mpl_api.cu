@@ -61,7 +61,6 @@ struct mpl_ctx {
     cudaEvent_t ev_fcnt = nullptr;                // ... and its finish count copied to fin_h
     int* fin_h = nullptr;                         // pinned
     cudaEvent_t ev_fin[FIN_SLOTS] = {};           // the exact finish of the last iteration of each slot
-    int* ctl_h = nullptr;                         // pinned: per slot {fslot, mslots} copied to the counters
     int use_graph = 1;
     struct GraphEntry {
         int p, tk, par, nog, prof, route, part;
@@ -111,6 +110,7 @@ struct mpl_ctx {
     // tensor-map block for the BF16 GEMM (A16, R16c)
     alignas(64) unsigned char tmap[TC_TMAP_BYTES];
     int gemm_bn = 128;  // signals per tile of the BF16 GEMM (MPL_OPT_GEMM_TILE)
+    int reentry = 0;    // MPL_OPT_REENTRY: 0 as soon as the finish is done, 1 two iterations on
     int tmap_p = -1;
     // last solve
     int last_p = 0;
@@ -221,8 +221,10 @@ mpl_status_t ensure_ws(mpl_ctx* h, int p) {
     // finish list slot (the finishes of consecutive iterations run at the same time); a
     // clustered launch has at most two CTAs per SM
 #if !defined(MPL_NO_FIN_CLUSTER)
-    d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
-    CK(alloc(h, &d.fin_pool, (size_t)FIN_SLOTS * d.fin_slots * smax * smax));
+    if (n >= FIN_CLUSTER_MIN_N && (n & 3) == 0) {
+        d.fin_slots = std::min(2 * std::max(h->sms, 1), FIN_CLUSTER_MAX * P);
+        CK(alloc(h, &d.fin_pool, (size_t)FIN_SLOTS * d.fin_slots * smax * smax));
+    }
 #endif
     // chunk maxima of the score rows above the shared-memory row cache (1/8 of the score matrix)
     if (m > SEL_ROWCACHE_ATOMS) {
@@ -434,7 +436,6 @@ mpl_status_t mpl_create(const float* A, int n, int m, mpl_handle_t* out) {
     if (cudaMalloc(&h->scal, 16 * sizeof(float)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMallocHost(&h->cnt_h, sizeof(Counters)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMallocHost(&h->fin_h, sizeof(int)) != cudaSuccess) return fail(MPL_ERR_OOM);
-    if (cudaMallocHost(&h->ctl_h, 2 * FIN_SLOTS * sizeof(int)) != cudaSuccess) return fail(MPL_ERR_OOM);
     if (cudaMemcpy(h->A32, A, bytes, cudaMemcpyDefault) != cudaSuccess) return fail(MPL_ERR_CUDA);
     int64_t nl = 0;
     if (launch_colnorm(h->A32, n, m, h->colnorm, nullptr, 0, &nl) != cudaSuccess) return fail(MPL_ERR_CUDA);
@@ -461,7 +462,6 @@ void mpl_destroy(mpl_handle_t h) {
     for (float* q : {h->pw, h->pwb, h->pm1, h->pm2, h->pgrad, h->pacc, h->rn}) cudaFree(q);
     if (h->cnt_h) cudaFreeHost(h->cnt_h);
     if (h->fin_h) cudaFreeHost(h->fin_h);
-    if (h->ctl_h) cudaFreeHost(h->ctl_h);
     clear_graphs(h);
     for (cudaStream_t q : h->fin_st)
         if (q) cudaStreamDestroy(q);
@@ -546,6 +546,10 @@ mpl_status_t mpl_set_option(mpl_handle_t h, int key, double v) {
             if (v != 64 && v != 128 && v != 256) return MPL_ERR_ARG;
             h->gemm_bn = (int)v;
             return MPL_OK;
+        case MPL_OPT_REENTRY:
+            if (v != 0 && v != 1) return MPL_ERR_ARG;
+            h->reentry = (int)v;
+            return MPL_OK;
         case MPL_OPT_OMEGA:
             if (v < 1 || v > 16) return MPL_ERR_ARG;
             h->omega = (int)v;
@@ -577,6 +581,7 @@ mpl_status_t mpl_get_option(mpl_handle_t h, int key, double* v) {
         case MPL_OPT_QROUTE: *v = h->qroute; return MPL_OK;
         case MPL_OPT_QGRAM: *v = h->qgram; return MPL_OK;
         case MPL_OPT_GEMM_TILE: *v = h->gemm_bn; return MPL_OK;
+        case MPL_OPT_REENTRY: *v = h->reentry; return MPL_OK;
         case MPL_OPT_OMEGA: *v = h->omega; return MPL_OK;
         case MPL_OPT_STOP_RINF: *v = h->stop_rinf; return MPL_OK;
         case MPL_OPT_STOP_R2: *v = h->stop_r2; return MPL_OK;
@@ -896,6 +901,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
     const int hard_cap = h->max_outer + (FIN_SLOTS + 1) * FIN_MAX_FAILS + 10;
     bool pend[FIN_SLOTS] = {};  // finish launched, its signals not merged yet
     int pend_n[FIN_SLOTS] = {};  // and how many signals it took
+    int pend_t[FIN_SLOTS] = {};  // and the iteration it was launched in
     std::vector<size_t> window;  // graphs launched since the last handshake (phase timing)
     double graph_phase[16] = {0};
     int t = 0;
@@ -916,12 +922,13 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
         const int fs = t % FIN_SLOTS;
         cudaStream_t fin_st = h->fin_st[fs];
         // re-entry: the finishes that are done by now, and the one whose slot this iteration's
-        // selection fills (launched FIN_SLOTS iterations ago), waited for
+        // selection fills (launched FIN_SLOTS iterations ago), waited for; with
+        // MPL_OPT_REENTRY = 1 exactly the finish of two iterations back, waited for
         int mask = 0;
         for (int q = 0; q < FIN_SLOTS; ++q) {
             if (!pend[q]) continue;
-            bool ready = q == fs;
-            if (!ready) {
+            bool ready = q == fs || (h->reentry == 1 && pend_t[q] + 2 <= t);
+            if (!ready && h->reentry == 0) {
                 const cudaError_t eq = cudaEventQuery(h->ev_fin[q]);
                 if (eq == cudaSuccess) {
                     ready = true;
@@ -938,10 +945,8 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
                 pend[q] = false;
             }
         }
-        int* ctl = h->ctl_h + 2 * fs;  // (the copy has run before the next use of this entry)
-        ctl[0] = fs;
-        ctl[1] = mask;
-        CK(cudaMemcpyAsync(&d.cnt->fslot, ctl, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+        // (the slot itself advances on the device, in the merge at the start of part 0)
+        if (mask) CK(launch_set_merge(d, mask, st, &nl));
 #ifdef MPL_TIMELINE
         mark(0, st);
 #endif
@@ -981,6 +986,7 @@ mpl_status_t bmpl_solve(mpl_handle_t h, const float* B, int p, const float* lamb
             CK(cudaEventRecord(h->ev_fin[fs], fin_st));
             pend[fs] = nf > 0;
             pend_n[fs] = nf;
+            pend_t[fs] = t;
 #ifdef MPL_TIMELINE
             mark(4, fin_st);
 #endif

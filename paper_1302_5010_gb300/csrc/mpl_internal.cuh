@@ -60,8 +60,9 @@ struct Counters {
     int fin_par[FIN_SLOTS];  // ... by list slot (a finish runs while the next iterations do)
     int reent_n[FIN_SLOTS];  // finished signals waiting to re-enter the active list, by the
                              // slot of the finish they left
-    int fslot;       // the slot this iteration's selection fills (set by the host per iteration)
+    int fslot;       // the slot this iteration's selection fills (t % FIN_SLOTS, kept by the merge)
     int mslots;      // bit s: the finish of slot s is done, merge its signals this iteration
+                     // (set by the host through k_set_merge, cleared by the merge)
     int apg_n;       // signals in the master-problem list (grow + failed finishes)
     int apg_head;    // work-queue head of the persistent master-problem kernel
     int apg_head2;   // head of its second queue (blocks streamed from global memory)
@@ -232,10 +233,13 @@ cudaError_t launch_gram_gather(const Dev& d, int ub, cudaStream_t s, int64_t* nl
 // number of finishing signals, est estimates it; when est is small against the sms SMs a
 // signal's finish runs on a cluster of up to FIN_CLUSTER_MAX CTAs.
 constexpr int FIN_CLUSTER_MAX = 8;
+constexpr int FIN_CLUSTER_MIN_N = 2048;
 cudaError_t launch_finish(const Dev& d, int slot, int ub, int est, int scap, cudaStream_t s, int64_t* nl, int sms);
+// Set the device counter mslots (the finished slots the next merge takes back).
+cudaError_t launch_set_merge(const Dev& d, int mask, cudaStream_t s, int64_t* nl);
 // Append reent[s] of every slot s in the device counter mslots to the active list of an
 // iteration with parity cur (rows for the GEMM included); the finishes that filled those
-// slots must be complete.
+// slots must be complete.  Advances the finish list slot to the one of this iteration.
 cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl);
 // Master-problem launches: every signal of the work list, or only those whose Gram block fits
 // shared memory, or only those streamed from global memory.

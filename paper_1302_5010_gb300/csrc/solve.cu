@@ -1341,6 +1341,8 @@ __global__ void __launch_bounds__(256) k_merge(Dev d, int cur) {
     }
 }
 
+// Also advances the finish list slot of the selection that follows (t % FIN_SLOTS for outer
+// iteration t; k_init starts it at 0) and clears the merge mask the host set.
 __global__ void k_merge_count(Dev d, int cur) {
     pdl_enter();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1350,7 +1352,22 @@ __global__ void k_merge_count(Dev d, int cur) {
             d.cnt->act_n[cur] += d.cnt->reent_n[q];
             d.cnt->reent_n[q] = 0;
         }
+        d.cnt->mslots = 0;
+        d.cnt->fslot = (d.cnt->fslot + 1) % FIN_SLOTS;
     }
+}
+
+// The finishes whose signals the next merge takes back (bit s: list slot s), from the host.
+__global__ void k_set_merge(Dev d, int mask) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) d.cnt->mslots = mask;
+}
+
+cudaError_t launch_set_merge(const Dev& d, int mask, cudaStream_t s, int64_t* nl) {
+    const cudaError_t e = launch_chain(k_set_merge, dim3(1), dim3(32), 0, s, d, mask);
+    if (e != cudaSuccess) return e;
+    ++*nl;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const Dev& d, int cur, int ub, cudaStream_t s, int64_t* nl) {

@@ -47,6 +47,7 @@ MPL_OPT_STOP_R2 = 16
 MPL_OPT_STOP_EPS = 17
 MPL_OPT_QGRAM = 18
 MPL_OPT_GEMM_TILE = 19
+MPL_OPT_REENTRY = 20
 MPL_PROPOSAL_NPARAM = 4487
 
 # limits of the allocation-free entry point (include/mpl.h)
@@ -317,7 +318,8 @@ class Solver:
                     sync_every=MPL_OPT_SYNC_EVERY, graph=MPL_OPT_GRAPH, warm_candidates=MPL_OPT_WARM_CANDIDATES,
                     warm_max=MPL_OPT_WARM_MAX, warm_threshold=MPL_OPT_WARM_THRESHOLD, qroute=MPL_OPT_QROUTE,
                     omega=MPL_OPT_OMEGA, stop_rinf=MPL_OPT_STOP_RINF, stop_r2=MPL_OPT_STOP_R2,
-                    stop_eps=MPL_OPT_STOP_EPS, qgram=MPL_OPT_QGRAM, gemm_tile=MPL_OPT_GEMM_TILE)
+                    stop_eps=MPL_OPT_STOP_EPS, qgram=MPL_OPT_QGRAM, gemm_tile=MPL_OPT_GEMM_TILE,
+                    reentry=MPL_OPT_REENTRY)
         for k, v in opts.items():
             mpl_set_option(self.h, keys[k], v)
 

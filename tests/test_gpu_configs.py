@@ -50,8 +50,8 @@ def test_large_dictionary_mixed_equals_plain(cfg, p, smax):
     signals are selected again from FP32 correlations in the same iteration, so
     the mixed path still picks exactly the plain path's atoms."""
     P = synth.make_config(cfg, p=p)
-    Xp, _, rp = solve_gpu(P, precision=0, smax=smax)
-    Xm, _, rm = solve_gpu(P, precision=1, smax=smax)
+    Xp, _, rp = solve_gpu(P, precision=0, smax=smax, reentry=1)
+    Xm, _, rm = solve_gpu(P, precision=1, smax=smax, reentry=1)
     assert_certified(rp)
     assert_certified(rm)
     np.testing.assert_array_equal(rp.stats["outer_iters"], rm.stats["outer_iters"])

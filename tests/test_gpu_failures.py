@@ -26,7 +26,7 @@ def test_nan_column_isolated(precision):
     B = P.B.copy()
     B[bad, 17] = np.nan
     Q = synth.Problem("nan", P.At, B, P.lam.copy(), P.rho)
-    X, X64, res = solve_gpu(Q, precision=precision)
+    X, X64, res = solve_gpu(Q, precision=precision, reentry=1)
     st = res.stats
     assert res.status == mpl.MPL_ERR_NOT_CONVERGED
     assert st["status"][bad] == mpl.MPL_SIG_NONFINITE
@@ -36,7 +36,7 @@ def test_nan_column_isolated(precision):
     assert np.all(X[bad] == 0)
     # the clean batch without the poisoned column gives the same solutions, bit for bit
     Pc = P.subset(others)
-    Xc, _, rc = solve_gpu(Pc, precision=precision)
+    Xc, _, rc = solve_gpu(Pc, precision=precision, reentry=1)
     assert_certified(rc)
     np.testing.assert_array_equal(X[others], Xc)
 

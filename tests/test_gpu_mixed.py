@@ -32,8 +32,9 @@ def test_mixed_ragged(n, m, p, rho):
 
 def test_mixed_identical_to_plain_c2():
     P = synth.make_config("c2", p=96)
-    Xp, X64p, rp = solve_gpu(P, precision=0)
-    Xm, X64m, rm = solve_gpu(P, precision=1)
+    # (bit-for-bit comparisons run with the fixed re-entry of MPL_OPT_REENTRY = 1)
+    Xp, X64p, rp = solve_gpu(P, precision=0, reentry=1)
+    Xm, X64m, rm = solve_gpu(P, precision=1, reentry=1)
     assert_certified(rp)
     assert_certified(rm)
     np.testing.assert_array_equal(rp.stats["outer_iters"], rm.stats["outer_iters"])
@@ -53,7 +54,7 @@ def test_gemm_tile_does_not_change_the_solution(bn):
     B, lam = torch.from_numpy(P.B).cuda(), torch.from_numpy(P.lam).cuda()
     out = []
     for tile in (128, bn):
-        s = mpl.Solver(At, rho=P.rho, precision=1, smax=512, gemm_tile=tile)
+        s = mpl.Solver(At, rho=P.rho, precision=1, smax=512, gemm_tile=tile, reentry=1)
         X = torch.empty((P.p, P.m), device="cuda")
         r = s.solve(B, lam, X)
         torch.cuda.synchronize()

@@ -145,17 +145,40 @@ def test_orthonormal_closed_form():
 
 def test_host_buffers_match_device_buffers():
     P = synth.small_problem(256, 1024, 10, 5, 20, rho=5, seed=11)
-    Xd, X64d, _ = solve_gpu(P)
-    Xh, X64h, resh = solve_gpu(P, host=True)
+    Xd, X64d, _ = solve_gpu(P, reentry=1)
+    Xh, X64h, resh = solve_gpu(P, host=True, reentry=1)
     assert_certified(resh)
     np.testing.assert_array_equal(Xd, Xh)
 
 
 def test_deterministic_repeat():
     P = synth.small_problem(256, 2048, 20, 10, 30, rho=6, seed=12)
-    X1, _, _ = solve_gpu(P)
-    X2, _, _ = solve_gpu(P)
+    # MPL_OPT_REENTRY = 1: the same bits on every run (the default re-entry may differ in
+    # the last bits from run to run, certified either way)
+    X1, _, _ = solve_gpu(P, reentry=1)
+    X2, _, _ = solve_gpu(P, reentry=1)
     np.testing.assert_array_equal(X1, X2)
+
+
+def test_reentry_modes_agree():
+    """Re-entry as soon as a signal's finish is done (the default) and exactly two outer
+    iterations later (MPL_OPT_REENTRY = 1) both certify every signal, with the same outer
+    iteration counts, and their solutions agree to the certificate's accuracy."""
+    P = synth.make_config("c2", p=64)
+    X0, X64_0, r0 = solve_gpu(P, precision=1)
+    X1, X64_1, r1 = solve_gpu(P, precision=1, reentry=1)
+    assert_certified(r0)
+    assert_certified(r1)
+    np.testing.assert_array_equal(r0.stats["outer_iters"], r1.stats["outer_iters"])
+    np.testing.assert_allclose(X64_0, X64_1, rtol=0, atol=1e-9 * np.abs(X64_1).max())
+    idx = np.arange(0, P.p, 8)
+    check_against_oracle(P, X64_0[idx], oracle_solve(P, idx), idx)
+    torch = _torch()
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho)
+    assert mpl.mpl_get_option(s.h, mpl.MPL_OPT_REENTRY) == 0
+    with pytest.raises(mpl.MplError):
+        s.set(mpl.MPL_OPT_REENTRY, 2)
+    s.close()
 
 
 def test_empty_batch_and_bad_lambda():
@@ -179,9 +202,9 @@ def test_graph_replay_matches_direct_launches():
     """Captured-and-replayed outer iterations give the same solutions as
     direct launches (first solve captures, second replays)."""
     P = synth.make_config("c2", p=40)
-    Xd, X64d, rd = solve_gpu(P, graph=0)
+    Xd, X64d, rd = solve_gpu(P, graph=0, reentry=1)
     torch = _torch()
-    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, graph=1)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, graph=1, reentry=1)
     B = torch.from_numpy(P.B).cuda()
     lam = torch.from_numpy(P.lam).cuda()
     for _ in range(3):

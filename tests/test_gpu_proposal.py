@@ -105,6 +105,7 @@ def test_warm_start_plain_and_mixed_identical():
     out = []
     for s in (s0, s1):
         s.set(mpl.MPL_OPT_WARM_START, 2)
+        s.set(mpl.MPL_OPT_REENTRY, 1)
         X = torch.zeros((P.p, P.m), device="cuda")
         r = s.solve(B, lam, X, TOL)
         assert_certified(r)

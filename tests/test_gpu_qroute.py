@@ -36,8 +36,8 @@ def _qcols(P, precision, qroute, **opts):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_identity_route_matches_gemm_route_c2(precision):
     P = synth.make_config("c2", p=64)
-    Xg, X64g, rg = solve_gpu(P, precision=precision)
-    Xq, X64q, rq = solve_gpu(P, precision=precision, qroute=1024)
+    Xg, X64g, rg = solve_gpu(P, precision=precision, reentry=1)
+    Xq, X64q, rq = solve_gpu(P, precision=precision, qroute=1024, reentry=1)
     assert_certified(rg)
     assert_certified(rq)
     np.testing.assert_array_equal(rg.stats["outer_iters"], rq.stats["outer_iters"])
@@ -50,8 +50,8 @@ def test_identity_route_matches_gemm_route_c2(precision):
 
 def test_identity_route_first_iterations_only():
     P = synth.make_config("c2", p=48)
-    Xg, _, rg = solve_gpu(P, precision=1)
-    Xq, _, rq = solve_gpu(P, precision=1, qroute=2 * P.rho)  # iterations 1 and 2 only
+    Xg, _, rg = solve_gpu(P, precision=1, reentry=1)
+    Xq, _, rq = solve_gpu(P, precision=1, qroute=2 * P.rho, reentry=1)  # iterations 1 and 2 only
     assert_certified(rq)
     np.testing.assert_array_equal(Xg, Xq)
     qc, cc = _qcols(P, 1, 2 * P.rho)
@@ -62,10 +62,10 @@ def test_identity_route_first_iterations_only():
 def test_identity_route_ragged_against_oracle(n, m, p, rho):
     """m % 4 != 0 takes the scalar path of the route; n % 4 != 0 the scalar GEMM."""
     P = synth.small_problem(n, m, p, 4, min(30, n // 6), rho=rho, seed=n + 7 * m + p, lam_frac=0.03)
-    X, X64, res = solve_gpu(P, precision=0, qroute=1024)
+    X, X64, res = solve_gpu(P, precision=0, qroute=1024, reentry=1)
     assert_certified(res)
     check_against_oracle(P, X64, oracle_solve(P))
-    Xg, _, _ = solve_gpu(P, precision=0)
+    Xg, _, _ = solve_gpu(P, precision=0, reentry=1)
     np.testing.assert_array_equal(X, Xg)
 
 
@@ -74,7 +74,7 @@ def test_identity_route_warm_start():
     import torch
     P = synth.make_config("c2", p=32)
     Pt = synth.make_config("c2", p=1024, seed_shift=9000)
-    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1, reentry=1)
     Xt = torch.empty((Pt.p, Pt.m), device="cuda")
     s.solve(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt)
     s.train_proposal(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt, epochs=2)
@@ -95,8 +95,8 @@ def test_identity_route_warm_start():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_gram_from_q_is_bit_identical_c2(precision):
     P = synth.make_config("c2", p=64)
-    Xg, X64g, rg = solve_gpu(P, precision=precision)
-    Xq, X64q, rq = solve_gpu(P, precision=precision, qgram=1)
+    Xg, X64g, rg = solve_gpu(P, precision=precision, reentry=1)
+    Xq, X64q, rq = solve_gpu(P, precision=precision, qgram=1, reentry=1)
     assert_certified(rq)
     for k in ("outer_iters", "inner_iters", "active_size", "finishes"):
         np.testing.assert_array_equal(rg.stats[k], rq.stats[k])
@@ -109,8 +109,8 @@ def test_gram_from_q_ragged(n, m, p, rho, omega):
     """n % 4 != 0: the scalar Gram kernel and the scalar h chain; n % 16 != 0:
     the vector chain's ragged tail; omega > 1: Algorithm 2's explored atoms."""
     P = synth.small_problem(n, m, p, 4, min(30, n // 6), rho=rho, seed=3 * n + m + p, lam_frac=0.03)
-    Xg, _, _ = solve_gpu(P, precision=0, omega=omega)
-    X, X64, res = solve_gpu(P, precision=0, omega=omega, qgram=1)
+    Xg, _, _ = solve_gpu(P, precision=0, omega=omega, reentry=1)
+    X, X64, res = solve_gpu(P, precision=0, omega=omega, qgram=1, reentry=1)
     assert_certified(res)
     np.testing.assert_array_equal(X, Xg)
     check_against_oracle(P, X64, oracle_solve(P))
@@ -120,7 +120,7 @@ def test_gram_from_q_with_identity_route_and_warm_start():
     import torch
     P = synth.make_config("c2", p=32)
     Pt = synth.make_config("c2", p=1024, seed_shift=9000)
-    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1, reentry=1)
     Xt = torch.empty((Pt.p, Pt.m), device="cuda")
     s.solve(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt)
     s.train_proposal(torch.from_numpy(Pt.B).cuda(), torch.from_numpy(Pt.lam).cuda(), Xt, epochs=2)
@@ -141,7 +141,7 @@ def test_gram_from_q_with_identity_route_and_warm_start():
 def test_autotune_keeps_the_solution():
     import torch
     P = synth.make_config("c2", p=64)
-    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1)
+    s = mpl.Solver(torch.from_numpy(P.At).cuda(), rho=P.rho, precision=1, reentry=1)
     B, lam = torch.from_numpy(P.B).cuda(), torch.from_numpy(P.lam).cuda()
     X0 = torch.empty((P.p, P.m), device="cuda")
     s.solve(B, lam, X0)

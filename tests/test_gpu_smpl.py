@@ -22,8 +22,8 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("omega", [2, 3])
 def test_smpl_c2_subset(omega):
     P = synth.make_config("c2", p=64)
-    Xp, X64p, rp = solve_gpu(P, precision=0, omega=omega)
-    Xm, X64m, rm = solve_gpu(P, precision=1, omega=omega)
+    Xp, X64p, rp = solve_gpu(P, precision=0, omega=omega, reentry=1)
+    Xm, X64m, rm = solve_gpu(P, precision=1, omega=omega, reentry=1)
     assert_certified(rp)
     assert_certified(rm)
     # the re-score decides selection in both precisions: identical paths
