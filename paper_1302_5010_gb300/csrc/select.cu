@@ -742,6 +742,13 @@ template <bool CHUNKED>
 __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, const PropArgs& pa, int route) {
     const int kblk = blockIdx.x;
     if (kblk >= d.cnt->act_n[cur]) return;
+    // the chunk maxima's non-finite flag of this position, read and cleared before any
+    // return, so that it cannot reach the signal the position holds next iteration
+    int nf_flag = 0;
+    if (CHUNKED && threadIdx.x == 0) {
+        nf_flag = d.sel_nf[kblk];
+        if (nf_flag) d.sel_nf[kblk] = 0;
+    }
     const int i = d.act[cur][kblk];
     const int st0 = d.state[i];
     if (st0 == ST_DONE || st0 == ST_REFINE) return;  // no worst-case analysis this iteration
@@ -797,10 +804,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
         unsigned kkey = 0, tlo = 0, below = 0;
         // (chunked: the row's chunk maxima are in d.sel_tmax; they describe the first attempt's scores)
         const int nch = (m + SEL_CHUNK - 1) / SEL_CHUNK;
-        if (CHUNKED && attempt == 0 && !cache && tid == 0 && d.sel_nf[kblk]) {
-            sh.nonfinite = 1;
-            d.sel_nf[kblk] = 0;  // (k_sel_maxima of the next iteration runs after this kernel)
-        }
+        if (CHUNKED && attempt == 0 && !cache && tid == 0 && nf_flag) sh.nonfinite = 1;
         bool listed = false;
         if (cache) {
             listed = fast_kth(ck.k, m, kth, tmax, sh, &kkey, &tlo, &below);

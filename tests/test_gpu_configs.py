@@ -21,6 +21,26 @@ def test_face_dictionary_subset():
     check_against_oracle(P, X64, oracle_solve(P))
 
 
+def test_face_dictionary_batch_all_certified_repeatedly():
+    """The default re-entry hands finished signals back one by one while other finishes still
+    run; on the face-shaped batch (many finishes, ill-conditioned blocks, failed finishes that
+    rejoin) every signal of every one of several solves ends certified, with handshakes every
+    iteration and every four."""
+    import torch
+    from paper_1302_5010_gb300 import mpl
+    P = synth.make_config("c4", p=1024)
+    At = torch.from_numpy(P.At).cuda()
+    B, lam = torch.from_numpy(P.B).cuda(), torch.from_numpy(P.lam).cuda()
+    for sync in (1, 4):
+        s = mpl.Solver(At, rho=P.rho, precision=1, smax=512, qgram=1, sync_every=sync)
+        X = torch.empty((P.p, P.m), device="cuda")
+        for _ in range(3):
+            r = s.solve(B, lam, X)
+            torch.cuda.synchronize()
+            assert_certified(r)
+        s.close()
+
+
 def test_c5_shape_mixed_subset():
     P = synth.make_config("c5", p=12)
     X, X64, res = solve_gpu(P, precision=1, smax=512)

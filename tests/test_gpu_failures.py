@@ -41,6 +41,29 @@ def test_nan_column_isolated(precision):
     np.testing.assert_array_equal(X[others], Xc)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nan_column_isolated_long_score_rows(precision):
+    """Score rows above the shared-memory row cache (2048 x 32768): the chunk maxima flag the
+    poisoned signal's non-finite scores; the flag stays with that signal, whose selection
+    stops at once, and does not reach the signal that takes its place in the next
+    iteration's active list."""
+    P = synth.make_config("c5", p=24)
+    bad = 3
+    B = P.B.copy()
+    B[bad, 11] = np.nan
+    Q = synth.Problem("nan-c5", P.At, B, P.lam.copy(), P.rho)
+    X, X64, res = solve_gpu(Q, precision=precision, smax=512, reentry=1)
+    st = res.stats
+    assert res.status == mpl.MPL_ERR_NOT_CONVERGED
+    assert st["status"][bad] == mpl.MPL_SIG_NONFINITE
+    others = np.array([i for i in range(P.p) if i != bad])
+    assert np.all(st["status"][others] == mpl.MPL_SIG_CERTIFIED), st["status"]
+    assert np.all(X[bad] == 0)
+    Xc, _, rc = solve_gpu(P.subset(others), precision=precision, smax=512, reentry=1)
+    assert_certified(rc)
+    np.testing.assert_array_equal(X[others], Xc)
+
+
 def test_nan_lambda_and_inf_signal():
     P = synth.small_problem(256, 1024, 6, 5, 12, rho=4, seed=31, lam_frac=0.03)
     B = P.B.copy()
