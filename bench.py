@@ -485,7 +485,7 @@ def solve_once(args):
     B = torch.from_numpy(P.B).to(dev)
     lam = torch.from_numpy(P.lam).to(dev)
     opts = dict(qgram=args.solve_qgram, graph=args.solve_graph, sync_every=args.solve_sync,
-                qroute=args.solve_qroute, reentry=args.solve_reentry)
+                qroute=args.solve_qroute, reentry=args.solve_reentry, omega=args.solve_omega)
     if SMAX.get(args.solve_once):
         opts["smax"] = SMAX[args.solve_once]
     if args.path == "mixed":
@@ -499,6 +499,10 @@ def solve_once(args):
         before += s.launches()
     r = s.solve(B, lam, X, TOL)
     torch.cuda.synchronize()
+    if args.solve_train > 0:
+        # the warm start's proposal network trained on the solved batch (its training kernels)
+        s.train_proposal(B, lam, X, epochs=args.solve_train)
+        torch.cuda.synchronize()
     print(json.dumps({"solve_once": args.solve_once, "p": P.p, "path": args.path, "options": opts,
                       "launches_before": before, "launches": s.launches(),
                       "certified": int(np.sum(r.stats["status"] == mpl.MPL_SIG_CERTIFIED))}), flush=True)
@@ -723,6 +727,9 @@ def main():
     ap.add_argument("--solve-graph", type=int, default=1)
     ap.add_argument("--solve-sync", type=int, default=4)
     ap.add_argument("--solve-qroute", type=int, default=0, help="identity route bound of the --solve-once run")
+    ap.add_argument("--solve-omega", type=int, default=1, help="Algorithm 2's omega of the --solve-once run")
+    ap.add_argument("--solve-train", type=int, default=0, metavar="EPOCHS",
+                    help="after the --solve-once solve, train the proposal network on it for this many epochs")
     ap.add_argument("--solve-reentry", type=int, default=0, choices=[0, 1],
                     help="MPL_OPT_REENTRY of the --solve-once run (1: the same launches on every run, e.g. "
                          "for a launch list whose skip count comes from a run without the profiler)")
