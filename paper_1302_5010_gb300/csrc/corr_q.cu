@@ -145,12 +145,10 @@ __global__ void k_gram_q_prep(Counters* cnt, int* act, int m) {
 
 // Gram growth from Q (Sec. 3: Q = A^T A is precomputed off-line, and the master
 // problem's Gram block G_SS is its S x S sub-block).  For each growing signal
-// the new columns of G_SS are copied out of Q, and h = A_S^T b gets its new
-// entries.  Q was built by the FP32 GEMM with one FMA chain per entry over k
-// ascending, the order of the computed Gram block, and h here is the same kind
-// of chain (a_k b_k, k ascending, from 0), so G and h are the same bits as
-// launch_gram's.
-constexpr int GQ_BUF = 10240;  // floats of the staging buffer for the h chains
+// the new columns of G_SS are copied out of Q (the new entries of h = A_S^T b
+// come with the selection's re-score).  Q was built by the FP32 GEMM with one
+// FMA chain per entry over k ascending, the order of the computed Gram block, so
+// G is the same bits as launch_gram's.
 
 __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     pdl_enter();
@@ -159,13 +157,14 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     const int i = d.list_grow[g];
     const int s = d.ssize[i], q = d.snew[i], s0 = s - q;
     if (q == 0) return;  // a refine pass: the block is complete
-    const int n = d.n, m = d.m, smax = d.smax;
+    const int m = d.m, smax = d.smax;
     const int* Si = d.S + (size_t)i * smax;
     float* Gi = d.G + (size_t)i * smax * smax;
     __shared__ int sidx[1024];  // smax <= 1024
-    __shared__ __align__(16) float hbuf[GQ_BUF];
-    if (threadIdx.x == 0)  // s q entries of Q read, 2 s q of G written, q atoms and b read, q of h written
-        atomicAdd(&d.cnt->gram_bytes, 12ull * s * q + 4ull * n * (q + 1) + 4ull * q);
+    constexpr int GT_A = 32, GT_C = 64;
+    __shared__ float gt[GT_C][GT_A + 1];
+    if (threadIdx.x == 0)  // s q entries of Q read, 2 s q of G written
+        atomicAdd(&d.cnt->gram_bytes, 12ull * s * q);
     if (MPL_OOB(s > smax || s > 1024 || q > s, 401)) return;
     for (int a = threadIdx.x; a < s; a += blockDim.x) sidx[a] = Si[a];
     __syncthreads();
@@ -173,9 +172,6 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
     // atoms: eight independent Q reads per thread in flight (scattered either way), the new
     // rows G[s0 + c][a] written along a, then through a shared-memory tile the new columns
     // G[a][s0 + c] written along c, so that both halves are stored in whole sectors
-    constexpr int GT_A = 32, GT_C = 64;
-    static_assert(GT_C * (GT_A + 1) <= GQ_BUF, "the tile lives in the staging buffer of h");
-    float (*gt)[GT_A + 1] = reinterpret_cast<float (*)[GT_A + 1]>(hbuf);  // (h's staging comes after)
     const int ta = threadIdx.x & (GT_A - 1), tc = threadIdx.x >> 5;  // 256 threads: tc < 8
     for (int a0 = 0; a0 < s; a0 += GT_A) {
         for (int c0 = 0; c0 < q; c0 += GT_C) {
@@ -206,72 +202,6 @@ __global__ void __launch_bounds__(256) k_gram_gather(Dev d) {
             }
             __syncthreads();
         }
-    }
-    // h of the new atoms, one FMA chain per atom (thread), over k ascending.  The
-    // atoms' columns and b pass through shared memory kc entries at a time (coalesced
-    // loads by the whole block), so the chains wait on shared memory, not on L2.
-    const float* b = d.B + (size_t)i * n;
-    const bool vec = (n & 3) == 0;
-    for (int c0 = 0; c0 < q; c0 += 256) {
-        const int qg = min(256, q - c0);
-        const int kc = (GQ_BUF / (qg + 1) - 4) & ~31;  // >= 32
-        const int ks = kc + 4;  // = 4 (mod 32): a row per thread, float4 reads conflict-free
-        const int c = threadIdx.x;
-        float acc = 0.f;
-        for (int k0 = 0; k0 < n; k0 += kc) {
-            const int kw = min(kc, n - k0);
-            __syncthreads();  // the previous chunk is consumed
-            if (vec) {
-                // eight float4 loads per thread in flight before their stores
-                const int v4 = kw >> 2, tot = (qg + 1) * v4;
-                for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * blockDim.x) {
-                    float4 v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int e = e0 + u * blockDim.x;
-                        if (e < tot) {
-                            const int r = e / v4, k4 = e - r * v4;
-                            const float* src = (r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b) + k0 + 4 * k4;
-                            v[u] = __ldg(reinterpret_cast<const float4*>(src));
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int e = e0 + u * blockDim.x;
-                        if (e < tot) {
-                            const int r = e / v4, k4 = e - r * v4;
-                            if (MPL_OOB(r * ks + 4 * k4 + 3 >= GQ_BUF, 402)) continue;
-                            *reinterpret_cast<float4*>(hbuf + r * ks + 4 * k4) = v[u];
-                        }
-                    }
-                }
-            } else {
-                for (int e = threadIdx.x; e < (qg + 1) * kw; e += blockDim.x) {
-                    const int r = e / kw, k = e - r * kw;
-                    const float* src = r < qg ? d.A32 + (size_t)sidx[s0 + c0 + r] * n : b;
-                    hbuf[r * ks + k] = __ldg(src + k0 + k);
-                }
-            }
-            __syncthreads();
-            if (c < qg) {
-                const float* ar = hbuf + c * ks;
-                const float* br = hbuf + qg * ks;
-                if (vec) {
-#pragma unroll 4
-                    for (int k = 0; k < kw; k += 4) {
-                        const float4 a4 = *reinterpret_cast<const float4*>(ar + k);
-                        const float4 b4 = *reinterpret_cast<const float4*>(br + k);
-                        acc = fmaf(a4.x, b4.x, acc);
-                        acc = fmaf(a4.y, b4.y, acc);
-                        acc = fmaf(a4.z, b4.z, acc);
-                        acc = fmaf(a4.w, b4.w, acc);
-                    }
-                } else {
-                    for (int k = 0; k < kw; ++k) acc = fmaf(ar[k], br[k], acc);
-                }
-            }
-        }
-        if (c < qg) d.h[(size_t)i * smax + s0 + c0 + c] = acc;
     }
 }
 

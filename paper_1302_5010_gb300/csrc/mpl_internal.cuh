@@ -122,7 +122,7 @@ struct Dev {
     float* xS;                   // p x smax FP32 master-problem iterate
     double* xS64;                // p x smax FP64 finished solution
     float* G;                    // p x smax x smax Gram blocks A_S^T A_S (ld = smax)
-    float* h;                    // p x smax A_S^T b
+    float* h;                    // p x smax A_S^T b (an entry per atom, from the selection's re-score)
     float* ritz;                 // p x smax power-iteration vector (warm start of L)
     double* chol;                // p x smax x smax FP64 workspace (large supports)
     double* fin_pool;            // FIN_SLOTS x fin_slots more such workspaces: one per CTA of a
@@ -224,6 +224,8 @@ cudaError_t launch_save_beta(const Dev& d, int cur, int act_n_ub, cudaStream_t s
 cudaError_t build_gram_q(const float* A32, int n, int m, float* Q, int* act, Counters* cnt, cudaStream_t s,
                          int64_t* nl);
 cudaError_t launch_compact(const Dev& d, int cur, cudaStream_t s, int64_t* nl);
+// The new rows and columns of each growing signal's Gram block (h of the new atoms was
+// written by the selection that appended them).
 // qmax: most atoms a signal can take this iteration (picks the tile width).
 cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t* nl);
 // Gram growth gathered from Q (MPL_OPT_QGRAM): same outputs, bit for bit, as launch_gram.

@@ -18,6 +18,10 @@
 // the FP64 residual of an exact finish, candidates whose re-score is within its
 // own bound of lambda(1+tol) are scored once more in FP64: this certifies the
 // off-support half of the KKT conditions (eq. 8).
+//
+// The re-score also forms a_j^T b for every candidate, with the same loads and in the same
+// summation order; an atom that joins S takes it as its entry of h = A_S^T b, the linear term
+// of the master problem, so the Gram growth that follows reads no atom column for h.
 #include "mpl_internal.cuh"
 
 namespace mpl {
@@ -70,26 +74,80 @@ __device__ __forceinline__ float warp_dot_f32(const float* __restrict__ a, const
     return acc;
 }
 
-// Two fixed-order FP32 dots by one warp, sharing the loads of r (each in the
-// order of warp_dot_f32, so both equal what warp_dot_f32 returns).  n % 4 == 0.
-__device__ __forceinline__ void warp_dot2_f32(const float* __restrict__ a0, const float* __restrict__ a1,
-                                              const float* __restrict__ r, int n, int lane, float* c0, float* c1) {
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
-    for (int k = lane * 4; k < n; k += 128) {
-        const float4 rv = __ldg(reinterpret_cast<const float4*>(r + k));
-        const float4 u = __ldg(reinterpret_cast<const float4*>(a0 + k));
-        const float4 v = __ldg(reinterpret_cast<const float4*>(a1 + k));
-        s0 = fmaf(u.x, rv.x, s0); s0 = fmaf(u.y, rv.y, s0); s0 = fmaf(u.z, rv.z, s0); s0 = fmaf(u.w, rv.w, s0);
-        s1 = fmaf(v.x, rv.x, s1); s1 = fmaf(v.y, rv.y, s1); s1 = fmaf(v.z, rv.z, s1); s1 = fmaf(v.w, rv.w, s1);
+// The re-score of two candidates: for each atom a, a^T r and a^T b as warp_dot_f32 computes
+// them (the same products summed in the same order), sharing the atoms' loads; r and b come
+// from shared memory when staged there.  Each step issues RS_U loads of both columns before
+// its products.  n % 4 == 0.
+constexpr int RS_U = 4;
+__device__ __forceinline__ void warp_dot2h_f32(const float* __restrict__ a0, const float* __restrict__ a1,
+                                               const float* r, const float* b, int n, int lane, float* c0,
+                                               float* c1, float* h0, float* h1) {
+    float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+    for (int kb = lane * 4; kb < n; kb += 128 * RS_U) {
+        float4 u[RS_U], v[RS_U];
+#pragma unroll
+        for (int e = 0; e < RS_U; ++e) {
+            const int k = kb + 128 * e;
+            u[e] = k < n ? __ldg(reinterpret_cast<const float4*>(a0 + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[e] = k < n ? __ldg(reinterpret_cast<const float4*>(a1 + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int e = 0; e < RS_U; ++e) {
+            const int k = kb + 128 * e;
+            if (k < n) {
+                const float4 rv = *reinterpret_cast<const float4*>(r + k);
+                const float4 bv = *reinterpret_cast<const float4*>(b + k);
+                s0 = fmaf(u[e].x, rv.x, s0); s0 = fmaf(u[e].y, rv.y, s0);
+                s0 = fmaf(u[e].z, rv.z, s0); s0 = fmaf(u[e].w, rv.w, s0);
+                s1 = fmaf(v[e].x, rv.x, s1); s1 = fmaf(v[e].y, rv.y, s1);
+                s1 = fmaf(v[e].z, rv.z, s1); s1 = fmaf(v[e].w, rv.w, s1);
+                t0 = fmaf(u[e].x, bv.x, t0); t0 = fmaf(u[e].y, bv.y, t0);
+                t0 = fmaf(u[e].z, bv.z, t0); t0 = fmaf(u[e].w, bv.w, t0);
+                t1 = fmaf(v[e].x, bv.x, t1); t1 = fmaf(v[e].y, bv.y, t1);
+                t1 = fmaf(v[e].z, bv.z, t1); t1 = fmaf(v[e].w, bv.w, t1);
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
     }
     *c0 = s0;
     *c1 = s1;
+    *h0 = t0;
+    *h1 = t1;
+}
+
+// One candidate: a^T r and a^T b, each in the order of warp_dot_f32.
+__device__ __forceinline__ void warp_doth_f32(const float* __restrict__ a, const float* r, const float* b, int n,
+                                              int lane, float* c, float* h) {
+    float s = 0.f, t = 0.f;
+    if ((n & 3) == 0) {
+#pragma unroll 4
+        for (int k = lane * 4; k < n; k += 128) {
+            const float4 av = __ldg(reinterpret_cast<const float4*>(a + k));
+            const float4 rv = *reinterpret_cast<const float4*>(r + k);
+            const float4 bv = *reinterpret_cast<const float4*>(b + k);
+            s = fmaf(av.x, rv.x, s); s = fmaf(av.y, rv.y, s); s = fmaf(av.z, rv.z, s); s = fmaf(av.w, rv.w, s);
+            t = fmaf(av.x, bv.x, t); t = fmaf(av.y, bv.y, t); t = fmaf(av.z, bv.z, t); t = fmaf(av.w, bv.w, t);
+        }
+    } else {
+        for (int k = lane; k < n; k += 32) {
+            const float av = __ldg(a + k);
+            s = fmaf(av, r[k], s);
+            t = fmaf(av, b[k], t);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    *c = s;
+    *h = t;
 }
 
 __device__ __forceinline__ double warp_dot_f64(const float* __restrict__ a, const double* __restrict__ r,
@@ -108,6 +166,7 @@ struct SelSmem {
     unsigned long long key[SEL_KCAP];  // sort keys of the violators
     int idx[SEL_KCAP];                 // candidate atoms
     float sc[SEL_KCAP];                // their re-scores, negated for non-violators
+    float hb[SEL_KCAP];                // their a^T b (the master problem's h when they join S)
     float row[SEL_ROWCACHE];           // selection keys of the signal's scores (when m fits): the
                                        // bits of |c_j|, 0 for members of S and non-finite scores
     unsigned wsum[32];                 // per-warp partial sums of the histogram scan
@@ -118,6 +177,7 @@ struct SelSmem {
     unsigned outmax;                   // largest key outside K
     float offmax;                      // largest certified bound inside K
     int nonfinite;
+    int qsel;                          // atoms appended to S by this selection
 };
 
 // Key of atom j: the IEEE bits of |score| (monotone for non-negative floats);
@@ -764,6 +824,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     float* row = d.Cs + (size_t)kblk * m;
     const uint32_t* msk = d.mask + (size_t)i * d.mw;
     const float* r32 = d.R32 + (size_t)i * n;
+    const float* b32 = d.B + (size_t)i * n;
     const double* r64 = d.R64 + (size_t)i * n;
     const int fin = d.finalized[i];
     const float lam = d.lam[i];
@@ -856,20 +917,32 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     if (threadIdx.x == 0 && i < 8192) g_sel_trace[i][15] = kc;
 #endif
 
-    // Re-score the candidates (one warp each) and mark the violators.
+    // Re-score the candidates (one warp each) and mark the violators.  The residual is staged
+    // in the row cache's space (free once the band is collected) when it fits.
+    const bool rstage = (n & 3) == 0 && n <= SEL_ROWCACHE && kc > 0;
+    const bool bstage = rstage && 2 * n <= SEL_ROWCACHE;
+    const float* rsm = rstage ? reinterpret_cast<const float*>(sh.row) : r32;
+    const float* bsm = bstage ? reinterpret_cast<const float*>(sh.row) + n : b32;
+    if (rstage) {
+        float* rw = reinterpret_cast<float*>(sh.row);
+        for (int k = tid * 4; k < n; k += 4 * (int)blockDim.x) {
+            *reinterpret_cast<float4*>(rw + k) = __ldg(reinterpret_cast<const float4*>(r32 + k));
+            if (bstage) *reinterpret_cast<float4*>(rw + n + k) = __ldg(reinterpret_cast<const float4*>(b32 + k));
+        }
+    }
     if (tid == 0) { sh.vc = 0; sh.offmax = 0.f; }
     __syncthreads();
     float offmax = 0.f;
     const bool pair = (n & 3) == 0;  // two candidates per warp, sharing the residual loads
     const unsigned cstep = pair ? 2u * nwarps : (unsigned)nwarps;
     for (unsigned c0 = pair ? 2u * warp : (unsigned)warp; c0 < kc; c0 += cstep) {
-      float dots[2];
+      float dots[2], hs[2];
       if (pair && c0 + 1 < kc) {
-          warp_dot2_f32(d.A32 + (size_t)sh.idx[c0] * n, d.A32 + (size_t)sh.idx[c0 + 1] * n, r32, n, lane,
-                        &dots[0], &dots[1]);
+          warp_dot2h_f32(d.A32 + (size_t)sh.idx[c0] * n, d.A32 + (size_t)sh.idx[c0 + 1] * n, rsm, bsm, n, lane,
+                         &dots[0], &dots[1], &hs[0], &hs[1]);
       } else {
-          dots[0] = warp_dot_f32(d.A32 + (size_t)sh.idx[c0] * n, r32, n, lane);
-          dots[1] = 0.f;
+          warp_doth_f32(d.A32 + (size_t)sh.idx[c0] * n, rsm, bsm, n, lane, &dots[0], &hs[0]);
+          dots[1] = hs[1] = 0.f;
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -887,7 +960,10 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             viol = c64 > lam_hi;
             certb = (float)(c64 * (1.0 + 1e-12));
         }
-        if (lane == 0) sh.sc[c] = viol ? score : -score;
+        if (lane == 0) {
+            sh.sc[c] = viol ? score : -score;
+            sh.hb[c] = hs[e];
+        }
         offmax = fmaxf(offmax, certb);
       }
     }
@@ -999,6 +1075,16 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
             if (d.explore) d.explore[i] = 0;
             d.state[i] = q > 0 ? ST_GROW : ST_FINALIZE;
             if (q > 0) d.finalized[i] = 0;
+            sh.qsel = q;
+        }
+        __syncthreads();
+        // h of the appended atoms (the order of the proposal's list is not the candidates')
+        const int qp = sh.qsel;
+        const int* Sp = d.S + (size_t)i * d.smax;
+        for (int a = warp; a < qp; a += nwarps) {
+            float c, h;
+            warp_doth_f32(d.A32 + (size_t)Sp[ss + a] * n, r32, b32, n, lane, &c, &h);
+            if (lane == 0) d.h[(size_t)i * d.smax + ss + a] = h;
         }
         return;
     }
@@ -1024,6 +1110,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
     ST_CNT(5);
     if (tid == 0) {
         d.outer[i] += 1;
+        sh.qsel = 0;
         if (sh.nonfinite) {
             d.sstatus[i] = MPL_SIG_NONFINITE;
             d.state[i] = ST_DONE;
@@ -1060,6 +1147,7 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
                 d.snew[i] = q;
                 d.finalized[i] = 0;
                 d.state[i] = ST_GROW;
+                sh.qsel = q;
             } else if (fin && stop1) {
                 // the current point is already the exact restricted solution
                 d.ginf[i] = fmax(d.ginf[i], offb);
@@ -1075,6 +1163,23 @@ __device__ __forceinline__ void select_body(const Dev& d, int cur, int no_grow, 
                 d.snew[i] = 0;
                 d.state[i] = ST_FINALIZE;
             }
+        }
+    }
+    __syncthreads();
+    // h of the appended atoms: a violator's rank among the sorted keys is its position after ss
+    const int qs = sh.qsel;
+    if (qs > 0) {
+        for (unsigned c = tid; c < kc; c += blockDim.x) {
+            if (!(sh.sc[c] > 0.f)) continue;
+            const unsigned long long kcand = ((unsigned long long)__float_as_uint(sh.sc[c]) << 32) |
+                                             (unsigned long long)(0xffffffffu - (unsigned)sh.idx[c]);
+            int lo = 0, hi = vc;  // keys descending: the first position whose key is <= kcand
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sh.key[mid] > kcand) lo = mid + 1; else hi = mid;
+            }
+            if (lo < qs && !MPL_OOB(ss + lo >= d.smax, 504))
+                d.h[(size_t)i * d.smax + ss + lo] = sh.hb[c];
         }
     }
 }

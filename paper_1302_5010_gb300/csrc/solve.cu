@@ -203,14 +203,14 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
     const int ty = tid >> 3, tx = tid & 7;
     const int lr = tid >> 3, lk = (tid & 7) * 4;
 
-    // columns 0..q-1 are the new atoms, column q is the signal b itself (gives h = A_S^T b)
-    for (int b0 = 0; b0 <= q; b0 += GBN) {
+    // columns 0..q-1 are the new atoms (their h = a^T b comes with the selection's re-score)
+    for (int b0 = 0; b0 < q; b0 += GBN) {
         float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         const int ra0 = a0 + lr, ra1 = a0 + lr + 32;
         const float* pa0 = (ra0 < s) ? d.A32 + (size_t)Si[ra0] * n : nullptr;
         const float* pa1 = (ra1 < s) ? d.A32 + (size_t)Si[ra1] * n : nullptr;
         const int rb = b0 + lr;
-        const float* pb = (rb < q) ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+        const float* pb = (rb < q) ? d.A32 + (size_t)Si[s0 + rb] * n : nullptr;
         float4 v0 = gram_load<VEC>(pa0, lk, n), v1 = gram_load<VEC>(pa1, lk, n), vb = gram_load<VEC>(pb, lk, n);
         const int nsl = (n + GBK - 1) / GBK;
         for (int sl = 0; sl < nsl; ++sl) {
@@ -244,11 +244,7 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int bb = b0 + tx * 4 + v;
-                if (bb > q) continue;
-                if (bb == q) {
-                    if (a >= s0) d.h[(size_t)i * smax + a] = acc[u][v];  // h of the new atoms
-                    continue;
-                }
+                if (bb >= q) continue;
                 const int col = s0 + bb;
                 Gi[(size_t)a * smax + col] = acc[u][v];
                 Gi[(size_t)col * smax + a] = acc[u][v];
@@ -260,8 +256,8 @@ __global__ void __launch_bounds__(256) k_gram(Dev d) {
 // Same per-output summation order (k ascending, one FMA chain) as k_gram, with
 // the K slices staged by cp.async in a GS-deep ring so that GS - 1 slices are in
 // flight while one is consumed.  Tile BM rows (atoms of S) x BN columns (new
-// atoms, then b); each thread computes TR rows x TC columns.  The host takes the
-// narrow 32 x 16 tile when at most 15 atoms arrive per signal (the columns of a
+// atoms); each thread computes TR rows x TC columns.  The host takes the
+// narrow 32 x 16 tile when at most 16 atoms arrive per signal (the columns of a
 // wider tile would mostly be empty).  Needs n % 4 == 0 (16-byte rows).
 constexpr int GS = 4, GPAD = GBK + 4;
 
@@ -286,8 +282,8 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
     const int a0 = blockIdx.y * BM;
     if (a0 >= s || q == 0) return;
     const int n = d.n, smax = d.smax;
-    if (blockIdx.y == 0 && threadIdx.x == 0)  // s + 1 columns (atoms, b) read, 2 s q of G and q of h written
-        atomicAdd(&d.cnt->gram_bytes, 4ull * n * (s + 1) + 8ull * s * q + 4ull * q);
+    if (blockIdx.y == 0 && threadIdx.x == 0)  // s atom columns read, 2 s q of G written
+        atomicAdd(&d.cnt->gram_bytes, 4ull * n * s + 8ull * s * q);
     const int* Si = d.S + (size_t)i * smax;
     float* Gi = d.G + (size_t)i * smax * smax;
     extern __shared__ __align__(16) float gsm[];
@@ -296,7 +292,7 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
     const int tid = threadIdx.x;
     const int ty = tid / NX, tx = tid % NX;
     const int nsl = (n + GBK - 1) / GBK;
-    for (int b0 = 0; b0 <= q; b0 += BN) {
+    for (int b0 = 0; b0 < q; b0 += BN) {
         // source rows of this thread's chunks (c = tid + 256 e), fixed for the column chunk
         constexpr int PER = (CHUNKS + 255) / 256;
         const float* src[PER];
@@ -312,7 +308,7 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
                     p = ra < s ? d.A32 + (size_t)Si[ra] * n : nullptr;
                 } else {
                     const int rb = b0 + rr - BM;
-                    p = rb < q ? d.A32 + (size_t)Si[s0 + rb] * n : (rb == q ? d.B + (size_t)i * n : nullptr);
+                    p = rb < q ? d.A32 + (size_t)Si[s0 + rb] * n : nullptr;
                 }
             }
             src[e] = p;
@@ -375,11 +371,7 @@ __global__ void __launch_bounds__(256) k_gram_async(Dev d) {
 #pragma unroll
             for (int v = 0; v < TC; ++v) {
                 const int bb = b0 + tx + NX * v;
-                if (bb > q) continue;
-                if (bb == q) {
-                    if (a >= s0) d.h[(size_t)i * smax + a] = acc[u][v];
-                    continue;
-                }
+                if (bb >= q) continue;
                 const int col = s0 + bb;
                 Gi[(size_t)a * smax + col] = acc[u][v];
                 Gi[(size_t)col * smax + a] = acc[u][v];
@@ -1224,10 +1216,10 @@ cudaError_t launch_gram(const Dev& d, int ub, int qmax, cudaStream_t s, int64_t*
     if ((d.n & 3) == 0) {
         cudaError_t ep = prepare_gram();
         if (ep != cudaSuccess) return ep;
-        if (qmax + 1 <= 16) {  // the new atoms and b fit one 16-column tile
+        if (qmax <= 16) {  // the new atoms fit one 16-column tile
             dim3 grid(ub, (d.smax + 31) / 32);
             ep = launch_chain(k_gram_async<32, 16, 1, 2>, grid, dim3(256), gram_smem<32, 16>(), s, d);
-        } else if (qmax + 1 <= 64) {  // one 64-column pass (e.g. a warm start's first iteration)
+        } else if (qmax <= 64) {  // one 64-column pass (e.g. a warm start's first iteration)
             dim3 grid(ub, (d.smax + 63) / 64);
             ep = launch_chain(k_gram_async<64, 64, 4, 4>, grid, dim3(256), gram_smem<64, 64>(), s, d);
         } else {
