@@ -87,6 +87,17 @@ def test_long_signals_residual_in_global_memory():
         check_against_oracle(P, X64, oracle_solve(P))
 
 
+def test_long_signals_rescore_from_global_memory():
+    """n > 8192: the selection's re-score reads the residual and b from global memory (up to
+    8192 floats of them are staged in shared memory), and the residual runs in nine row blocks."""
+    P = synth.small_problem(8200, 2000, 6, 20, 60, rho=10, seed=8200, lam_frac=0.02)
+    Xo = oracle_solve(P)
+    for precision in (0, 1):
+        X, X64, res = solve_gpu(P, precision=precision)
+        assert_certified(res)
+        check_against_oracle(P, X64, Xo)
+
+
 def test_c2_subset_all_signals():
     P = synth.make_config("c2", p=48)
     X, X64, res = solve_gpu(P)
