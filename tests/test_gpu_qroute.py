@@ -106,8 +106,8 @@ def test_gram_from_q_is_bit_identical_c2(precision):
 
 @pytest.mark.parametrize("n,m,p,rho,omega", [(198, 777, 9, 3, 1), (260, 1000, 13, 5, 1), (256, 1000, 11, 4, 3)])
 def test_gram_from_q_ragged(n, m, p, rho, omega):
-    """n % 4 != 0: the scalar Gram kernel and the scalar h chain; n % 16 != 0:
-    the vector chain's ragged tail; omega > 1: Algorithm 2's explored atoms."""
+    """n % 4 != 0: the scalar Gram kernel and the selection's scalar re-score (which forms h);
+    n % 16 != 0: ragged K slices; omega > 1: Algorithm 2's explored atoms."""
     P = synth.small_problem(n, m, p, 4, min(30, n // 6), rho=rho, seed=3 * n + m + p, lam_frac=0.03)
     Xg, _, _ = solve_gpu(P, precision=0, omega=omega, reentry=1)
     X, X64, res = solve_gpu(P, precision=0, omega=omega, qgram=1, reentry=1)
